@@ -1,0 +1,215 @@
+/*
+ * bqrrp.h -- C ABI of the B300 (sm_103a) BQRRP library.
+ *
+ * BQRRP is the blocked randomized column-pivoted QR of arXiv 2507.00976
+ * ("Anatomy of High-Performance Column-Pivoted QR Decomposition"), Alg. 1:
+ * sketch A once, then per block of b columns pick pivots by LU with partial
+ * pivoting on the small d x (n-s) sketch (Alg. 2), permute A's columns
+ * (Alg. 5), factor the panel by preconditioned Cholesky QR plus Householder
+ * reconstruction (Alg. 3), apply the block reflector to the trailing matrix and
+ * update the sketch (Duersch-Gu update, last step of Alg. 1).
+ *
+ * Common conventions
+ *  - Matrices are FP64, column-major: element (i,j) of X lives at
+ *    X[i + j*ldx].  All matrix and vector pointers are DEVICE pointers unless
+ *    the name ends in _host.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) unless stated otherwise, and allocates no device memory:
+ *    scratch space comes from the caller's `workspace`.
+ *  - Return value: 0 on success; -i when argument i is invalid (LAPACK "info"
+ *    convention, arguments counted from 1); a positive BQRRP_E* code
+ *    otherwise.  The message of the last failure on the calling thread is
+ *    returned by bqrrp_last_error().  No call aborts the process.
+ */
+#ifndef BQRRP_H
+#define BQRRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define BQRRP_OK 0
+#define BQRRP_ENOMEM 1      /* workspace smaller than bqrrp_workspace_query() */
+#define BQRRP_ECUDA 2       /* a CUDA runtime call failed                      */
+#define BQRRP_ENUMERIC 3    /* A holds NaN or Inf                              */
+#define BQRRP_ETIMEOUT 4    /* a grid-wide barrier gave up waiting             */
+#define BQRRP_EUNSUPPORTED 5 /* shape outside the supported range             */
+
+/* Sketching operator kinds (Alg. 1 sample step, Sec. 4.2). */
+#define BQRRP_SKETCH_DENSE 0   /* d x m, entries +-1 from Philox4x32-10          */
+#define BQRRP_SKETCH_SPARSE 1  /* d x m, nnz entries +-1 per column              */
+
+/* Panel factorizations for qr_tall (Sec. 2.3 / Sec. 4.5). */
+#define BQRRP_PANEL_CHOLQR 0   /* Alg. 3: preconditioned CholQR + reconstruction */
+#define BQRRP_PANEL_HQR 1      /* Householder QR of the panel                    */
+
+typedef struct bqrrp_opts {
+    int sketch_kind;     /* BQRRP_SKETCH_DENSE (default) or BQRRP_SKETCH_SPARSE */
+    int64_t sketch_nnz;  /* nonzeros per column of a sparse sketch (default 8)  */
+    int panel_kind;      /* BQRRP_PANEL_CHOLQR (default) or BQRRP_PANEL_HQR    */
+    int64_t reserved[5]; /* must be zero                                        */
+} bqrrp_opts;
+
+/*
+ * bqrrp_factor -- column-pivoted QR  A*P = Q*R  by BQRRP (Alg. 1 with Alg. 2
+ * as qrcp_wide and Alg. 3 as qr_tall; Sec. 4 for the storage layout).
+ *
+ *  m, n      rows and columns of A; 0 <= n <= m (m < n returns -1).
+ *  A         device, m x n, column-major, leading dimension lda >= max(1,m).
+ *            In: the matrix.  Out (GEQP3 format, Sec. 1.2): rows 0..rank-1 of
+ *            the upper trapezoid hold R; below the diagonal of columns
+ *            0..rank-1 the Householder vectors v_i (v_i(i) = 1 implicit).
+ *            When rank < n the rows rank..m-1 of columns rank..n-1 are
+ *            unspecified.
+ *  b         block size, b >= 1 (b > n factors in one block).
+ *  d         sketch rows, d >= b (the paper's d = ceil(gamma*b)).
+ *  seed      64-bit key of the sketching operator (see bqrrp_sketch_operator).
+ *  jpvt      device, n int64, out: 1-based permutation, column j of A*P is
+ *            column jpvt[j]-1 of A.
+ *  tau       device, n doubles, out: tau[0..rank-1] are the reflector scalars,
+ *            the rest are zero.
+ *  rank      HOST, out: the numerical rank l (Sec. 2.2).  Written before the
+ *            call returns: the call synchronizes `stream` a few times per
+ *            block (the block rank k decides the control flow).
+ *  opts      nullable (defaults above).
+ *  workspace device scratch of at least bqrrp_workspace_query() bytes,
+ *            256-byte aligned; owned by the caller, contents undefined on exit.
+ *
+ * Errors: -1 m, -2 n, -3 A, -4 lda, -5 b, -6 d, -8 jpvt, -9 tau, -10 rank,
+ * -11 opts, -12 workspace, BQRRP_ENOMEM when workspace_bytes is too small,
+ * BQRRP_ENUMERIC for NaN/Inf in A (A is then left unchanged), BQRRP_ETIMEOUT,
+ * BQRRP_ECUDA.  On any error rank is set to -1 when rank is non-null.
+ */
+int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_t d,
+                 uint64_t seed, int64_t* jpvt, double* tau, int64_t* rank,
+                 const bqrrp_opts* opts, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* Bytes of device workspace bqrrp_factor needs for this shape (0 on invalid
+ * arguments).  Dominant terms: 2*d*n + 2*b*n + m*b + max(m,d)*min(n, 2d) doubles. */
+size_t bqrrp_workspace_query(int64_t m, int64_t n, int64_t b, int64_t d, const bqrrp_opts* opts);
+
+/*
+ * bqrrp_factor_host -- the same factorization for HOST buffers: A_host
+ * (m x n, ld lda, in/out), jpvt_host (n) and tau_host (n) live in host memory
+ * (pinned memory gives full PCIe/C2C bandwidth).  The call copies A to the
+ * device, factors it with bqrrp_factor, copies A, jpvt and tau back and
+ * synchronizes `stream` before returning.  workspace must hold
+ * bqrrp_workspace_query_host() bytes.
+ */
+int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t b, int64_t d,
+                      uint64_t seed, int64_t* jpvt_host, double* tau_host, int64_t* rank,
+                      const bqrrp_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream);
+size_t bqrrp_workspace_query_host(int64_t m, int64_t n, int64_t b, int64_t d, const bqrrp_opts* opts);
+
+/*
+ * bqrrp_sketch_operator -- write the d x m sketching operator S explicitly
+ * (Alg. 1 sample step; the paper samples Gaussian entries, this library uses
+ * +-1 entries, whose scale is immaterial per the paper's footnote to Alg. 1).
+ * Dense: key = (seed low word, seed high word); for column j and row r the
+ * Philox4x32-10 counter is (j, r/128, 0, 0) and bit r%128 of the 128-bit output
+ * (word (r%128)/32, bit r%32) set means -1.  Sparse: column j holds exactly nnz
+ * entries at distinct rows; draw t = 0,1,... uses counter (j, 1+t, 0, 0), each
+ * output word w proposes row ((w>>1)*d)>>31 with sign -1 iff w&1, repeats are
+ * skipped.  S: device, d x m, ld lds >= d.  Test hook; the factorization never
+ * stores S.  Errors: -1 d, -2 m, -4 kind, -5 nnz, -6 S, -7 lds.
+ */
+int bqrrp_sketch_operator(int64_t d, int64_t m, uint64_t seed, int kind, int64_t nnz,
+                          double* S, int64_t lds, void* stream);
+
+/*
+ * bqrrp_sketch_apply -- Msk = S*A (Alg. 1 sketching step) with S generated on
+ * the fly from (seed, kind, nnz) as above.  A: device m x n (ld lda);
+ * Msk: device d x n (ld ldsk >= d), overwritten.  The sparse kind needs
+ * bqrrp_sketch_apply_workspace() bytes of workspace (the dense kind none).
+ */
+int bqrrp_sketch_apply(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda,
+                       uint64_t seed, int kind, int64_t nnz, double* Msk, int64_t ldsk,
+                       void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_sketch_apply_workspace(int64_t d, int64_t m, int kind, int64_t nnz);
+
+/*
+ * bqrrp_qrcp_wide -- Alg. 2 on a d x N sketch: row-pivoted LU of Msk^T (all
+ * min(N,d) steps, first-maximum pivot rule), piv_transform, column gather and
+ * unpivoted Householder QR.  Msk: device d x N (ld ldsk), in: the sketch;
+ * out: R^sk (upper trapezoid, zeros below the diagonal).  Jsk: device, N int64,
+ * out: 0-based permutation (column t of the permuted sketch was column
+ * Jsk[t]).  ipiv: device, min(N,d) int64, out: the LU swap sequence (0-based).
+ * If the sketch holds NaN/Inf, Jsk is the identity (Sec. 2.2).
+ */
+int bqrrp_qrcp_wide(int64_t d, int64_t N, double* Msk, int64_t ldsk, int64_t* Jsk, int64_t* ipiv,
+                    void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_qrcp_wide_workspace(int64_t d, int64_t N);
+
+/*
+ * bqrrp_col_perm -- column permutation of Alg. 5 in place: afterwards column t
+ * of M (m x N, ld ldm) is the former column J[t] (0-based J, a permutation of
+ * 0..N-1).  Only columns with J[t] != t move; they are staged through the
+ * workspace (bqrrp_col_perm_workspace(m, moved) bytes, moved = an upper bound
+ * on the number of such columns, e.g. N or 2*min(N,d) after Alg. 2).
+ */
+int bqrrp_col_perm(int64_t m, int64_t N, double* M, int64_t ldm, const int64_t* J, int64_t max_moved,
+                   void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_col_perm_workspace(int64_t m, int64_t N, int64_t max_moved);
+
+/*
+ * bqrrp_cholqr_panel -- Alg. 3 on one panel: Pre = M(:,0:k) * Rsk(0:k,0:k)^-1,
+ * Cholesky QR of Pre, Householder reconstruction (modified LU), and
+ * R11 = diag(D) * Rchol * Rsk(0:k, 0:w).  M: device rows x w (ld ldm), in: the
+ * permuted panel, out: R11 in rows 0..k-1 of the upper trapezoid and the
+ * reflectors below the diagonal of columns 0..k-1.  Rsk: device, upper
+ * triangle of a k x w block (ld ldr).  T: device k x k (ld ldt), out: the
+ * compact-WY factor (upper).  tau: device, k doubles, out: diag(T).
+ * kout: HOST, out: k, lowered if the Cholesky factorization breaks down.
+ */
+int bqrrp_cholqr_panel(int64_t rows, int64_t w, int64_t k, double* M, int64_t ldm,
+                       const double* Rsk, int64_t ldr, double* T, int64_t ldt, double* tau,
+                       int64_t* kout, void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_cholqr_panel_workspace(int64_t rows, int64_t w);
+
+/*
+ * bqrrp_geqrf -- the library's own unpivoted blocked Householder QR (GEQRF
+ * semantics, the denominator of the paper's canonical comparison, Sec. 7):
+ * A (m x n, ld lda, m >= n) is overwritten with R and the reflectors,
+ * tau (n) receives the scalars.  nb: outer block (0 = default 64).
+ */
+int bqrrp_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau, int64_t nb,
+                void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_geqrf_workspace(int64_t m, int64_t n, int64_t nb);
+
+/*
+ * bqrrp_dgemm -- C = alpha*op(A)*op(B) + beta*C with the library's FP64 SIMT
+ * GEMM (the kernel behind the trailing update of Alg. 1).  transa/transb:
+ * 'N' or 'T'.  C is M x N, op(A) M x K, op(B) K x N.  beta == 0 never reads C.
+ * Uses up to bqrrp_dgemm_workspace() bytes of workspace for split-K partials
+ * (pass NULL/0 to disable splitting).
+ */
+int bqrrp_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha,
+                const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_dgemm_workspace(int64_t M, int64_t N, int64_t K);
+
+/*
+ * bqrrp_probe_fp64_peak -- measurement helper: runs an FP64 fused-multiply-add
+ * loop on every SM for about `iters` x 32 DFMA per thread and returns the
+ * achieved FP64 rate in TFLOP/s (timed with CUDA events; synchronizes).
+ * Returns a negative value on failure.
+ */
+double bqrrp_probe_fp64_peak(int iters, void* stream);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* bqrrp_last_error(void);
+
+/* Library version string. */
+const char* bqrrp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BQRRP_H */

@@ -59,6 +59,8 @@ def lib():
             L.bqrrp_ref_lupp.restype = _i64
             L.bqrrp_ref_piv_transform.argtypes = [_i64, _i64, _ip, _ip]
             L.bqrrp_ref_orhr_col.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp]
+            L.bqrrp_ref_cholqr_panel.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64, _dp]
+            L.bqrrp_ref_cholqr_panel.restype = _i64
             L.bqrrp_ref_factor.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _u64, ctypes.c_int, _i64,
                                            ctypes.c_int, _ip, _dp, _ip, _dp, _i64, _i64, _dp]
             L.bqrrp_ref_factor.restype = ctypes.c_int
@@ -154,6 +156,19 @@ def orhr_col(Q):
     D = np.zeros(k, dtype=np.float64)
     lib().bqrrp_ref_orhr_col(rows, k, _p(Y), max(rows, 1), _p(T), max(k, 1), _p(D))
     return Y, T, D
+
+
+def cholqr_panel(M, Rsk, k):
+    """Alg. 3 on one panel: returns (panel with R11 and reflectors, T (k x k),
+    tau, k kept)."""
+    M = _f(M)
+    Rsk = _f(Rsk)
+    rows, w = M.shape
+    T = np.zeros((max(k, 1), max(k, 1)), dtype=np.float64, order="F")
+    tau = np.zeros(max(k, 1), dtype=np.float64)
+    kc = lib().bqrrp_ref_cholqr_panel(rows, w, k, _p(M), max(rows, 1), _p(Rsk), max(Rsk.shape[0], 1),
+                                      _p(T), max(k, 1), _p(tau))
+    return M, T[:k, :k], tau[:k], kc
 
 
 class Factorization:

@@ -392,6 +392,72 @@ static void apply_qt(int64_t rows, int64_t k, const double* Y, int64_t ldy, cons
     }
 }
 
+/* Alg. 3 on one panel.  Mp: rows x w permuted panel (read only); Rsk: upper
+ * triangle of the sketch's R (ld ldr).  Pre = Mp(:, 0:k) Rsk11^{-1}; G =
+ * Pre^T Pre; Rchol = chol(G); Qc = Pre Rchol^{-1}; (Y, T, D) = ORHR_COL(Qc)
+ * with Y left in Y (rows x k, ld ldy); R11 = diag(D) Rchol Rsk(0:k, 0:w) in
+ * R11 (k x w, ld ldb).  G, Rc, T are k x k with ld ldb.  Returns the number of
+ * columns kept (k, or the column where the Cholesky factorization broke down;
+ * on breakdown Y, T and R11 are not formed). */
+static int64_t ref_cholqr_panel(int64_t rows, int64_t w, int64_t k, const double* Mp, int64_t ldm,
+                                const double* Rsk, int64_t ldr, double* Y, int64_t ldy, double* G,
+                                double* Rc, double* T, double* D, double* R11, int64_t ldb)
+{
+    for (int64_t j = 0; j < k; ++j)
+        for (int64_t i = 0; i < rows; ++i) AT(Y, i, j, ldy) = AT(Mp, i, j, ldm);
+    trsm_right_upper(rows, k, Rsk, ldr, Y, ldy);                  /* Pre = M(:,0:k) Rsk11^{-1} */
+    for (int64_t j = 0; j < k; ++j)                                /* G = Pre^T Pre */
+        for (int64_t l = 0; l < k; ++l) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < rows; ++i) acc += AT(Y, i, j, ldy) * AT(Y, i, l, ldy);
+            AT(G, j, l, ldb) = acc;
+        }
+    int64_t kc = chol_upper(k, G, ldb, Rc, ldb);
+    if (kc < k) return kc;
+    trsm_right_upper(rows, k, Rc, ldb, Y, ldy);                   /* Qc = Pre Rchol^{-1} */
+    bqrrp_ref_orhr_col(rows, k, Y, ldy, T, ldb, D);               /* Y, T, D */
+    /* R11 = diag(D) * Rchol * Rsk(0:k, 0:w)  (k x w) */
+    for (int64_t j = 0; j < w; ++j)
+        for (int64_t i = 0; i < k; ++i) {
+            double acc = 0.0;
+            int64_t tmax = j < k - 1 ? j : k - 1;                 /* Rsk(t,j) = 0 for t > j */
+            for (int64_t t = i; t <= tmax; ++t) acc += AT(Rc, i, t, ldb) * AT(Rsk, t, j, ldr);
+            AT(R11, i, j, ldb) = D[i] * acc;
+        }
+    return k;
+}
+
+/* Test hook: Alg. 3 on a panel with the same layout as above; also writes R11
+ * into the upper trapezoid of Mp's first k rows and the reflectors below the
+ * diagonal (the storage the factorization uses).  tau = diag(T). */
+int64_t bqrrp_ref_cholqr_panel(int64_t rows, int64_t w, int64_t k, double* Mp, int64_t ldm,
+                               const double* Rsk, int64_t ldr, double* T, int64_t ldt, double* tau)
+{
+    int64_t kb = k > 0 ? k : 1;
+    double* Y = (double*)malloc(sizeof(double) * (size_t)(rows > 0 ? rows : 1) * (size_t)kb);
+    double* G = (double*)malloc(sizeof(double) * (size_t)kb * (size_t)kb);
+    double* Rc = (double*)malloc(sizeof(double) * (size_t)kb * (size_t)kb);
+    double* Tk = (double*)malloc(sizeof(double) * (size_t)kb * (size_t)kb);
+    double* D = (double*)malloc(sizeof(double) * (size_t)kb);
+    double* R11 = (double*)malloc(sizeof(double) * (size_t)kb * (size_t)(w > 0 ? w : 1));
+    int64_t kc = -1;
+    if (Y && G && Rc && Tk && D && R11) {
+        kc = ref_cholqr_panel(rows, w, k, Mp, ldm, Rsk, ldr, Y, rows, G, Rc, Tk, D, R11, kb);
+        if (kc == k) {
+            for (int64_t j = 0; j < w; ++j)
+                for (int64_t i = 0; i < k && i <= j; ++i) AT(Mp, i, j, ldm) = AT(R11, i, j, kb);
+            for (int64_t j = 0; j < k; ++j)
+                for (int64_t i = j + 1; i < rows; ++i) AT(Mp, i, j, ldm) = AT(Y, i, j, rows);
+            for (int64_t j = 0; j < k; ++j) {
+                tau[j] = AT(Tk, j, j, kb);
+                for (int64_t i = 0; i < k; ++i) AT(T, i, j, ldt) = AT(Tk, i, j, kb);
+            }
+        }
+    }
+    free(Y); free(G); free(Rc); free(Tk); free(D); free(R11);
+    return kc;
+}
+
 /* trace (nullable): for iteration i, trace[4*i + 0] = k, [1] = min LU margin,
  * [2] = 1 if the sketch was non-finite (identity pivots), [3] = w.
  * Test hooks: max_iters > 0 stops after that many full iterations (the sketch
@@ -503,32 +569,15 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
 
         if (panel_kind == 0) {
             /* ---- Alg. 3: preconditioned Cholesky QR + reconstruction ---- */
-            for (int64_t j = 0; j < k; ++j)
-                for (int64_t i = 0; i < rows; ++i) AT(Pre, i, j, m) = AT(Mp, i, j, lda);
-            trsm_right_upper(rows, k, Ssk, d, Pre, m);          /* Pre = M(:,0:k) Rsk11^{-1} */
-            for (int64_t j = 0; j < k; ++j)                      /* G = Pre^T Pre */
-                for (int64_t l = 0; l < k; ++l) {
-                    double acc = 0.0;
-                    for (int64_t i = 0; i < rows; ++i) acc += AT(Pre, i, j, m) * AT(Pre, i, l, m);
-                    AT(G, j, l, b) = acc;
-                }
-            int64_t kc = chol_upper(k, G, b, Rc, b);
+            int64_t kc = ref_cholqr_panel(rows, w, k, Mp, lda, Ssk, d, Pre, m, G, Rc, T, D, R11, b);
             if (kc < k) {
-                /* Cholesky breakdown: the block is numerically rank kc. */
+                /* Cholesky breakdown: the block is numerically rank kc; redo the
+                 * panel on its leading kc columns (same Gram block). */
                 k = kc;
                 if (trace && it < trace_iters) trace[4 * it + 0] = (double)k;
                 if (k == 0) { ell = s; break; }
+                ref_cholqr_panel(rows, w, k, Mp, lda, Ssk, d, Pre, m, G, Rc, T, D, R11, b);
             }
-            trsm_right_upper(rows, k, Rc, b, Pre, m);           /* Qc = Pre Rchol^{-1} */
-            bqrrp_ref_orhr_col(rows, k, Pre, m, T, b, D);       /* Y, T, D */
-            /* R11 = diag(D) * Rchol * Rsk(0:k, 0:w)  (k x w) */
-            for (int64_t j = 0; j < w; ++j)
-                for (int64_t i = 0; i < k; ++i) {
-                    double acc = 0.0;
-                    int64_t tmax = j < k - 1 ? j : k - 1;     /* Rsk(t,j) = 0 for t > j */
-                    for (int64_t t = i; t <= tmax; ++t) acc += AT(Rc, i, t, b) * AT(Ssk, t, j, d);
-                    AT(R11, i, j, b) = D[i] * acc;
-                }
             for (int64_t j = 0; j < k; ++j) tau[s + j] = AT(T, j, j, b);
         } else {
             /* ---- Householder panel (GEQRF on all w panel columns) ---- */

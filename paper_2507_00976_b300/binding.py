@@ -1,0 +1,306 @@
+"""ctypes binding of ``libbqrrp.so`` (argument marshalling only).
+
+Each function mirrors one entry point of ``include/bqrrp.h`` under the same
+name; every step of the computation runs in the library's CUDA kernels.
+Matrices are torch float64 tensors in column-major layout (``stride(0) == 1``,
+``stride(1)`` = leading dimension), on the current CUDA device; the current
+torch stream is passed to the library.  ``colmajor_empty``/``to_colmajor``
+build such tensors.
+
+There is no fallback: if the shared library is missing or fails to load, the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbqrrp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bqrrp.h")
+
+OK, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+SKETCH_DENSE, SKETCH_SPARSE = 0, 1
+PANEL_CHOLQR, PANEL_HQR = 0, 1
+
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_d = ctypes.c_double
+_lock = threading.Lock()
+_lib = None
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("sketch_kind", ctypes.c_int), ("sketch_nnz", _i64), ("panel_kind", ctypes.c_int),
+                ("reserved", _i64 * 5)]
+
+
+class BqrrpError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} returned {code}: {msg}")
+        self.code = code
+
+
+_SIGS = {
+    "bqrrp_factor": ([_i64, _i64, _vp, _i64, _i64, _i64, _u64, _vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(Opts),
+                      _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_workspace_query": ([_i64, _i64, _i64, _i64, ctypes.POINTER(Opts)], _sz),
+    "bqrrp_factor_host": ([_i64, _i64, _vp, _i64, _i64, _i64, _u64, _vp, _vp, ctypes.POINTER(_i64),
+                           ctypes.POINTER(Opts), _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_workspace_query_host": ([_i64, _i64, _i64, _i64, ctypes.POINTER(Opts)], _sz),
+    "bqrrp_sketch_operator": ([_i64, _i64, _u64, ctypes.c_int, _i64, _vp, _i64, _vp], ctypes.c_int),
+    "bqrrp_sketch_apply": ([_i64, _i64, _i64, _vp, _i64, _u64, ctypes.c_int, _i64, _vp, _i64, _vp, _sz, _vp],
+                           ctypes.c_int),
+    "bqrrp_sketch_apply_workspace": ([_i64, _i64, ctypes.c_int, _i64], _sz),
+    "bqrrp_qrcp_wide": ([_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_qrcp_wide_workspace": ([_i64, _i64], _sz),
+    "bqrrp_col_perm": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_col_perm_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_cholqr_panel": ([_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, ctypes.POINTER(_i64), _vp, _sz,
+                            _vp], ctypes.c_int),
+    "bqrrp_cholqr_panel_workspace": ([_i64, _i64], _sz),
+    "bqrrp_geqrf": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_geqrf_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_dgemm": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _vp,
+                     _sz, _vp], ctypes.c_int),
+    "bqrrp_dgemm_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_probe_fp64_peak": ([ctypes.c_int, _vp], _d),
+    "bqrrp_last_error": ([], ctypes.c_char_p),
+    "bqrrp_version": ([], ctypes.c_char_p),
+}
+
+
+def header_symbols():
+    """Names of the functions declared in include/bqrrp.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(bqrrp_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Load libbqrrp.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_00976_b300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().bqrrp_last_error().decode()
+
+
+def _check(fn, rc):
+    if rc != 0:
+        raise BqrrpError(fn, rc, last_error())
+    return rc
+
+
+# ----------------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def colmajor_empty(m, n, dtype=None, device="cuda"):
+    torch = _torch()
+    dtype = dtype or torch.float64
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def to_colmajor(x, device="cuda"):
+    """Column-major float64 copy of a numpy array or tensor on ``device``."""
+    torch = _torch()
+    t = torch.as_tensor(x, dtype=torch.float64)
+    out = colmajor_empty(t.shape[0], t.shape[1], device=device)
+    out.copy_(t)
+    return out
+
+
+def _ld(t):
+    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[0] > 1):
+        raise ValueError("expected a column-major 2-D tensor (stride(0) == 1)")
+    return max(int(t.stride(1)), max(int(t.shape[0]), 1))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR):
+    o = Opts()
+    o.sketch_kind = sketch_kind
+    o.sketch_nnz = nnz
+    o.panel_kind = panel_kind
+    return o
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------- entry points
+def bqrrp_workspace_query(m, n, b, d, opts=None):
+    return int(lib().bqrrp_workspace_query(m, n, b, d, ctypes.byref(opts) if opts else None))
+
+
+def bqrrp_factor(A, b, d, seed, jpvt, tau, opts=None, workspace=None, stream=None):
+    """A (m x n column-major float64, in/out), jpvt (int64, n), tau (float64, n).
+    Returns the rank.  Allocates the workspace with torch when none is given."""
+    m, n = A.shape
+    if workspace is None:
+        workspace = _workspace(bqrrp_workspace_query(m, n, b, d, opts), A.device)
+    rank = _i64(0)
+    rc = lib().bqrrp_factor(m, n, _ptr(A), _ld(A), b, d, seed, _ptr(jpvt), _ptr(tau), ctypes.byref(rank),
+                            ctypes.byref(opts) if opts else None, _ptr(workspace), workspace.numel(), _stream(stream))
+    _check("bqrrp_factor", rc)
+    return rank.value
+
+
+def bqrrp_factor_status(A, b, d, seed, jpvt, tau, opts=None, workspace=None, workspace_bytes=None, stream=None):
+    """Like bqrrp_factor but returns (status code, rank) instead of raising."""
+    m, n = A.shape
+    rank = _i64(0)
+    nbytes = workspace.numel() if workspace is not None else 0
+    if workspace_bytes is not None:
+        nbytes = workspace_bytes
+    rc = lib().bqrrp_factor(m, n, _ptr(A), _ld(A) if n > 0 else max(m, 1), b, d, seed, _ptr(jpvt), _ptr(tau),
+                            ctypes.byref(rank), ctypes.byref(opts) if opts else None, _ptr(workspace), nbytes,
+                            _stream(stream))
+    return rc, rank.value
+
+
+def bqrrp_workspace_query_host(m, n, b, d, opts=None):
+    return int(lib().bqrrp_workspace_query_host(m, n, b, d, ctypes.byref(opts) if opts else None))
+
+
+def bqrrp_factor_host(A_host, b, d, seed, jpvt_host, tau_host, workspace, opts=None, stream=None):
+    """Host-buffer form: A_host (column-major host tensor, in/out), jpvt_host,
+    tau_host host tensors; workspace a device uint8 tensor."""
+    m, n = A_host.shape
+    rank = _i64(0)
+    rc = lib().bqrrp_factor_host(m, n, _ptr(A_host), _ld(A_host), b, d, seed, _ptr(jpvt_host), _ptr(tau_host),
+                                 ctypes.byref(rank), ctypes.byref(opts) if opts else None, _ptr(workspace),
+                                 workspace.numel(), _stream(stream))
+    _check("bqrrp_factor_host", rc)
+    return rank.value
+
+
+def bqrrp_sketch_operator(d, m, seed, kind=SKETCH_DENSE, nnz=8, S=None, stream=None):
+    if S is None:
+        S = colmajor_empty(d, m)
+    rc = lib().bqrrp_sketch_operator(d, m, seed, kind, nnz, _ptr(S), _ld(S), _stream(stream))
+    _check("bqrrp_sketch_operator", rc)
+    return S
+
+
+def bqrrp_sketch_apply(A, d, seed, kind=SKETCH_DENSE, nnz=8, Msk=None, stream=None):
+    m, n = A.shape
+    if Msk is None:
+        Msk = colmajor_empty(d, n, device=A.device)
+    ws = _workspace(lib().bqrrp_sketch_apply_workspace(d, m, kind, nnz), A.device)
+    rc = lib().bqrrp_sketch_apply(d, m, n, _ptr(A), _ld(A), seed, kind, nnz, _ptr(Msk), _ld(Msk), _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check("bqrrp_sketch_apply", rc)
+    return Msk
+
+
+def bqrrp_qrcp_wide(Msk, stream=None):
+    """Alg. 2 in place on the d x N sketch; returns (Jsk, ipiv) int64 tensors."""
+    torch = _torch()
+    d, N = Msk.shape
+    Jsk = torch.empty(max(N, 1), dtype=torch.int64, device=Msk.device)
+    ipiv = torch.empty(max(min(N, d), 1), dtype=torch.int64, device=Msk.device)
+    ws = _workspace(lib().bqrrp_qrcp_wide_workspace(d, N), Msk.device)
+    rc = lib().bqrrp_qrcp_wide(d, N, _ptr(Msk), _ld(Msk), _ptr(Jsk), _ptr(ipiv), _ptr(ws), ws.numel(),
+                               _stream(stream))
+    _check("bqrrp_qrcp_wide", rc)
+    return Jsk[:N], ipiv[: min(N, d)]
+
+
+def bqrrp_col_perm(M, J, max_moved=None, stream=None):
+    m, N = M.shape
+    mm = N if max_moved is None else max_moved
+    ws = _workspace(lib().bqrrp_col_perm_workspace(m, N, mm), M.device)
+    rc = lib().bqrrp_col_perm(m, N, _ptr(M), _ld(M), _ptr(J), mm, _ptr(ws), ws.numel(), _stream(stream))
+    _check("bqrrp_col_perm", rc)
+    return M
+
+
+def bqrrp_cholqr_panel(M, Rsk, k, stream=None):
+    """Alg. 3 in place on the rows x w panel M; returns (T, tau, k kept)."""
+    torch = _torch()
+    rows, w = M.shape
+    T = colmajor_empty(max(k, 1), max(k, 1), device=M.device)
+    tau = torch.zeros(max(k, 1), dtype=torch.float64, device=M.device)
+    kout = _i64(0)
+    ws = _workspace(lib().bqrrp_cholqr_panel_workspace(rows, w), M.device)
+    rc = lib().bqrrp_cholqr_panel(rows, w, k, _ptr(M), _ld(M), _ptr(Rsk), _ld(Rsk), _ptr(T), _ld(T), _ptr(tau),
+                                  ctypes.byref(kout), _ptr(ws), ws.numel(), _stream(stream))
+    _check("bqrrp_cholqr_panel", rc)
+    kk = kout.value
+    return T[:kk, :kk], tau[:kk], kk
+
+
+def bqrrp_geqrf(A, nb=0, tau=None, workspace=None, stream=None):
+    torch = _torch()
+    m, n = A.shape
+    if tau is None:
+        tau = torch.zeros(max(min(m, n), 1), dtype=torch.float64, device=A.device)
+    if workspace is None:
+        workspace = _workspace(lib().bqrrp_geqrf_workspace(m, n, nb), A.device)
+    rc = lib().bqrrp_geqrf(m, n, _ptr(A), _ld(A), _ptr(tau), nb, _ptr(workspace), workspace.numel(), _stream(stream))
+    _check("bqrrp_geqrf", rc)
+    return tau
+
+
+def bqrrp_geqrf_workspace(m, n, nb=0):
+    return int(lib().bqrrp_geqrf_workspace(m, n, nb))
+
+
+def bqrrp_dgemm(transa, transb, alpha, A, B, beta, C, workspace=None, stream=None):
+    M, N = C.shape
+    K = A.shape[0] if transa.upper() == "T" else A.shape[1]
+    if workspace is None:
+        workspace = _workspace(lib().bqrrp_dgemm_workspace(M, N, K), C.device)
+    rc = lib().bqrrp_dgemm(transa.encode(), transb.encode(), M, N, K, alpha, _ptr(A), _ld(A), _ptr(B), _ld(B), beta,
+                           _ptr(C), _ld(C), _ptr(workspace), workspace.numel(), _stream(stream))
+    _check("bqrrp_dgemm", rc)
+    return C
+
+
+def bqrrp_probe_fp64_peak(iters=2000, stream=None):
+    return float(lib().bqrrp_probe_fp64_peak(iters, _stream(stream)))
+
+
+# ----------------------------------------------------------------- convenience
+def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", stream=None):
+    """Factor a copy of A (any 2-D float64 tensor/array); returns
+    (F column-major with R and reflectors, jpvt, tau, rank) as device tensors."""
+    torch = _torch()
+    F = to_colmajor(A)
+    m, n = F.shape
+    jpvt = torch.empty(max(n, 1), dtype=torch.int64, device=F.device)
+    tau = torch.empty(max(n, 1), dtype=torch.float64, device=F.device)
+    opts = make_opts(SKETCH_DENSE if sketch == "dense" else SKETCH_SPARSE, nnz,
+                     PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR)
+    rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
+    return F, jpvt[:n], tau[:n], rank

@@ -1,0 +1,532 @@
+// bqrrp.cu -- host orchestrator of BQRRP (Alg. 1) and the C ABI.
+//
+// Per block (iteration i, s = i*b, c = min(n, s+b), w = c-s, N = n-s):
+//   Alg. 2  : LU with partial pivoting of the sketch's transpose (lu panels +
+//             GEMM), piv_transform, gather of the moved sketch columns,
+//             Householder QR of the d x N sketch -> R^sk
+//   tri_rank: k from diag(R^sk11) (device), permutation of A(:, s:) and J(s:)
+//   host    : one read-back (k, zero-column flag, barrier status)
+//   Alg. 3  : Pre = M Rsk11^-1, G = Pre^T Pre, Rchol = chol(G)
+//   host    : one read-back (Cholesky breakdown lowers k)
+//             Qc = Pre Rchol^-1, modified LU -> Y, U, D; T = -U D Y1^-T;
+//             R11 = D Rchol Rsk(0:k, 0:w)
+//   trailing: A(s:, c:) -= Y (T^T (Y^T A(s:, c:)))   (first k rows if k < w)
+//   sketch  : Msk(0:w, c:) -= (Rsk11 R11^-1) R12      (Duersch-Gu update)
+// All arithmetic runs in the library's kernels; the host only sequences
+// launches and reads k.
+#include <climits>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace bq {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local char g_err[512] = "";
+}
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* get_error() { return g_err; }
+
+int current_device(Device* dev) {
+    static std::mutex mu;
+    static int cached_sms[64] = {0};
+    int id = 0;
+    BQ_CUDA(cudaGetDevice(&id));
+    std::lock_guard<std::mutex> lk(mu);
+    if (id < 0 || id >= 64) { set_error("device id out of range"); return BQRRP_ECUDA; }
+    if (cached_sms[id] == 0) {
+        int sms = 0;
+        BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, id));
+        cached_sms[id] = sms;
+    }
+    dev->id = id;
+    dev->sms = cached_sms[id];
+    return 0;
+}
+
+
+namespace {
+
+constexpr double kUnitRoundoff = 1.1102230246251565e-16;   // 2^-53
+
+// ------------------------------------------------------------------ small kernels
+__global__ void init_status_kernel(DevStatus* st) {
+    st->err_timeout = 0;
+    st->potrf_info = INT_MAX;
+    st->sk_nonfinite = 0;
+    st->a_nonfinite = 0;
+    st->zero_col = 0;
+    st->k = 0;
+    st->moved = 0;
+    st->r00 = 0.0;
+    st->bar.count = 0;
+    st->bar.gen = 0;
+}
+
+__global__ void iota_kernel(i64 n, i64* J) {
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) J[i] = i;
+}
+
+__global__ void plus_one_kernel(i64 n, const i64* J, i64* jpvt) {
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) jpvt[i] = J[i] + 1;
+}
+
+// tri_rank (Sec. 2.2, reading): k = largest j <= w with |Rsk(t,t)| > 10 d u r00
+// for all t < j, r00 = |Rsk(0,0)| of the first iteration.
+__global__ void tri_rank_kernel(DevStatus* st, const double* Rsk, i64 ldr, i64 w, i64 d, int first) {
+    if (threadIdx.x != 0) return;
+    if (first) st->r00 = fabs(Rsk[0]);
+    const double r00 = st->r00;
+    const double thr = 10.0 * (double)d * kUnitRoundoff * r00;
+    i64 k = 0;
+    if (r00 > 0.0 && isfinite(r00))
+        while (k < w) {
+            const double v = Rsk[k + k * ldr];
+            if (!isfinite(v) || !(fabs(v) > thr)) break;
+            ++k;
+        }
+    st->k = k;
+}
+
+// st->zero_col <- 1 if any entry of the column is nonzero (early-exit test)
+__global__ void col_nonzero_kernel(i64 rows, const double* col, int* flag) {
+    int nz = 0;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (i64)gridDim.x * blockDim.x)
+        nz |= (col[i] != 0.0);
+    nz = __syncthreads_or(nz);
+    if (nz && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// From the modified LU result in Y's top k x k block: U = triu, Tb = -U diag(D),
+// and Y's top block becomes unit lower triangular.
+__global__ void recon_split_kernel(i64 k, double* Y, i64 ldy, const double* D, double* U, double* Tb, i64 ldb) {
+    const i64 total = k * k;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % k, j = e / k;
+        const double y = Y[i + j * ldy];
+        if (i <= j) {
+            U[i + j * ldb] = y;
+            Tb[i + j * ldb] = -y * D[j];
+            Y[i + j * ldy] = (i == j) ? 1.0 : 0.0;
+        } else {
+            U[i + j * ldb] = 0.0;
+            Tb[i + j * ldb] = 0.0;
+        }
+    }
+}
+
+// Write the panel back into A (GEQP3 layout): rows 0..k-1 of the upper
+// trapezoid get diag(D) * R11, column j < k below the diagonal gets Y(:, j);
+// tau[j] = T(j, j).
+__global__ void panel_writeback_kernel(i64 rows, i64 w, i64 k, double* A, i64 lda, const double* Y, i64 ldy,
+                                       const double* R11, const double* D, const double* Tb, i64 ldb, double* tau) {
+    const i64 total = rows * w;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % rows, j = e / rows;
+        if (i < k && i <= j) A[i + j * lda] = D[i] * R11[i + j * ldb];
+        else if (j < k && i > j) A[i + j * lda] = Y[i + j * ldy];
+    }
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < k) tau[t] = Tb[t + t * ldb];
+}
+
+__global__ void zero_tail_kernel(i64 from, i64 to, double* tau) {
+    const i64 i = from + (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < to) tau[i] = 0.0;
+}
+
+inline unsigned gblocks(const Ctx& c, i64 total) { return (unsigned)imax(1, imin(cdiv(total, 256), 8LL * c.dev.sms)); }
+
+// ------------------------------------------------------------------ workspace plan
+struct Bufs {
+    DevStatus* st;
+    double *Msk, *Xlu, *stage, *Ypan, *Vqr, *Tqr, *W, *W2, *G, *U, *Tb, *R11, *Z, *D, *sktau, *splitk, *coop;
+    i64 *ipiv, *Jsk, *pos, *src, *cnt, *J, *Jstage;
+    char* sparse_ws;
+    size_t sparse_bytes, splitk_elems, coop_elems;
+    i64 max_moved, ldst, bb, wrows;
+};
+
+void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) {
+    const i64 bb = imax(1, imin(b, n));
+    B->bb = bb;
+    B->max_moved = imax(1, imin(n, 2 * imin(d, n)));
+    B->ldst = imax(m, d);
+    B->wrows = imax(bb, 64);
+    B->st = ar.take<DevStatus>(1);
+    B->Msk = ar.take<double>((size_t)d * n);
+    B->Xlu = ar.take<double>((size_t)d * n);
+    B->stage = ar.take<double>((size_t)B->ldst * B->max_moved);
+    B->Ypan = ar.take<double>((size_t)m * bb);
+    B->Vqr = ar.take<double>((size_t)imax(m, d) * 64);
+    B->Tqr = ar.take<double>(64 * 64);
+    B->W = ar.take<double>((size_t)B->wrows * n);
+    B->W2 = ar.take<double>((size_t)B->wrows * n);
+    B->G = ar.take<double>((size_t)bb * bb);
+    B->U = ar.take<double>((size_t)bb * bb);
+    B->Tb = ar.take<double>((size_t)bb * bb);
+    B->R11 = ar.take<double>((size_t)bb * bb);
+    B->Z = ar.take<double>((size_t)bb * bb);
+    B->D = ar.take<double>((size_t)bb);
+    B->sktau = ar.take<double>((size_t)imax(d, n));
+    B->splitk_elems = (size_t)imax(16 * bb * bb, (i64)1 << 22);
+    B->splitk = ar.take<double>(B->splitk_elems);
+    coop_scratch_elems(64, 148, &B->coop_elems);
+    B->coop = ar.take<double>(B->coop_elems);
+    B->ipiv = ar.take<i64>((size_t)d);
+    B->Jsk = ar.take<i64>((size_t)n);
+    B->pos = ar.take<i64>((size_t)B->max_moved);
+    B->src = ar.take<i64>((size_t)B->max_moved);
+    B->cnt = ar.take<i64>(4);
+    B->J = ar.take<i64>((size_t)n);
+    B->Jstage = ar.take<i64>((size_t)B->max_moved);
+    B->sparse_bytes = 0;
+    B->sparse_ws = nullptr;
+    if (o.sketch_kind == BQRRP_SKETCH_SPARSE) {
+        B->sparse_bytes = sketch_sparse_ws(d, m, o.sketch_nnz);
+        B->sparse_ws = ar.take<char>(B->sparse_bytes);
+    }
+}
+
+bqrrp_opts defaults(const bqrrp_opts* o) {
+    bqrrp_opts r{};
+    r.sketch_kind = BQRRP_SKETCH_DENSE;
+    r.sketch_nnz = 8;
+    r.panel_kind = BQRRP_PANEL_CHOLQR;
+    if (o) {
+        r.sketch_kind = o->sketch_kind;
+        r.sketch_nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
+        r.panel_kind = o->panel_kind;
+    }
+    return r;
+}
+
+int check_opts(const bqrrp_opts* o, i64 d) {
+    if (!o) return 0;
+    if (o->sketch_kind != BQRRP_SKETCH_DENSE && o->sketch_kind != BQRRP_SKETCH_SPARSE) return 1;
+    if (o->panel_kind != BQRRP_PANEL_CHOLQR && o->panel_kind != BQRRP_PANEL_HQR) return 1;
+    if (o->sketch_kind == BQRRP_SKETCH_SPARSE) {
+        const i64 nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
+        if (nnz > d || nnz > 64) return 1;
+    }
+    for (int i = 0; i < 5; ++i)
+        if (o->reserved[i] != 0) return 1;
+    return 0;
+}
+
+int read_status(const Ctx& c, DevStatus* host) {
+    BQ_CUDA(cudaMemcpyAsync(host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.stream));
+    BQ_CUDA(cudaStreamSynchronize(c.stream));
+    if (host->err_timeout) {
+        set_error("a grid-wide barrier timed out");
+        return BQRRP_ETIMEOUT;
+    }
+    return 0;
+}
+
+}  // namespace
+
+// Alg. 3 on one panel Mp (rows x w, ld ldm) with preconditioner Rsk (upper
+// triangle, ld ldr): Pre = Mp(:, 0:k) Rsk11^-1 in Y, G = Pre^T Pre, Rchol =
+// chol(G) (a breakdown lowers *k), Qc = Pre Rchol^-1, modified LU of Qc (Y
+// unit lower trapezoidal, U, D), T = -U D Y1^-T in Tb, R11 = D Rchol
+// Rsk(0:k, 0:w); R11 and the reflectors are written into Mp and diag(T) into
+// tau.  Y and Tb stay valid for the trailing update.  Synchronizes the stream
+// once (to read the Cholesky status).
+int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 ldm, const double* Rsk, i64 ldr,
+                       double* Y, i64 ldy, double* G, double* U, double* Tb, double* R11, double* D, i64 ldb,
+                       double* tau) {
+    i64 k = *kio;
+    View Yv = colmajor(Y, ldy);
+    BQ_TRY(copy_mat(c, rows, k, Mp, ldm, Y, ldy));
+    BQ_TRY(trsm_ru(c, rows, k, colmajor(Rsk, ldr), Yv, false));                       // Pre = M Rsk11^-1
+    BQ_TRY(dgemm(c, true, false, k, k, rows, 1.0, Y, ldy, Y, ldy, 0.0, G, ldb));       // G = Pre^T Pre
+    BQ_CUDA(cudaMemsetAsync(&c.st->potrf_info, 0x7f, sizeof(int), c.stream));         // "no failure"
+    BQ_TRY(potrf_u(c, k, G, ldb));                                                     // Rchol
+    DevStatus hs{};
+    BQ_TRY(read_status(c, &hs));
+    if (hs.potrf_info < k) {
+        k = hs.potrf_info;   // Cholesky breakdown: the block's numerical rank is lower
+        *kio = k;
+        if (k <= 0) return 0;
+    }
+    BQ_TRY(trsm_ru(c, rows, k, colmajor(G, ldb), Yv, false));                         // Qc = Pre Rchol^-1
+    BQ_TRY(modlu(c, rows, k, Y, ldy, D));                                              // Qc - [S;0] = Y U
+    recon_split_kernel<<<gblocks(c, k * k), 256, 0, c.stream>>>(k, Y, ldy, D, U, Tb, ldb);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(trsm_ru(c, k, k, Yv.t(), colmajor(Tb, ldb), true));                        // T = -U S Y1^-T
+    BQ_TRY(dgemm(c, false, false, k, w, k, 1.0, G, ldb, Rsk, ldr, 0.0, R11, ldb));     // Rchol Rsk(0:k, 0:w)
+    panel_writeback_kernel<<<gblocks(c, rows * w), 256, 0, c.stream>>>(rows, w, k, Mp, ldm, Y, ldy, R11, D, Tb, ldb,
+                                                                       tau);
+    BQ_LAUNCH_CHECK();
+    *kio = k;
+    return 0;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ the factorization
+int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i64* jpvt, double* tau, i64* rank,
+                const bqrrp_opts& o, const Bufs& B, Ctx& c) {
+    DevStatus hs{};
+    init_status_kernel<<<1, 1, 0, c.stream>>>(B.st);
+    BQ_LAUNCH_CHECK();
+    // NaN/Inf in A -> BQRRP_ENUMERIC before anything is written
+    BQ_TRY(any_nonfinite(c, m, n, A, lda, &B.st->a_nonfinite));
+    BQ_TRY(read_status(c, &hs));
+    if (hs.a_nonfinite) {
+        set_error("A contains NaN or Inf");
+        return BQRRP_ENUMERIC;
+    }
+    BQ_CUDA(cudaMemsetAsync(tau, 0, sizeof(double) * (size_t)n, c.stream));
+    iota_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c.stream>>>(n, B.J);
+    BQ_LAUNCH_CHECK();
+
+    // Alg. 1: sketch Msk = S * A (d x n)
+    if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
+        BQ_TRY(sketch_dense_gemm(c, d, m, n, seed, A, lda, B.Msk, d));
+    } else {
+        BQ_TRY(sketch_sparse_apply(c, d, m, n, seed, o.sketch_nnz, A, lda, B.Msk, d, B.sparse_ws, B.sparse_bytes));
+    }
+
+    i64 ell = 0;
+    for (i64 it = 0;; ++it) {
+        const i64 s = it * b;
+        const i64 cend = imin(n, s + b);
+        const i64 w = cend - s;
+        const i64 N = n - s;
+        const i64 rows = m - s;
+        double* Ssk = B.Msk + s * d;
+        View Sv = colmajor(Ssk, d);
+
+        // ---- Alg. 2 on the sketch
+        BQ_CUDA(cudaMemsetAsync(&B.st->sk_nonfinite, 0, sizeof(int), c.stream));
+        BQ_CUDA(cudaMemsetAsync(&B.st->zero_col, 0, sizeof(int), c.stream));
+        BQ_TRY(any_nonfinite(c, d, N, Ssk, d, &B.st->sk_nonfinite));
+        BQ_CUDA(cudaMemcpy2DAsync(B.Xlu, sizeof(double) * d, Ssk, sizeof(double) * d, sizeof(double) * d, N,
+                                  cudaMemcpyDeviceToDevice, c.stream));
+        const i64 steps = imin(N, d);
+        BQ_TRY(getrf_pivots(c, N, d, B.Xlu, d, B.ipiv));
+        BQ_TRY(piv_transform_moved(c, N, steps, B.ipiv, B.Jsk, &B.st->sk_nonfinite, B.pos, B.src, B.cnt));
+        const i64 mm = imin(N, 2 * steps);
+        BQ_TRY(gather_cols(c, d, Ssk, d, B.pos, B.src, B.cnt, mm, B.stage, d));
+        BQ_TRY(geqrf_blocked(c, d, N, Ssk, d, B.sktau, B.Vqr, B.Tqr, B.W, B.W2, 64));
+        BQ_TRY(set_zero_below(c, d, N, Ssk, d));
+        tri_rank_kernel<<<1, 32, 0, c.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
+        BQ_LAUNCH_CHECK();
+
+        // ---- permute A(:, s:) (all m rows: R rows and working rows, merged) and J(s:)
+        BQ_TRY(gather_cols(c, m, A + s * lda, lda, B.pos, B.src, B.cnt, mm, B.stage, B.ldst));
+        BQ_TRY(gather_idx(c, B.J + s, B.pos, B.src, B.cnt, mm, B.Jstage));
+        col_nonzero_kernel<<<gblocks(c, rows), 256, 0, c.stream>>>(rows, A + s + s * lda, &B.st->zero_col);
+        BQ_LAUNCH_CHECK();
+        BQ_TRY(read_status(c, &hs));
+        if (!hs.zero_col) { ell = s; break; }   // first permuted working column is zero
+        i64 k = hs.k;
+        if (k <= 0) { ell = s; break; }
+
+        double* Ap = A + s + s * lda;   // panel / working block origin
+        const i64 nc = n - cend;
+        if (o.panel_kind == BQRRP_PANEL_HQR) {
+            // Householder QR of all w panel columns, reflectors applied to the
+            // whole trailing block; only the first k are kept (Sec. 4.5).
+            BQ_TRY(geqrf_blocked(c, rows, N, Ap, lda, tau + s, B.Vqr, B.Tqr, B.W, B.W2, 64, w));
+            if (k < w) {
+                zero_tail_kernel<<<(unsigned)cdiv(w, 256), 256, 0, c.stream>>>(s + k, s + w, tau);
+                BQ_LAUNCH_CHECK();
+            }
+        } else {
+            // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
+            BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
+                                      tau + s));
+            if (k <= 0) { ell = s; break; }
+            // ---- trailing update with the block reflector (I - Y T Y^T)^T
+            if (nc > 0) {
+                double* C = A + s + cend * lda;
+                const i64 keep = (k == w) ? rows : k;
+                BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
+                BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
+                BQ_TRY(dgemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+            }
+        }
+        if (cend == n || k < w) { ell = s + k; break; }
+
+        // ---- sketch update: Msk(0:w, c:) = Rsk12 - (Rsk11 R11^-1) R12; Rsk22 stays
+        BQ_TRY(copy_triu(c, w, w, Ssk, d, B.Z, B.bb));
+        BQ_TRY(trsm_ru(c, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
+        BQ_TRY(dgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
+    }
+    plus_one_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c.stream>>>(n, B.J, jpvt);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(read_status(c, &hs));
+    *rank = ell;
+    return 0;
+}
+
+int make_ctx(void* stream, Ctx* c) {
+    BQ_TRY(current_device(&c->dev));
+    c->stream = (cudaStream_t)stream;
+    return 0;
+}
+
+}  // namespace
+}  // namespace bq
+
+using namespace bq;
+
+extern "C" {
+
+const char* bqrrp_last_error(void) { return get_error(); }
+
+const char* bqrrp_version(void) { return "bqrrp-b300 0.1 (sm_103a, FP64 SIMT)"; }
+
+size_t bqrrp_workspace_query(int64_t m, int64_t n, int64_t b, int64_t d, const bqrrp_opts* opts) {
+    if (m < 0 || n < 0 || m < n || b < 1 || d < b || check_opts(opts, d)) return 0;
+    bqrrp_opts o = defaults(opts);
+    Arena ar;
+    ar.dry = true;
+    Bufs B{};
+    carve(ar, m, imax(n, 1), b, d, o, &B);
+    return ar.off + 256;
+}
+
+int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_t d, uint64_t seed, int64_t* jpvt,
+                 double* tau, int64_t* rank, const bqrrp_opts* opts, void* workspace, size_t workspace_bytes,
+                 void* stream) {
+    set_error("");
+    if (rank) *rank = -1;
+    if (m < 0 || m < n) { set_error("m must satisfy m >= n >= 0"); return -1; }
+    if (n < 0) return -2;
+    if (lda < imax(1, m)) { set_error("lda < max(1, m)"); return -4; }
+    if (b < 1) { set_error("b < 1"); return -5; }
+    if (d < b) { set_error("d < b"); return -6; }
+    if (!rank) return -10;
+    if (check_opts(opts, d)) { set_error("invalid opts"); return -11; }
+    if (n == 0) { *rank = 0; return 0; }
+    if (!A) return -3;
+    if (!jpvt) return -8;
+    if (!tau) return -9;
+    if (!workspace) return -12;
+    const size_t need = bqrrp_workspace_query(m, n, b, d, opts);
+    if (workspace_bytes < need) {
+        set_error("workspace has %zu bytes, needs %zu", workspace_bytes, need);
+        return BQRRP_ENOMEM;
+    }
+    bqrrp_opts o = defaults(opts);
+    Arena ar;
+    ar.base = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    ar.cap = workspace_bytes - (size_t)(ar.base - (char*)workspace);
+    Bufs B{};
+    carve(ar, m, n, b, d, o, &B);
+    if (!ar.ok()) { set_error("workspace too small after alignment"); return BQRRP_ENOMEM; }
+    Ctx c{};
+    BQ_TRY(make_ctx(stream, &c));
+    c.st = B.st;
+    c.splitk = B.splitk;
+    c.splitk_elems = B.splitk_elems;
+    c.coop = B.coop;
+    c.coop_elems = B.coop_elems;
+    i64 r = 0;
+    const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c);
+    if (rc == 0) *rank = r;
+    return rc;
+}
+
+size_t bqrrp_workspace_query_host(int64_t m, int64_t n, int64_t b, int64_t d, const bqrrp_opts* opts) {
+    const size_t base = bqrrp_workspace_query(m, n, b, d, opts);
+    if (!base) return 0;
+    const size_t am = ((size_t)m * (size_t)n * 8 + 255) & ~(size_t)255;
+    const size_t jv = ((size_t)n * 8 + 255) & ~(size_t)255;
+    return base + am + 2 * jv + 512;
+}
+
+int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t b, int64_t d, uint64_t seed,
+                      int64_t* jpvt_host, double* tau_host, int64_t* rank, const bqrrp_opts* opts, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    set_error("");
+    if (rank) *rank = -1;
+    if (m < 0 || m < n) return -1;
+    if (n < 0) return -2;
+    if (lda < imax(1, m)) return -4;
+    if (!rank) return -10;
+    if (n == 0) { *rank = 0; return 0; }
+    if (!A_host) return -3;
+    if (!jpvt_host) return -8;
+    if (!tau_host) return -9;
+    if (!workspace) return -12;
+    const size_t need = bqrrp_workspace_query_host(m, n, b, d, opts);
+    if (!need) { set_error("invalid arguments"); return b < 1 ? -5 : (d < b ? -6 : -11); }
+    if (workspace_bytes < need) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    double* dA = (double*)base;
+    const size_t am = ((size_t)m * (size_t)n * 8 + 255) & ~(size_t)255;
+    const size_t jv = ((size_t)n * 8 + 255) & ~(size_t)255;
+    int64_t* dj = (int64_t*)(base + am);
+    double* dt = (double*)(base + am + jv);
+    char* rest = base + am + 2 * jv;
+    const size_t rest_bytes = workspace_bytes - (size_t)(rest - (char*)workspace);
+    BQ_CUDA(cudaMemcpy2DAsync(dA, sizeof(double) * m, A_host, sizeof(double) * lda, sizeof(double) * m, n,
+                              cudaMemcpyHostToDevice, st));
+    int rc = bqrrp_factor(m, n, dA, m, b, d, seed, dj, dt, rank, opts, rest, rest_bytes, stream);
+    if (rc != 0) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    BQ_CUDA(cudaMemcpy2DAsync(A_host, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+                              cudaMemcpyDeviceToHost, st));
+    BQ_CUDA(cudaMemcpyAsync(jpvt_host, dj, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
+    BQ_CUDA(cudaMemcpyAsync(tau_host, dt, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    BQ_CUDA(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int bqrrp_sketch_operator(int64_t d, int64_t m, uint64_t seed, int kind, int64_t nnz, double* S, int64_t lds,
+                          void* stream) {
+    set_error("");
+    if (d < 0) return -1;
+    if (m < 0) return -2;
+    if (kind != BQRRP_SKETCH_DENSE && kind != BQRRP_SKETCH_SPARSE) return -4;
+    if (kind == BQRRP_SKETCH_SPARSE && (nnz < 1 || nnz > d || nnz > 64)) return -5;
+    if (d * m > 0 && !S) return -6;
+    if (lds < imax(1, d)) return -7;
+    Ctx c{};
+    BQ_TRY(make_ctx(stream, &c));
+    c.st = nullptr;
+    return sketch_write(c, d, m, seed, kind, nnz, S, lds);
+}
+
+size_t bqrrp_sketch_apply_workspace(int64_t d, int64_t m, int kind, int64_t nnz) {
+    if (kind == BQRRP_SKETCH_SPARSE) return sketch_sparse_ws(d, m, nnz) + 256;
+    return 0;
+}
+
+int bqrrp_sketch_apply(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda, uint64_t seed, int kind,
+                       int64_t nnz, double* Msk, int64_t ldsk, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+    set_error("");
+    if (d < 0) return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (lda < imax(1, m)) return -5;
+    if (kind != BQRRP_SKETCH_DENSE && kind != BQRRP_SKETCH_SPARSE) return -7;
+    if (kind == BQRRP_SKETCH_SPARSE && (nnz < 1 || nnz > d || nnz > 64)) return -8;
+    if (ldsk < imax(1, d)) return -10;
+    Ctx c{};
+    BQ_TRY(make_ctx(stream, &c));
+    if (kind == BQRRP_SKETCH_DENSE) return sketch_dense_gemm(c, d, m, n, seed, A, lda, Msk, ldsk);
+    if (workspace_bytes < sketch_sparse_ws(d, m, nnz)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    return sketch_sparse_apply(c, d, m, n, seed, nnz, A, lda, Msk, ldsk, workspace, workspace_bytes);
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+// dense.cu -- blocked FP64 triangular kernels built on the SIMT GEMM.
+//
+// Every O(b^3) step of the panel (Alg. 3) is cast as a right-looking blocked
+// algorithm: a 64-wide diagonal block handled by one CTA in shared memory (or,
+// for triangular solves, one thread per matrix row with the block in shared
+// memory) plus GEMM updates that spread over all SMs.  With B300's slow FP64
+// pipe a single SM runs at ~8 GFLOP/s, so nothing of size b^3 may stay on one
+// SM.
+#include <climits>
+
+#include "common.cuh"
+
+namespace bq {
+
+namespace {
+
+constexpr int NBD = 64;   // diagonal block size
+
+// X <- X * R^{-1} for the nb (<= 64) columns of X; R upper (unit diagonal if
+// unit != 0; then only the strictly upper part of R is read).  One thread per
+// row of X, the triangle of R in shared memory.
+template <int NB>
+__global__ void __launch_bounds__(128) trsm_small_kernel(i64 rows, int nb, View R, View X, int unit) {
+    __shared__ double Rs[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int t = e % NB, j = e / NB;
+        double v = 0.0;
+        if (t < nb && j < nb && t <= j) v = (t == j && unit) ? 1.0 : *R.at(t, j);
+        Rs[t][j] = v;
+    }
+    __syncthreads();
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = (j < nb) ? *X.at(i, j) : 0.0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nb) {
+            double s = x[j];
+#pragma unroll
+            for (int t = 0; t < j; ++t) s = fma(-x[t], Rs[t][j], s);
+            x[j] = unit ? s : s / Rs[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < nb) *X.at(i, j) = x[j];
+}
+
+// Upper Cholesky of one nb x nb diagonal block in place (G = R^T R), reading
+// and writing only the upper triangle; zeroes the strict lower triangle.  A
+// non-positive or non-finite pivot at local column j records jg0 + j in
+// st->potrf_info (atomicMin) and stops.
+__global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* G, i64 ldg, int jg0, DevStatus* st) {
+    __shared__ double A[NBD][NBD + 1];
+    __shared__ int fail;
+    for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
+        const int i = e % NBD, j = e / NBD;
+        A[i][j] = (i < nb && j < nb && i <= j) ? G[i + (i64)j * ldg] : 0.0;
+    }
+    if (threadIdx.x == 0) fail = (st->potrf_info < jg0) ? 1 : 0;   // an earlier block failed
+    __syncthreads();
+    if (fail) return;
+    int done = nb;
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double dj = A[j][j];
+            if (!(dj > 0.0) || !isfinite(dj)) {
+                fail = 1;
+                atomicMin(&st->potrf_info, jg0 + j);
+            } else {
+                A[j][j] = sqrt(dj);
+            }
+        }
+        __syncthreads();
+        if (fail) { done = j; break; }
+        const double rjj = A[j][j];
+        for (int c = j + 1 + threadIdx.x; c < nb; c += blockDim.x) A[j][c] /= rjj;
+        __syncthreads();
+        const int w = nb - j - 1;
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int c1 = j + 1 + e % w, c2 = j + 1 + e / w;
+            if (c1 <= c2) A[c1][c2] = fma(-A[j][c1], A[j][c2], A[c1][c2]);
+        }
+        __syncthreads();
+    }
+    (void)done;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        G[i + (i64)j * ldg] = (i <= j) ? A[i][j] : 0.0;
+    }
+}
+
+// Modified LU (Householder reconstruction, BD2015 Alg. 5 as cited in Sec. 2.3)
+// of one nb x nb diagonal block in place: for each column j the sign
+// s_j = -sign(a_jj) (sign(0) = +1) is recorded in D[j], a_jj -= s_j, then the
+// column below is divided by the new a_jj and the block's trailing part gets
+// the rank-1 update.  No pivoting.
+__global__ void __launch_bounds__(256) modlu_small_kernel(int nb, double* Y, i64 ldy, double* D) {
+    __shared__ double A[NBD][NBD + 1];
+    for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
+        const int i = e % NBD, j = e / NBD;
+        A[i][j] = (i < nb && j < nb) ? Y[i + (i64)j * ldy] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double a = A[j][j];
+            const double s = (a >= 0.0) ? -1.0 : 1.0;
+            D[j] = s;
+            A[j][j] = a - s;
+        }
+        __syncthreads();
+        const double piv = A[j][j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] /= piv;
+        __syncthreads();
+        const int w = nb - j - 1;
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int i = j + 1 + e % w, c = j + 1 + e / w;
+            A[i][c] = fma(-A[i][j], A[j][c], A[i][c]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        Y[i + (i64)j * ldy] = A[i][j];
+    }
+}
+
+__global__ void copy_kernel(i64 rows, i64 cols, const double* __restrict__ s, i64 lds, double* __restrict__ d,
+                            i64 ldd, int triu) {
+    const i64 total = rows * cols;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % rows, j = e / rows;
+        d[i + j * ldd] = (triu && i > j) ? 0.0 : s[i + j * lds];
+    }
+}
+
+__global__ void zero_below_kernel(i64 rows, i64 cols, double* A, i64 lda) {
+    const i64 total = rows * cols;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % rows, j = e / rows;
+        if (i > j) A[i + j * lda] = 0.0;
+    }
+}
+
+__global__ void nonfinite_kernel(i64 rows, i64 cols, const double* __restrict__ A, i64 lda, int* flag) {
+    const i64 total = rows * cols;
+    int bad = 0;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % rows, j = e / rows;
+        if (!isfinite(A[i + j * lda])) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+inline int grid_for(const Ctx& c, i64 total) {
+    return (int)imax(1, imin(cdiv(total, 256), 16LL * c.dev.sms));
+}
+
+}  // namespace
+
+int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit) {
+    if (rows <= 0 || k <= 0) return 0;
+    for (i64 jb = 0; jb < k; jb += NBD) {
+        const int nb = (int)imin(NBD, k - jb);
+        const int blocks = (int)cdiv(rows, 128);
+        trsm_small_kernel<NBD><<<blocks, 128, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb), unit ? 1 : 0);
+        BQ_LAUNCH_CHECK();
+        if (jb + nb < k) {
+            // X(:, jb+nb:k) -= X(:, jb:jb+nb) * R(jb:jb+nb, jb+nb:k)
+            BQ_TRY(gemm_view(c, rows, k - jb - nb, nb, -1.0, X.sub(0, jb), R.sub(jb, jb + nb), 1.0,
+                             X.sub(0, jb + nb)));
+        }
+    }
+    return 0;
+}
+
+int potrf_u(const Ctx& c, i64 k, double* G, i64 ldg) {
+    View Gv = colmajor(G, ldg);
+    for (i64 jb = 0; jb < k; jb += NBD) {
+        const int nb = (int)imin(NBD, k - jb);
+        potrf_small_kernel<<<1, 256, 0, c.stream>>>(nb, G + jb + jb * ldg, ldg, (int)jb, c.st);
+        BQ_LAUNCH_CHECK();
+        const i64 rest = k - jb - nb;
+        if (rest > 0) {
+            // R12 = R11^{-T} G12  <=>  R12^T = G12^T R11^{-1}
+            BQ_TRY(trsm_ru(c, rest, nb, Gv.sub(jb, jb), Gv.sub(jb, jb + nb).t(), false));
+            // G22 -= R12^T R12
+            BQ_TRY(dgemm(c, true, false, rest, rest, nb, -1.0, G + jb + (jb + nb) * ldg, ldg,
+                         G + jb + (jb + nb) * ldg, ldg, 1.0, G + (jb + nb) + (jb + nb) * ldg, ldg));
+        }
+    }
+    return set_zero_below(c, k, k, G, ldg);
+}
+
+int modlu(const Ctx& c, i64 rows, i64 k, double* Y, i64 ldy, double* D) {
+    View Yv = colmajor(Y, ldy);
+    for (i64 jb = 0; jb < k; jb += NBD) {
+        const int nb = (int)imin(NBD, k - jb);
+        modlu_small_kernel<<<1, 256, 0, c.stream>>>(nb, Y + jb + jb * ldy, ldy, D + jb);
+        BQ_LAUNCH_CHECK();
+        const i64 below = rows - jb - nb;
+        if (below > 0)   // L21 = A21 U11^{-1}
+            BQ_TRY(trsm_ru(c, below, nb, Yv.sub(jb, jb), Yv.sub(jb + nb, jb), false));
+        const i64 right = k - jb - nb;
+        if (right > 0) {
+            // U12 = L11^{-1} A12  <=>  U12^T = A12^T L11^{-T}, L11^T unit upper
+            BQ_TRY(trsm_ru(c, right, nb, Yv.sub(jb, jb).t(), Yv.sub(jb, jb + nb).t(), true));
+            if (below > 0)   // A22 -= L21 U12
+                BQ_TRY(dgemm(c, false, false, below, right, nb, -1.0, Y + (jb + nb) + jb * ldy, ldy,
+                             Y + jb + (jb + nb) * ldy, ldy, 1.0, Y + (jb + nb) + (jb + nb) * ldy, ldy));
+        }
+    }
+    return 0;
+}
+
+int copy_mat(const Ctx& c, i64 rows, i64 cols, const double* src, i64 lds, double* dst, i64 ldd) {
+    if (rows <= 0 || cols <= 0) return 0;
+    copy_kernel<<<grid_for(c, rows * cols), 256, 0, c.stream>>>(rows, cols, src, lds, dst, ldd, 0);
+    BQ_LAUNCH_CHECK();
+    return 0;
+}
+
+int copy_triu(const Ctx& c, i64 rows, i64 cols, const double* src, i64 lds, double* dst, i64 ldd) {
+    if (rows <= 0 || cols <= 0) return 0;
+    copy_kernel<<<grid_for(c, rows * cols), 256, 0, c.stream>>>(rows, cols, src, lds, dst, ldd, 1);
+    BQ_LAUNCH_CHECK();
+    return 0;
+}
+
+int set_zero_below(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda) {
+    if (rows <= 1 || cols <= 0) return 0;
+    zero_below_kernel<<<grid_for(c, rows * cols), 256, 0, c.stream>>>(rows, cols, A, lda);
+    BQ_LAUNCH_CHECK();
+    return 0;
+}
+
+int any_nonfinite(const Ctx& c, i64 rows, i64 cols, const double* A, i64 lda, int* flag) {
+    if (rows <= 0 || cols <= 0) return 0;
+    nonfinite_kernel<<<grid_for(c, rows * cols), 256, 0, c.stream>>>(rows, cols, A, lda, flag);
+    BQ_LAUNCH_CHECK();
+    return 0;
+}
+
+}  // namespace bq

@@ -1,0 +1,518 @@
+// panels.cu -- cooperative (grid-wide) panel kernels and the blocked LU / QR
+// drivers built on them.
+//
+//  * lu_panel_kernel: one nb-wide panel of the row-pivoted LU that Alg. 2
+//    runs on the transposed sketch.  X = Sk^T is never formed: a row of X is a
+//    column of the sketch buffer Sk (d x N, column-major), so each CTA keeps a
+//    contiguous slab of X rows (= sketch columns) of the panel in shared memory
+//    and one grid barrier per pivot step exchanges the per-CTA argmax
+//    candidates (first maximum, as GETRF/IDAMAX).
+//  * hh_panel_kernel: Householder QR (dlarfg convention) of a tall panel,
+//    rows split across CTAs, two grid barriers per column (norm, then the
+//    reflector's dot products), then the compact-WY factor T of the panel
+//    (LAPACK larft recurrence from V^T V).
+//
+// Both are launched cooperatively so that all CTAs are co-resident; every
+// barrier wait is bounded (see grid_barrier).
+#include <cooperative_groups.h>
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace bq {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int kMaxSmemLu = 210 * 1024;   // dynamic part; static use is ~2 KB
+constexpr int kMaxSmemHh = 185 * 1024;   // dynamic part; static use is ~35 KB
+
+struct Best {
+    double v;
+    i64 t;
+};
+
+__device__ inline Best better(Best a, Best b) {
+    if (b.v > a.v) return b;
+    if (b.v == a.v && b.t < a.t && b.t >= 0) return b;
+    if (a.t < 0) return b;
+    return a;
+}
+
+__device__ Best block_best(Best x) {
+    __shared__ double sv[NT / 32];
+    __shared__ long long st[NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best y;
+        y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+        y.t = __shfl_down_sync(0xffffffffu, x.t, o);
+        x = better(x, y);
+    }
+    if (lane == 0) { sv[w] = x.v; st[w] = x.t; }
+    __syncthreads();
+    if (w == 0) {
+        x.v = lane < NT / 32 ? sv[lane] : -1.0;
+        x.t = lane < NT / 32 ? st[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Best y;
+            y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+            y.t = __shfl_down_sync(0xffffffffu, x.t, o);
+            x = better(x, y);
+        }
+        if (lane == 0) { sv[0] = x.v; st[0] = x.t; }
+    }
+    __syncthreads();
+    Best r{sv[0], st[0]};
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// LU panel.  X(t, c) = Sk[c + t*ldsk]; panel = X rows [jb, N), columns
+// [jb, jb+pw); steps pivot steps.  CTA g owns rows [jb + g*R, jb + (g+1)*R).
+struct LuArgs {
+    i64 N, jb, ldsk;
+    int pw, steps, R, Rp;
+    double* Sk;
+    i64* ipiv;
+    DevStatus* st;
+    double* cand_v;    // [2][G]
+    double* cand_t;    // [2][G]
+    double* cand_row;  // [2][G][pw]
+    double* cur_row;   // [2][pw]
+};
+
+__global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
+    extern __shared__ double slab[];          // [pw][Rp]
+    __shared__ double prow[64], crow[64];
+    __shared__ long long s_p;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const i64 t0 = a.jb + (i64)g * a.R;
+    const i64 t1 = (t0 + a.R < a.N) ? t0 + a.R : a.N;
+    const int nloc = t1 > t0 ? (int)(t1 - t0) : 0;
+    const int pw = a.pw;
+
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int c = e % pw, rl = e / pw;
+        slab[c * a.Rp + rl] = a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
+    }
+    __syncthreads();
+
+    for (int j = 0; j < a.steps; ++j) {
+        const i64 jg = a.jb + j;
+        const int par = j & 1;
+        // (1) local first-maximum of |X(t, jg)| over owned rows t >= jg
+        Best b{-1.0, -1};
+        const int rl0 = (jg > t0) ? (int)(jg - t0) : 0;
+        for (int rl = rl0 + tid; rl < nloc; rl += NT) {
+            const double v = fabs(slab[j * a.Rp + rl]);
+            if (v > b.v) { b.v = v; b.t = t0 + rl; }
+        }
+        b = block_best(b);
+        // (2) publish candidate, its row, and (owner) the current row jg
+        if (tid == 0) {
+            a.cand_v[par * G + g] = b.v;
+            a.cand_t[par * G + g] = (double)b.t;
+        }
+        if (b.t >= 0)
+            for (int c = tid; c < pw; c += NT) a.cand_row[((size_t)par * G + g) * pw + c] = slab[c * a.Rp + (b.t - t0)];
+        if (jg >= t0 && jg < t1)
+            for (int c = tid; c < pw; c += NT) a.cur_row[par * pw + c] = slab[c * a.Rp + (jg - t0)];
+        // (3)
+        if (!grid_barrier(a.st, G)) return;
+        // (4) winner over all CTAs (fixed rule: largest value, then smallest index)
+        Best w{-1.0, -1};
+        for (int q = tid; q < G; q += NT) {
+            Best y{__ldcg(&a.cand_v[par * G + q]), (i64)__ldcg(&a.cand_t[par * G + q])};
+            if (y.t >= 0) w = better(w, y);
+        }
+        w = block_best(w);
+        if (tid == 0) s_p = w.t;
+        __syncthreads();
+        const i64 p = s_p;
+        // locate the winning CTA from the row index
+        const int gw = (int)((p - a.jb) / a.R);
+        // (5)
+        for (int c = tid; c < pw; c += NT) {
+            prow[c] = __ldcg(&a.cand_row[((size_t)par * G + gw) * pw + c]);
+            crow[c] = __ldcg(&a.cur_row[par * pw + c]);
+        }
+        __syncthreads();
+        // (6) row interchange jg <-> p
+        if (jg >= t0 && jg < t1)
+            for (int c = tid; c < pw; c += NT) slab[c * a.Rp + (jg - t0)] = prow[c];
+        if (p != jg && p >= t0 && p < t1)
+            for (int c = tid; c < pw; c += NT) slab[c * a.Rp + (p - t0)] = crow[c];
+        __syncthreads();
+        // (7) elimination below the pivot (skipped on an exact zero pivot, as GETRF)
+        const double piv = prow[j];
+        if (piv != 0.0) {
+            const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
+            for (int rl = r0 + tid; rl < nloc; rl += NT) {
+                const double l = slab[j * a.Rp + rl] / piv;
+                slab[j * a.Rp + rl] = l;
+                for (int c = j + 1; c < pw; ++c) slab[c * a.Rp + rl] = fma(-l, prow[c], slab[c * a.Rp + rl]);
+            }
+        }
+        if (g == 0 && tid == 0) a.ipiv[jg] = p;
+        __syncthreads();
+    }
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int c = e % pw, rl = e / pw;
+        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * a.Rp + rl];
+    }
+}
+
+// Apply the panel's interchanges to sketch rows [r0, d): swap columns jb+j and
+// ipiv[jb+j] in order.  One thread per row.
+__global__ void lu_swap_rows_kernel(i64 r0, i64 d, i64 jb, int steps, const i64* __restrict__ ipiv, double* Sk,
+                                    i64 ldsk) {
+    const i64 r = r0 + (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    for (int j = 0; j < steps; ++j) {
+        const i64 a = jb + j, p = ipiv[jb + j];
+        if (p != a) {
+            double* x = Sk + r + a * ldsk;
+            double* y = Sk + r + p * ldsk;
+            const double t = *x;
+            *x = *y;
+            *y = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder panel: rows x pw panel A (ld lda).
+struct HhArgs {
+    i64 rows, lda, ldv, ldt;
+    int pw, R, Rp;
+    double* A;
+    double* tau;
+    double* V;
+    double* T;
+    DevStatus* st;
+    double* part1;   // [G]
+    double* alpha;   // [1]
+    double* part2;   // [G][pw]
+    double* gpart;   // [G][pw*pw]
+    double* gsum;    // [pw*pw]
+};
+
+__global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
+    extern __shared__ double slab[];   // [pw][Rp]
+    __shared__ double red[NT / 32];
+    __shared__ double wv[64];
+    __shared__ double s_tau, s_beta, s_scal;
+    __shared__ double Ts[64][65];
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const i64 r0 = (i64)g * a.R;
+    const i64 r1 = (r0 + a.R < a.rows) ? r0 + a.R : a.rows;
+    const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
+    const int pw = a.pw;
+
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int rl = e % nloc, c = e / nloc;
+        slab[c * a.Rp + rl] = a.A[(r0 + rl) + c * a.lda];
+    }
+    __syncthreads();
+
+    const int jmax = (a.rows < pw) ? (int)a.rows : pw;
+    for (int j = 0; j < jmax; ++j) {
+        // (1) partial sum of squares below the diagonal; owner publishes alpha
+        double s = 0.0;
+        const int rb = (j + 1 > r0) ? (int)(j + 1 - r0) : 0;
+        for (int rl = rb + tid; rl < nloc; rl += NT) {
+            const double x = slab[j * a.Rp + rl];
+            s = fma(x, x, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NT / 32; ++q) t += red[q];
+            a.part1[g] = t;
+            if (j >= r0 && j < r1) *a.alpha = slab[j * a.Rp + (j - r0)];
+        }
+        if (!grid_barrier(a.st, G)) return;
+        // (3) reflector (every CTA computes the same numbers in the same order)
+        if (warp == 0) {
+            double xs = 0.0;
+            for (int q = lane; q < G; q += 32) xs += __ldcg(&a.part1[q]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) xs += __shfl_down_sync(0xffffffffu, xs, o);
+            if (lane == 0) red[0] = xs;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double xn2 = red[0];
+            const double al = __ldcg(a.alpha);
+            if (xn2 == 0.0) {
+                s_tau = 0.0; s_beta = al; s_scal = 1.0;
+            } else {
+                const double nrm = sqrt(fma(al, al, xn2));
+                const double be = (al >= 0.0) ? -nrm : nrm;
+                s_tau = (be - al) / be;
+                s_beta = be;
+                s_scal = 1.0 / (al - be);
+            }
+            if (g == 0) a.tau[j] = s_tau;
+        }
+        __syncthreads();
+        const double tau = s_tau;
+        if (tau != 0.0) {
+            const double scal = s_scal;
+            for (int rl = rb + tid; rl < nloc; rl += NT) slab[j * a.Rp + rl] *= scal;
+            if (tid == 0 && j >= r0 && j < r1) slab[j * a.Rp + (j - r0)] = s_beta;
+        }
+        __syncthreads();
+        if (tau == 0.0 || j + 1 >= pw) continue;   // uniform across CTAs: no barrier skipped unevenly
+        // (5) partial dots w_c = v^T A(:, c), c > j, v_j = 1
+        const int rv = (j > r0) ? (int)(j - r0) : 0;
+        for (int c = j + 1 + warp; c < pw; c += NT / 32) {
+            double acc = 0.0;
+            for (int rl = rv + lane; rl < nloc; rl += 32) {
+                const i64 r = r0 + rl;
+                const double v = (r == j) ? 1.0 : slab[j * a.Rp + rl];
+                acc = fma(v, slab[c * a.Rp + rl], acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) a.part2[(size_t)g * pw + c] = acc;
+        }
+        if (!grid_barrier(a.st, G)) return;
+        // (7) reduce partial dots in a fixed order, then update owned rows
+        for (int c = j + 1 + warp; c < pw; c += NT / 32) {
+            double acc = 0.0;
+            for (int q = lane; q < G; q += 32) acc += __ldcg(&a.part2[(size_t)q * pw + c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) wv[c] = acc * tau;
+        }
+        __syncthreads();
+        for (int e = tid; e < (pw - j - 1) * (nloc - rv > 0 ? nloc - rv : 0); e += NT) {
+            const int span = nloc - rv;
+            const int rl = rv + e % span, c = j + 1 + e / span;
+            const i64 r = r0 + rl;
+            const double v = (r == j) ? 1.0 : slab[j * a.Rp + rl];
+            slab[c * a.Rp + rl] = fma(-wv[c], v, slab[c * a.Rp + rl]);
+        }
+        __syncthreads();
+    }
+    if (g == 0)
+        for (int j = jmax + tid; j < pw; j += NT) a.tau[j] = 0.0;
+
+    // write the panel back (R above, v below) and V explicitly
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int rl = e % nloc, c = e / nloc;
+        const i64 r = r0 + rl;
+        const double x = slab[c * a.Rp + rl];
+        a.A[r + c * a.lda] = x;
+        a.V[r + c * a.ldv] = (c >= jmax) ? 0.0 : (r > c ? x : (r == c ? 1.0 : 0.0));
+    }
+    // partial Gram V^T V (upper triangle) over owned rows
+    for (int e = tid; e < pw * pw; e += NT) {
+        const int i = e % pw, j = e / pw;
+        double acc = 0.0;
+        if (i <= j && j < jmax) {
+            const int rs = (j > r0) ? (int)(j - r0) : 0;   // V(r, j) = 0 for r < j
+            for (int rl = rs; rl < nloc; ++rl) {
+                const i64 r = r0 + rl;
+                const double vi = (r > i) ? slab[i * a.Rp + rl] : (r == i ? 1.0 : 0.0);
+                const double vj = (r > j) ? slab[j * a.Rp + rl] : (r == j ? 1.0 : 0.0);
+                acc = fma(vi, vj, acc);
+            }
+        }
+        a.gpart[(size_t)g * pw * pw + e] = acc;
+    }
+    if (!grid_barrier(a.st, G)) return;
+    // distributed fixed-order reduction of the Gram partials
+    for (int e = g * NT + tid; e < pw * pw; e += G * NT) {
+        double acc = 0.0;
+#pragma unroll 8
+        for (int q = 0; q < G; ++q) acc += __ldcg(&a.gpart[(size_t)q * pw * pw + e]);
+        a.gsum[e] = acc;
+    }
+    if (!grid_barrier(a.st, G)) return;
+    if (g != 0) return;
+    // T by the larft recurrence: T(j,j) = tau_j, T(0:j,j) = -tau_j T(0:j,0:j) G(0:j,j)
+    for (int e = tid; e < 64 * 65; e += NT) (&Ts[0][0])[e] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < pw; ++j) {
+        const double tj = (j < jmax) ? __ldcg(&a.tau[j]) : 0.0;
+        for (int i = tid; i < j; i += NT) {
+            double z = 0.0;
+            for (int l = i; l < j; ++l) z = fma(Ts[i][l], __ldcg(&a.gsum[l + j * pw]), z);
+            Ts[i][j] = -tj * z;
+        }
+        if (tid == 0) Ts[j][j] = tj;
+        __syncthreads();
+    }
+    for (int e = tid; e < pw * pw; e += NT) {
+        const int i = e % pw, j = e / pw;
+        a.T[i + j * a.ldt] = Ts[i][j];
+    }
+}
+
+int coop_grid(const void* kernel, size_t smem, const Ctx& c, int want) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem) != cudaSuccess || per_sm < 1)
+        return 0;
+    const int cap = per_sm * c.dev.sms;
+    return want < cap ? want : cap;
+}
+
+}  // namespace
+
+int coop_scratch_elems(i64 nb, int grid, size_t* elems) {
+    // LU: 2G (vals) + 2G (idx) + 2*G*nb + 2*nb ; HH: G + 1 + G*nb + G*nb*nb + nb*nb
+    const size_t G = (size_t)grid;
+    const size_t lu = 4 * G + 2 * G * nb + 2 * nb;
+    const size_t hh = G + 8 + G * nb + G * nb * nb + nb * nb;
+    *elems = (lu > hh ? lu : hh) + 64;
+    return 0;
+}
+
+static int launch_coop(const Ctx& c, const void* kernel, int grid, size_t smem, void* args) {
+    void* kargs[] = {args};
+    cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(NT), kargs, smem, c.stream);
+    if (e != cudaSuccess) {
+        set_error("cooperative launch (grid %d, smem %zu): %s", grid, smem, cudaGetErrorString(e));
+        return BQRRP_ECUDA;
+    }
+    return 0;
+}
+
+// Row-pivoted LU (first-maximum rule) of X = Sk^T, X: N x d, Sk: d x N with ld
+// ldsk, all min(N, d) steps; writes the 0-based swap sequence to ipiv.  Sk is
+// overwritten by the factors (in transposed layout).
+int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
+    const i64 steps = imin(N, d);
+    if (steps <= 0) return 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemLu);
+        attr_set = true;
+    }
+    const i64 nbmax = 64;
+    const int Gmax_all = (int)imin(c.dev.sms, 148);
+    size_t need = 0;
+    coop_scratch_elems(nbmax, Gmax_all, &need);
+    if (need > c.coop_elems) {
+        set_error("getrf_pivots: cooperative scratch too small");
+        return BQRRP_ENOMEM;
+    }
+    View Skv = colmajor(Sk, ldsk);
+    for (i64 jb = 0; jb < steps; jb += nbmax) {
+        const int pw = (int)imin(nbmax, d - jb);
+        const int st = (int)imin(nbmax, steps - jb);
+        const i64 rows = N - jb;
+        // CTAs: one slab of >= 16 rows each, at most one per SM
+        int G = (int)imin(cdiv(rows, 16), Gmax_all);
+        i64 R = cdiv(rows, G);
+        size_t smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
+        if (smem > (size_t)kMaxSmemLu) {
+            set_error("getrf_pivots: %lld rows exceed the panel capacity", (long long)rows);
+            return BQRRP_EUNSUPPORTED;
+        }
+        const int Gc = coop_grid((const void*)lu_panel_kernel, smem, c, G);
+        if (Gc < G) {
+            G = Gc;
+            if (G < 1) { set_error("getrf_pivots: no co-resident grid"); return BQRRP_ECUDA; }
+            R = cdiv(rows, G);
+            smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
+            if (smem > (size_t)kMaxSmemLu) { set_error("getrf_pivots: panel too tall"); return BQRRP_EUNSUPPORTED; }
+        }
+        G = (int)cdiv(rows, R);   // drop CTAs that would own no rows
+        LuArgs a{};
+        a.N = N; a.jb = jb; a.ldsk = ldsk; a.pw = pw; a.steps = st; a.R = (int)R; a.Rp = (int)(R | 1);
+        a.Sk = Sk; a.ipiv = ipiv; a.st = c.st;
+        a.cand_v = c.coop;
+        a.cand_t = c.coop + 2 * G;
+        a.cand_row = c.coop + 4 * G;
+        a.cur_row = c.coop + 4 * G + 2 * (size_t)G * pw;
+        BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));
+        const i64 below = d - (jb + pw);
+        if (below > 0) {
+            lu_swap_rows_kernel<<<(unsigned)cdiv(below, 128), 128, 0, c.stream>>>(jb + pw, d, jb, st, ipiv, Sk, ldsk);
+            BQ_LAUNCH_CHECK();
+        }
+        if (jb + st >= steps) break;
+        if (below > 0) {
+            // U12^T = Sk(jb+pw:d, jb:jb+pw) * L11^{-T}; L11^T = unit upper part of Sk(jb:jb+pw, jb:jb+pw)
+            BQ_TRY(trsm_ru(c, below, pw, Skv.sub(jb, jb), Skv.sub(jb + pw, jb), true));
+            // trailing: Sk(jb+pw:d, jb+pw:N) -= U12^T * L21^T
+            BQ_TRY(dgemm(c, false, false, below, N - jb - pw, pw, -1.0, Sk + (jb + pw) + jb * ldsk, ldsk,
+                         Sk + jb + (jb + pw) * ldsk, ldsk, 1.0, Sk + (jb + pw) + (jb + pw) * ldsk, ldsk));
+        }
+    }
+    return 0;
+}
+
+// Blocked Householder QR (GEQRF semantics) of rows x cols A: panels of nb
+// columns by hh_panel_kernel, trailing update C -= V (T^T (V^T C)).
+// V: rows x nb, T: nb x nb, W, W2: nb x cols.
+int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* tau, double* V, double* T,
+                  double* W, double* W2, i64 nb, i64 kstop) {
+    i64 kk = imin(rows, cols);
+    if (kstop >= 0) kk = imin(kk, kstop);   // factor only the first kstop columns, update all
+    if (kk <= 0) return 0;
+    if (nb > 64) nb = 64;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(hh_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
+        attr_set = true;
+    }
+    const int Gmax_all = (int)imin(c.dev.sms, 148);
+    size_t need = 0;
+    coop_scratch_elems(nb, Gmax_all, &need);
+    if (need > c.coop_elems) {
+        set_error("geqrf_blocked: cooperative scratch too small");
+        return BQRRP_ENOMEM;
+    }
+    for (i64 jb = 0; jb < kk; jb += nb) {
+        const int pw = (int)imin(nb, kk - jb);
+        const i64 prow = rows - jb;
+        int G = (int)imin(cdiv(prow, 32), Gmax_all);
+        i64 R = cdiv(prow, G);
+        size_t smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
+        if (smem > (size_t)kMaxSmemHh) {
+            set_error("geqrf_blocked: %lld rows exceed the panel capacity", (long long)prow);
+            return BQRRP_EUNSUPPORTED;
+        }
+        const int Gc = coop_grid((const void*)hh_panel_kernel, smem, c, G);
+        if (Gc < G) {
+            G = Gc;
+            if (G < 1) { set_error("geqrf_blocked: no co-resident grid"); return BQRRP_ECUDA; }
+            R = cdiv(prow, G);
+            smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
+            if (smem > (size_t)kMaxSmemHh) { set_error("geqrf_blocked: panel too tall"); return BQRRP_EUNSUPPORTED; }
+        }
+        G = (int)cdiv(prow, R);
+        HhArgs a{};
+        a.rows = prow; a.lda = lda; a.ldv = rows; a.ldt = nb; a.pw = pw; a.R = (int)R; a.Rp = (int)(R | 1);
+        a.A = A + jb + jb * lda; a.tau = tau + jb; a.V = V; a.T = T; a.st = c.st;
+        a.part1 = c.coop;
+        a.alpha = c.coop + G;
+        a.part2 = c.coop + G + 8;
+        a.gpart = c.coop + G + 8 + (size_t)G * pw;
+        a.gsum = a.gpart + (size_t)G * pw * pw;
+        BQ_TRY(launch_coop(c, (const void*)hh_panel_kernel, G, smem, &a));
+        const i64 nc = cols - jb - pw;
+        if (nc > 0) {
+            double* C = A + jb + (jb + pw) * lda;
+            BQ_TRY(dgemm(c, true, false, pw, nc, prow, 1.0, V, rows, C, lda, 0.0, W, nb));
+            BQ_TRY(dgemm(c, true, false, pw, nc, pw, 1.0, T, nb, W, nb, 0.0, W2, nb));
+            BQ_TRY(dgemm(c, false, false, prow, nc, pw, -1.0, V, rows, W2, nb, 1.0, C, lda));
+        }
+    }
+    return 0;
+}
+
+}  // namespace bq

@@ -1,0 +1,145 @@
+"""End-to-end GPU parity of bqrrp_factor (C ABI) against the CPU oracle.
+
+Bar (from the method's specification): pivot vectors identical where every
+LU pivot step of the oracle is gapped (relative top-2 margin > 1e-6, far above
+the 1e-13-level differences two FP64 summation orders produce); ranks equal;
+||AP - QR||_F / ||A||_F <= 1e-12; ||Q^T Q - I||_F <= 1e-12; the rank-s
+truncation error ||R(s:, s:)||_F at every block boundary s within 1.1x of the
+oracle's; R itself within 1e-10 * ||A||_F of the oracle's (R is unique up to
+row signs, and both sides use the same sign rule); tau_j within
+100 sqrt(m) u ||A||_F / |R_jj| (a reflector is only as well determined as the
+trailing block it annihilates).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2507_00976_b300 as bq
+from checks import metrics, trailing_norms, upper_r
+from gpu_util import np_
+from paper_2507_00976_b300 import binding as B
+from paper_2507_00976_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(A, b, d, seed, sketch="dense", panel="cholqr"):
+    F, jpvt, tau, rank = bq.factor(A, b, d, seed, sketch=sketch, panel=panel)
+    torch.cuda.synchronize()
+    return np_(F), np_(jpvt), np_(tau), rank
+
+
+def compare(A, b, d, seed, sketch="dense", panel="cholqr", expect_rank=None):
+    kind = 0 if sketch == "dense" else 1
+    fo = oracle.bqrrp(A, b, d, seed, sketch_kind=kind, panel=panel)
+    F, jpvt, tau, rank = run_gpu(A, b, d, seed, sketch, panel)
+    assert rank == fo.rank
+    if expect_rank is not None:
+        assert rank == expect_rank
+    gapped = all(t["margin"] > 1e-6 for t in fo.trace)
+    if gapped:
+        # beyond the numerical rank the sketch is rounding noise, so only the
+        # first `rank` pivots are determined by the input
+        assert np.array_equal(jpvt[:rank], fo.jpvt[:rank])
+        assert set(jpvt[rank:]) == set(fo.jpvt[rank:])
+    res, orth, ok = metrics(A, F, jpvt, tau, rank)
+    assert ok and res <= 1e-12 and orth <= 1e-12, (res, orth)
+    n = A.shape[1]
+    bounds = list(range(0, n, b))
+    tg = trailing_norms(F, rank, bounds)
+    to = trailing_norms(fo.A, fo.rank, bounds)
+    nrm = np.linalg.norm(A)
+    assert np.all(tg <= 1.1 * to + 1e-13 * nrm)
+    if gapped and rank == n:
+        R = upper_r(F, rank)[:n]
+        Ro = upper_r(fo.A, fo.rank)[:n]
+        assert np.linalg.norm(R - Ro) <= 1e-10 * nrm
+        # tau_j is fixed only up to the conditioning of the trailing block it
+        # comes from: relative error ~ u ||A||_F / |R_jj| (times a sqrt(m) factor)
+        m = A.shape[0]
+        rjj = np.abs(np.diag(Ro)[:rank])
+        bound = 100 * np.sqrt(m) * 2.0 ** -53 * nrm / np.maximum(rjj, 1e-300)
+        assert np.all(np.abs(tau[:rank] - fo.tau[:rank]) <= np.minimum(bound, 1.0) + 1e-14)
+    return F, jpvt, tau, rank, fo
+
+
+def test_c1_parity():
+    """2000 x 1000, sigma_k = 10^(-10(k-1)/999), b = 128, d = 160, Philox seed 1."""
+    A = W.c1_matrix()
+    compare(A, 128, 160, 1, expect_rank=1000)
+
+
+@pytest.mark.parametrize("m,n,b,d", [(777, 500, 64, 80), (300, 300, 300, 375), (1000, 100, 128, 160),
+                                     (513, 257, 32, 40), (4100, 130, 64, 80), (65, 65, 8, 10)])
+def test_shapes_with_ragged_tails(m, n, b, d):
+    A = W.gaussian(m, n, m * 3 + n)
+    compare(A, b, d, 5, expect_rank=n)
+
+
+def test_exact_low_rank():
+    A = W.low_rank(1000, 600, 150, 4)
+    compare(A, 64, 80, 2, expect_rank=150)
+
+
+def test_low_rank_at_block_boundary():
+    A = W.low_rank(700, 400, 128, 8)
+    compare(A, 64, 80, 2, expect_rank=128)
+
+
+def test_sparse_sign_sketch():
+    A = W.c1_matrix()
+    compare(A, 128, 160, 1, sketch="sparse")
+
+
+def test_householder_panel_variant():
+    A = W.gaussian(900, 700, 12)
+    compare(A, 96, 120, 3, panel="hqr", expect_rank=700)
+
+
+def test_kahan_matrix_valid_factorization():
+    A = W.kahan(512)
+    F, jpvt, tau, rank = run_gpu(A, 64, 80, 3)
+    res, orth, ok = metrics(A, F, jpvt, tau, rank)
+    assert ok and res <= 1e-12 and orth <= 1e-12
+
+
+def test_zero_matrix():
+    F, jpvt, tau, rank = run_gpu(np.zeros((300, 200)), 32, 40, 1)
+    assert rank == 0 and np.all(tau == 0) and sorted(jpvt) == list(range(1, 201))
+
+
+def test_deterministic_and_host_entry_point_identical():
+    A = W.gaussian(1500, 900, 21)
+    F1, j1, t1, r1 = run_gpu(A, 100, 125, 9)
+    F2, j2, t2, r2 = run_gpu(A, 100, 125, 9)
+    assert np.array_equal(F1, F2) and np.array_equal(j1, j2) and np.array_equal(t1, t2) and r1 == r2
+    m, n = A.shape
+    Ah = torch.as_tensor(A).t().contiguous().t().pin_memory() if False else None
+    Ah = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+    Ah.copy_(torch.as_tensor(A))
+    jh = torch.empty(n, dtype=torch.int64).pin_memory()
+    th = torch.empty(n, dtype=torch.float64).pin_memory()
+    ws = torch.empty(B.bqrrp_workspace_query_host(m, n, 100, 125), dtype=torch.uint8, device="cuda")
+    r3 = B.bqrrp_factor_host(Ah, 100, 125, 9, jh, th, ws)
+    assert r3 == r1
+    assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
+
+
+def test_error_codes():
+    A = bq.to_colmajor(W.gaussian(40, 30, 1))
+    jp = torch.empty(30, dtype=torch.int64, device="cuda")
+    tau = torch.empty(30, dtype=torch.float64, device="cuda")
+    need = B.bqrrp_workspace_query(40, 30, 8, 10)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    rc, _ = B.bqrrp_factor_status(A, 8, 10, 1, jp, tau, workspace=ws, workspace_bytes=need - 4096)
+    assert rc == B.ENOMEM
+    A2 = A.clone()
+    A2[5, 5] = float("nan")
+    before = A2.clone()
+    rc, rank = B.bqrrp_factor_status(A2, 8, 10, 1, jp, tau, workspace=ws)
+    assert rc == B.ENUMERIC and rank == -1
+    assert torch.equal(torch.isnan(A2), torch.isnan(before))
+    wide = bq.to_colmajor(W.gaussian(20, 30, 1))
+    rc, _ = B.bqrrp_factor_status(wide, 8, 10, 1, jp, tau, workspace=ws)
+    assert rc == -1
