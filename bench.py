@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 BQRRP on B300, canonical GFLOP/s (2mn^2 - 2n^3/3 per solve,
+the GEQRF count the paper uses, Sec. 1.3) next to the library's own unpivoted
+blocked Householder QR on the same input, with p50/p99 solve latency.
+
+Default workload: one m = n = 16384 matrix with iid N(0,1) entries (the
+paper's performance matrices), block b = 512 (= n/32, the paper's
+recommendation), sketch d = ceil(1.25 b) = 640 rows of a Philox +-1 operator,
+CholQR panel.  One step = one complete bqrrp_factor call on a fresh copy of
+the input already resident in HBM.
+
+  python bench.py [--gpus N --steps K --warmup W] [--n 32768 --b 1024 ...]
+  python bench.py --impl reference ...   # the CPU oracle, timed on the host
+
+Multi-GPU: the factorization of one matrix does not shard (every block needs
+a global pivot choice), so N GPUs run N independent replicas ("replicas
+only"); value = total canonical FLOPs of all ranks / max over ranks of the
+timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BQRRP GFLOP/s (2mn²−2n³/3) vs own unpivoted QR on 1 B300; p50/p99 solve latency"
+SM_COUNT = 148
+SM_MAX_MHZ = 2032.0
+# FP64: 2 DFMA per clock per SM (the measured DFMA rate is 1.82-1.97 per clock
+# per SM; tcgen05 has no f64 kind), 2 FLOP per DFMA.
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def canonical_flops(m, n):
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--m", type=int, default=None)
+    p.add_argument("--b", type=int, default=512)
+    p.add_argument("--d", type=int, default=None)
+    p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
+    p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")
+    p.add_argument("--panel", choices=["cholqr", "hqr"], default="cholqr")
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
+    p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
+    p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
+    a = p.parse_args()
+    a.m = a.m or a.n
+    a.d = a.d or int(math.ceil(1.25 * a.b))
+    return a
+
+
+def workload_name(a):
+    fam = "iid N(0,1)" if a.family == "gaussian" else "U diag(sigma) V^T, sigma geometric 1..1e-12"
+    sk = "dense Philox +-1" if a.sketch == "dense" else "sparse-sign (8 nnz/col)"
+    return f"FP64 BQRRP m={a.m} n={a.n} b={a.b} d={a.d}, {fam}, {sk} sketch, {a.panel} panel"
+
+
+def config(a, world):
+    return {"workload": workload_name(a), "m": a.m, "n": a.n, "b": a.b, "d": a.d, "family": a.family,
+            "sketch": a.sketch, "panel": a.panel, "seed": a.seed,
+            "l2": f"inputs larger than L2 (A is {a.m * a.n * 8 / 1e9:.2f} GB, L2 126 MB)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="bqrrp_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def cpu_sample(a, budget_s=20.0):
+    """Time the CPU oracle (single thread, as it stands) on a bounded sample of
+    the workload: the leading s x s block of a seeded matrix of the same
+    family, with the same b/n ratio and gamma.  Returns (GFLOP/s, description)."""
+    import numpy as np
+
+    import oracle
+    from paper_2507_00976_b300 import workloads as W
+    s = 2560
+    b = max(8, int(round(a.b * s / a.n)))
+    d = max(b, int(math.ceil(a.d / a.b * b)))
+    if a.family == "gaussian":
+        A = W.gaussian(s, s, a.seed)
+    else:
+        A = W.spectrum(s, s, W.geometric_sigma(s, -12.0), a.seed)
+    t0 = time.perf_counter()
+    oracle.bqrrp(A, b, d, 1, sketch_kind=0 if a.sketch == "dense" else 1)
+    dt = time.perf_counter() - t0
+    gf = canonical_flops(s, s) / dt / 1e9
+    return gf, f"oracle BQRRP on {s}x{s} ({a.family}), b={b}, d={d}, 1 thread, {dt:.1f} s", 1
+
+
+def run_reference(a, world, rank):
+    """--impl reference: the oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2507_00976_b300 import workloads as W
+    s = 1536
+    b = max(8, int(round(a.b * s / a.n)))
+    d = max(b, int(math.ceil(a.d / a.b * b)))
+    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -12.0), a.seed)
+    for _ in range(a.warmup):
+        oracle.bqrrp(A, b, d, 1)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.bqrrp(A, b, d, 1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = canonical_flops(s, s) * len(times) / tot / 1e9
+    sample = f"oracle BQRRP on {s}x{s} (leading-size sample of the workload), b={b}, d={d}, 1 thread per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a, world),
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+        return
+
+    import torch
+
+    import paper_2507_00976_b300 as bq
+    from paper_2507_00976_b300 import binding as B
+    from paper_2507_00976_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    m, n, b, d = a.m, a.n, a.b, a.d
+    seed = a.seed + 1000 * rank
+    if a.family == "gaussian":
+        A0 = W.gaussian_torch(m, n, seed)
+    else:
+        A0 = W.spectrum_torch(m, n, W.geometric_sigma(min(m, n), -12.0), seed)
+    A = bq.colmajor_empty(m, n)
+    jpvt = torch.empty(n, dtype=torch.int64, device="cuda")
+    tau = torch.empty(n, dtype=torch.float64, device="cuda")
+    opts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
+                       B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR)
+    ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    probe = B.bqrrp_probe_fp64_peak(4000)
+
+    def one_factor():
+        A.copy_(A0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rk = B.bqrrp_factor(A, b, d, 1, jpvt, tau, opts=opts, workspace=ws)
+        e1.record(stream)
+        return e0, e1, rk
+
+    for _ in range(a.warmup):
+        one_factor()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: exactly K steps
+    sampler = ClockSampler(local)
+    B.bqrrp_profile_reset()
+    B.bqrrp_profile_enable(True)
+    launches0 = B.bqrrp_launch_counter()
+    barrier()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    evs = []
+    ranks = []
+    for _ in range(a.steps):
+        e0, e1, rk = one_factor()
+        evs.append((e0, e1))
+        ranks.append(rk)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clocks = sampler.stop()
+    launches = B.bqrrp_launch_counter() - launches0
+    B.bqrrp_profile_enable(False)
+    prof = B.bqrrp_profile_read()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    flops = canonical_flops(m, n)
+    value = flops * a.steps * world / (tot_ms * 1e-3) / 1e9
+
+    # ---------------- the library's own unpivoted QR on the same input
+    qr = None
+    if not a.skip_qr:
+        qtau = torch.empty(n, dtype=torch.float64, device="cuda")
+        qws = torch.empty(B.bqrrp_geqrf_workspace(m, n, 0), dtype=torch.uint8, device="cuda")
+        qms = []
+        for i in range(a.steps + 1):
+            A.copy_(A0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bqrrp_geqrf(A, 0, tau=qtau, workspace=qws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                qms.append(e0.elapsed_time(e1))
+        qr_gf = flops / (statistics.mean(qms) * 1e-3) / 1e9
+        qr = {"gflops": qr_gf, "ms_mean": statistics.mean(qms), "ms_best": min(qms),
+              "bqrrp_over_qr": (flops / (statistics.mean(step_ms) * 1e-3) / 1e9) / qr_gf}
+        del qws
+
+    # ---------------- end to end through the host-buffer entry point
+    e2e = None
+    if not a.skip_e2e:
+        Ah0 = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+        Ah0.copy_(A0)
+        Ah = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+        jh = torch.empty(n, dtype=torch.int64).pin_memory()
+        th = torch.empty(n, dtype=torch.float64).pin_memory()
+        del ws
+        torch.cuda.empty_cache()
+        hws = torch.empty(B.bqrrp_workspace_query_host(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
+        ems = []
+        k_e2e = max(1, min(a.steps, 3))
+        for _ in range(k_e2e):
+            Ah.copy_(Ah0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bqrrp_factor_host(Ah, b, d, 1, jh, th, hws, opts=opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ems.append(e0.elapsed_time(e1))
+        tot = sum(ems)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": flops * k_e2e * world / (tot * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * 16, "steps": k_e2e,
+               "entry_point": "bqrrp_factor_host (pinned host buffers)"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel: the FP64 GEMMs of the trailing update
+    tr_ms, tr_fl = prof["trailing"]
+    achieved = tr_fl / (tr_ms * 1e-3) / 1e12 if tr_ms > 0 else None
+    phases = {}
+    for name in B.PHASES:
+        ms, fl = prof[name]
+        phases[name] = {"ms_per_step": ms / max(1, prof["calls"]),
+                        "share": ms / max(1e-9, sum(prof[p][0] for p in B.PHASES)),
+                        "tflops": (fl / (ms * 1e-3) / 1e12) if ms > 0 and fl > 0 else None}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                "kernel": "dgemm_kernel (FP64 SIMT GEMMs of the trailing block-reflector update)",
+                "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
+                "dfma_probe_tflops": probe}
+    cpu = None
+    if not a.skip_cpu and world == 1:
+        gf, sample, cores = cpu_sample(a)
+        cpu = {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+    lat = sorted(step_ms)
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": config(a, world),
+        "latency_ms": {"p50": statistics.median(lat), "p99": p99, "best": lat[0]},
+        "best_gflops": flops / (lat[0] * 1e-3) / 1e9,
+        "own_qr": qr, "rank": ranks[0], "gpu_launches": launches, "wall_s": t_wall,
+        "roofline": roofline, "phases": phases, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

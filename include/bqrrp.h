@@ -202,6 +202,29 @@ size_t bqrrp_dgemm_workspace(int64_t M, int64_t N, int64_t K);
  */
 double bqrrp_probe_fp64_peak(int iters, void* stream);
 
+/*
+ * Phase profile (measurement helper, off by default).  When enabled,
+ * bqrrp_factor records CUDA events on its stream around each step of Alg. 1
+ * and, after its final synchronization, adds the device time (ms) and the
+ * algorithmic FLOP count of each phase to a process-wide accumulator.
+ * Phases: 0 sketch S*A, 1 LU with partial pivoting + piv_transform,
+ * 2 sketch gather + Householder QR + tri_rank, 3 permutation of A and J,
+ * 4 panel (Alg. 3), 5 trailing update (three GEMMs), 6 sketch update,
+ * 7 other (checks, setup, rank read-backs).
+ */
+#define BQRRP_NPHASES 8
+typedef struct bqrrp_profile {
+    double ms[BQRRP_NPHASES];     /* accumulated device time per phase          */
+    double flops[BQRRP_NPHASES];  /* accumulated algorithmic FLOPs per phase    */
+    int64_t calls;                /* profiled bqrrp_factor calls                */
+} bqrrp_profile;
+void bqrrp_profile_enable(int on);
+void bqrrp_profile_reset(void);
+int bqrrp_profile_read(bqrrp_profile* out);
+
+/* Number of kernel launches the library has issued since it was loaded. */
+int64_t bqrrp_launch_counter(void);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* bqrrp_last_error(void);
 

@@ -39,6 +39,14 @@ class Opts(ctypes.Structure):
                 ("reserved", _i64 * 5)]
 
 
+NPHASES = 8
+PHASES = ["sketch", "lupp", "sketch_qr", "permute", "panel", "trailing", "sketch_update", "other"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", _d * NPHASES), ("flops", _d * NPHASES), ("calls", _i64)]
+
+
 class BqrrpError(RuntimeError):
     def __init__(self, fn, code, msg):
         super().__init__(f"{fn} returned {code}: {msg}")
@@ -69,6 +77,10 @@ _SIGS = {
                      _sz, _vp], ctypes.c_int),
     "bqrrp_dgemm_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_probe_fp64_peak": ([ctypes.c_int, _vp], _d),
+    "bqrrp_profile_enable": ([ctypes.c_int], None),
+    "bqrrp_profile_reset": ([], None),
+    "bqrrp_profile_read": ([ctypes.POINTER(Profile)], ctypes.c_int),
+    "bqrrp_launch_counter": ([], _i64),
     "bqrrp_last_error": ([], ctypes.c_char_p),
     "bqrrp_version": ([], ctypes.c_char_p),
 }
@@ -289,6 +301,27 @@ def bqrrp_dgemm(transa, transb, alpha, A, B, beta, C, workspace=None, stream=Non
 
 def bqrrp_probe_fp64_peak(iters=2000, stream=None):
     return float(lib().bqrrp_probe_fp64_peak(iters, _stream(stream)))
+
+
+def bqrrp_profile_enable(on=True):
+    lib().bqrrp_profile_enable(1 if on else 0)
+
+
+def bqrrp_profile_reset():
+    lib().bqrrp_profile_reset()
+
+
+def bqrrp_profile_read():
+    """dict phase -> (ms, flops) plus 'calls'."""
+    p = Profile()
+    lib().bqrrp_profile_read(ctypes.byref(p))
+    out = {name: (p.ms[i], p.flops[i]) for i, name in enumerate(PHASES)}
+    out["calls"] = p.calls
+    return out
+
+
+def bqrrp_launch_counter():
+    return int(lib().bqrrp_launch_counter())
 
 
 # ----------------------------------------------------------------- convenience

@@ -14,10 +14,13 @@
 //   sketch  : Msk(0:w, c:) -= (Rsk11 R11^-1) R12      (Duersch-Gu update)
 // All arithmetic runs in the library's kernels; the host only sequences
 // launches and reads k.
+#include <atomic>
 #include <climits>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -34,6 +37,71 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 const char* get_error() { return g_err; }
+
+namespace {
+std::atomic<long long> g_launches{0};
+
+// Phase profiler: event pairs recorded on the factorization's stream,
+// resolved after the call's final synchronization.
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    double ms[BQRRP_NPHASES] = {0};
+    double flops[BQRRP_NPHASES] = {0};
+    long long calls = 0;
+};
+Profiler g_prof;
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-call recorder (only active when the profiler is on).
+struct PhaseRec {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+    double fl[BQRRP_NPHASES] = {0};
+    int cur = -1;
+    cudaEvent_t cur_ev = nullptr;
+    std::vector<cudaEvent_t> events;   // created per call, destroyed in resolve()
+    cudaEvent_t take() {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        events.push_back(e);
+        return e;
+    }
+    void begin(int phase) {
+        if (!on) return;
+        end();
+        cur = phase;
+        cur_ev = take();
+        cudaEventRecord(cur_ev, st);
+    }
+    void end() {
+        if (!on || cur < 0) return;
+        cudaEvent_t e = take();
+        cudaEventRecord(e, st);
+        spans.push_back({cur, {cur_ev, e}});
+        cur = -1;
+    }
+    void flops(int phase, double f) { if (on) fl[phase] += f; }
+    void resolve() {   // after the stream has been synchronized
+        if (!on) return;
+        end();
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        for (auto& sp : spans) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, sp.second.first, sp.second.second) == cudaSuccess) g_prof.ms[sp.first] += t;
+        }
+        for (int i = 0; i < BQRRP_NPHASES; ++i) g_prof.flops[i] += fl[i];
+        g_prof.calls += 1;
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        events.clear();
+    }
+    ~PhaseRec() {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+    }
+};
 
 int current_device(Device* dev) {
     static std::mutex mu;
@@ -276,9 +344,22 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
 namespace {
 
 // ------------------------------------------------------------------ the factorization
+inline double geqrf_flops(double r, double c) {   // LAWN 41 count of GEQRF on r x c
+    return r >= c ? 2.0 * r * c * c - 2.0 * c * c * c / 3.0 : 2.0 * c * r * r - 2.0 * r * r * r / 3.0;
+}
+
+inline double lupp_flops(double N, double d) {      // GETRF on N x d: sum_j (N-j-1)(1 + 2(d-j-1))
+    const double s = N < d ? N : d;
+    double f = 0.0;
+    for (double j = 0; j < s; j += 1.0) f += (N - j - 1.0) * (1.0 + 2.0 * (d - j - 1.0));
+    return f;
+}
+
 int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i64* jpvt, double* tau, i64* rank,
-                const bqrrp_opts& o, const Bufs& B, Ctx& c) {
+                const bqrrp_opts& o, const Bufs& B, Ctx& c, PhaseRec& pr) {
+    enum { P_SKETCH = 0, P_LUPP, P_SKQR, P_PERM, P_PANEL, P_TRAIL, P_SKUPD, P_OTHER };
     DevStatus hs{};
+    pr.begin(P_OTHER);
     init_status_kernel<<<1, 1, 0, c.stream>>>(B.st);
     BQ_LAUNCH_CHECK();
     // NaN/Inf in A -> BQRRP_ENUMERIC before anything is written
@@ -293,10 +374,13 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
     BQ_LAUNCH_CHECK();
 
     // Alg. 1: sketch Msk = S * A (d x n)
+    pr.begin(P_SKETCH);
     if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
         BQ_TRY(sketch_dense_gemm(c, d, m, n, seed, A, lda, B.Msk, d));
+        pr.flops(P_SKETCH, 2.0 * d * m * n);
     } else {
         BQ_TRY(sketch_sparse_apply(c, d, m, n, seed, o.sketch_nnz, A, lda, B.Msk, d, B.sparse_ws, B.sparse_bytes));
+        pr.flops(P_SKETCH, 2.0 * (double)o.sketch_nnz * m * n);
     }
 
     i64 ell = 0;
@@ -307,9 +391,9 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         const i64 N = n - s;
         const i64 rows = m - s;
         double* Ssk = B.Msk + s * d;
-        View Sv = colmajor(Ssk, d);
 
-        // ---- Alg. 2 on the sketch
+        // ---- Alg. 2 on the sketch: LUPP of Ssk^T and piv_transform
+        pr.begin(P_LUPP);
         BQ_CUDA(cudaMemsetAsync(&B.st->sk_nonfinite, 0, sizeof(int), c.stream));
         BQ_CUDA(cudaMemsetAsync(&B.st->zero_col, 0, sizeof(int), c.stream));
         BQ_TRY(any_nonfinite(c, d, N, Ssk, d, &B.st->sk_nonfinite));
@@ -318,18 +402,24 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         const i64 steps = imin(N, d);
         BQ_TRY(getrf_pivots(c, N, d, B.Xlu, d, B.ipiv));
         BQ_TRY(piv_transform_moved(c, N, steps, B.ipiv, B.Jsk, &B.st->sk_nonfinite, B.pos, B.src, B.cnt));
+        pr.flops(P_LUPP, lupp_flops((double)N, (double)d));
+        // ---- gather + Householder QR of the sketch, tri_rank
+        pr.begin(P_SKQR);
         const i64 mm = imin(N, 2 * steps);
         BQ_TRY(gather_cols(c, d, Ssk, d, B.pos, B.src, B.cnt, mm, B.stage, d));
         BQ_TRY(geqrf_blocked(c, d, N, Ssk, d, B.sktau, B.Vqr, B.Tqr, B.W, B.W2, 64));
         BQ_TRY(set_zero_below(c, d, N, Ssk, d));
         tri_rank_kernel<<<1, 32, 0, c.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
         BQ_LAUNCH_CHECK();
+        pr.flops(P_SKQR, geqrf_flops((double)d, (double)N));
 
         // ---- permute A(:, s:) (all m rows: R rows and working rows, merged) and J(s:)
+        pr.begin(P_PERM);
         BQ_TRY(gather_cols(c, m, A + s * lda, lda, B.pos, B.src, B.cnt, mm, B.stage, B.ldst));
         BQ_TRY(gather_idx(c, B.J + s, B.pos, B.src, B.cnt, mm, B.Jstage));
         col_nonzero_kernel<<<gblocks(c, rows), 256, 0, c.stream>>>(rows, A + s + s * lda, &B.st->zero_col);
         BQ_LAUNCH_CHECK();
+        pr.begin(P_OTHER);
         BQ_TRY(read_status(c, &hs));
         if (!hs.zero_col) { ell = s; break; }   // first permuted working column is zero
         i64 k = hs.k;
@@ -340,35 +430,50 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         if (o.panel_kind == BQRRP_PANEL_HQR) {
             // Householder QR of all w panel columns, reflectors applied to the
             // whole trailing block; only the first k are kept (Sec. 4.5).
+            pr.begin(P_PANEL);
             BQ_TRY(geqrf_blocked(c, rows, N, Ap, lda, tau + s, B.Vqr, B.Tqr, B.W, B.W2, 64, w));
             if (k < w) {
                 zero_tail_kernel<<<(unsigned)cdiv(w, 256), 256, 0, c.stream>>>(s + k, s + w, tau);
                 BQ_LAUNCH_CHECK();
             }
+            pr.flops(P_PANEL, geqrf_flops((double)rows, (double)w) + 4.0 * rows * w * nc);
         } else {
             // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
+            pr.begin(P_PANEL);
             BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
                                       tau + s));
+            {
+                const double r = (double)rows, kk = (double)k;
+                // TRSM, Gram, TRSM, reconstruction (rows k^2 each) + Cholesky, T, R11 (k^3 terms)
+                pr.flops(P_PANEL, 2.0 * r * kk * kk * 4.0 + kk * kk * kk * (1.0 / 3.0 + 1.0 / 3.0) + 2.0 * kk * kk * w);
+            }
             if (k <= 0) { ell = s; break; }
             // ---- trailing update with the block reflector (I - Y T Y^T)^T
             if (nc > 0) {
+                pr.begin(P_TRAIL);
                 double* C = A + s + cend * lda;
                 const i64 keep = (k == w) ? rows : k;
                 BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
                 BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
                 BQ_TRY(dgemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+                pr.flops(P_TRAIL, 2.0 * (double)k * nc * (double)rows + 2.0 * (double)k * k * nc +
+                                      2.0 * (double)keep * nc * k);
             }
         }
         if (cend == n || k < w) { ell = s + k; break; }
 
         // ---- sketch update: Msk(0:w, c:) = Rsk12 - (Rsk11 R11^-1) R12; Rsk22 stays
+        pr.begin(P_SKUPD);
         BQ_TRY(copy_triu(c, w, w, Ssk, d, B.Z, B.bb));
         BQ_TRY(trsm_ru(c, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
         BQ_TRY(dgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
+        pr.flops(P_SKUPD, (double)w * w * w + 2.0 * (double)w * w * nc);
     }
+    pr.begin(P_OTHER);
     plus_one_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c.stream>>>(n, B.J, jpvt);
     BQ_LAUNCH_CHECK();
     BQ_TRY(read_status(c, &hs));
+    pr.end();
     *rank = ell;
     return 0;
 }
@@ -387,6 +492,27 @@ using namespace bq;
 extern "C" {
 
 const char* bqrrp_last_error(void) { return get_error(); }
+
+void bqrrp_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = on != 0;
+}
+
+void bqrrp_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (int i = 0; i < BQRRP_NPHASES; ++i) { g_prof.ms[i] = 0.0; g_prof.flops[i] = 0.0; }
+    g_prof.calls = 0;
+}
+
+int bqrrp_profile_read(bqrrp_profile* out) {
+    if (!out) return -1;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (int i = 0; i < BQRRP_NPHASES; ++i) { out->ms[i] = g_prof.ms[i]; out->flops[i] = g_prof.flops[i]; }
+    out->calls = g_prof.calls;
+    return 0;
+}
+
+int64_t bqrrp_launch_counter(void) { return g_launches.load(); }
 
 const char* bqrrp_version(void) { return "bqrrp-b300 0.1 (sm_103a, FP64 SIMT)"; }
 
@@ -437,8 +563,17 @@ int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_
     c.coop = B.coop;
     c.coop_elems = B.coop_elems;
     i64 r = 0;
-    const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c);
-    if (rc == 0) *rank = r;
+    PhaseRec pr;
+    {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        pr.on = g_prof.on;
+    }
+    pr.st = c.stream;
+    const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c, pr);
+    if (rc == 0) {
+        *rank = r;
+        pr.resolve();
+    }
     return rc;
 }
 

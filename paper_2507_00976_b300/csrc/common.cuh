@@ -34,8 +34,11 @@ const char* get_error();
         if (rc_ != 0) return rc_;                                                  \
     } while (0)
 
+void count_launch();
+
 #define BQ_LAUNCH_CHECK()                                                          \
     do {                                                                           \
+        ::bq::count_launch();                                                      \
         cudaError_t e_ = cudaGetLastError();                                       \
         if (e_ != cudaSuccess) {                                                   \
             ::bq::set_error("%s:%d launch: %s", __FILE__, __LINE__,                \

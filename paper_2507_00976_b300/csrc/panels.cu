@@ -381,6 +381,7 @@ int coop_scratch_elems(i64 nb, int grid, size_t* elems) {
 
 static int launch_coop(const Ctx& c, const void* kernel, int grid, size_t smem, void* args) {
     void* kargs[] = {args};
+    count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(NT), kargs, smem, c.stream);
     if (e != cudaSuccess) {
         set_error("cooperative launch (grid %d, smem %zu): %s", grid, smem, cudaGetErrorString(e));
