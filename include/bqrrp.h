@@ -134,6 +134,30 @@ int bqrrp_sketch_apply(int64_t d, int64_t m, int64_t n, const double* A, int64_t
 size_t bqrrp_sketch_apply_workspace(int64_t d, int64_t m, int kind, int64_t nnz);
 
 /*
+ * bqrrp_sketch_apply_sparse_noalloc -- the sparse-sign form of
+ * bqrrp_sketch_apply (same operator, same result) for callers that cannot
+ * allocate device memory or hand over a workspace: code whose device memory is
+ * entirely owned by another allocator, plug-ins that get device pointers but
+ * no allocator, loops that must never enter an allocator.  The operator's index
+ * lists live in a fixed array inside the library's device image (about
+ * 12.6 MB, held on every GPU that loads the library until process exit); the
+ * call allocates nothing.  The paper has no counterpart: this is a deployment
+ * convenience, not part of the method.
+ *  Limits: d <= 4096 and m*nnz <= 524288 (2^19); larger shapes return
+ *  BQRRP_EUNSUPPORTED with a message in bqrrp_last_error().
+ *  The first call on each device looks up the array's device address (with
+ *  that device current); make that first call before any stream capture.
+ *  All calls share the one array, which keeps the previous call's contents
+ *  (the call clears what must start at zero): calls that can overlap on the
+ *  GPU -- concurrent streams, other host threads -- race and must be
+ *  serialized by the caller.
+ *  Arguments as bqrrp_sketch_apply with kind = sparse: -1 d, -2 m, -3 n, -4 A,
+ *  -5 lda, -7 nnz, -8 Msk, -9 ldsk.
+ */
+int bqrrp_sketch_apply_sparse_noalloc(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda,
+                                      uint64_t seed, int64_t nnz, double* Msk, int64_t ldsk, void* stream);
+
+/*
  * bqrrp_qrcp_wide -- Alg. 2 on a d x N sketch: row-pivoted LU of Msk^T (all
  * min(N,d) steps, first-maximum pivot rule), piv_transform, column gather and
  * unpivoted Householder QR.  Msk: device d x N (ld ldsk), in: the sketch;

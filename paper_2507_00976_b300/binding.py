@@ -64,6 +64,7 @@ _SIGS = {
     "bqrrp_sketch_apply": ([_i64, _i64, _i64, _vp, _i64, _u64, ctypes.c_int, _i64, _vp, _i64, _vp, _sz, _vp],
                            ctypes.c_int),
     "bqrrp_sketch_apply_workspace": ([_i64, _i64, ctypes.c_int, _i64], _sz),
+    "bqrrp_sketch_apply_sparse_noalloc": ([_i64, _i64, _i64, _vp, _i64, _u64, _i64, _vp, _i64, _vp], ctypes.c_int),
     "bqrrp_qrcp_wide": ([_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_qrcp_wide_workspace": ([_i64, _i64], _sz),
     "bqrrp_col_perm": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
@@ -232,6 +233,18 @@ def bqrrp_sketch_apply(A, d, seed, kind=SKETCH_DENSE, nnz=8, Msk=None, stream=No
     rc = lib().bqrrp_sketch_apply(d, m, n, _ptr(A), _ld(A), seed, kind, nnz, _ptr(Msk), _ld(Msk), _ptr(ws), ws.numel(),
                                   _stream(stream))
     _check("bqrrp_sketch_apply", rc)
+    return Msk
+
+
+def bqrrp_sketch_apply_sparse_noalloc(A, d, seed, nnz=8, Msk=None, stream=None):
+    """Sparse-sign Msk = S*A with the library's fixed scratch (no workspace,
+    no allocation inside the call; Msk is allocated here when not given)."""
+    m, n = A.shape
+    if Msk is None:
+        Msk = colmajor_empty(d, n, device=A.device)
+    rc = lib().bqrrp_sketch_apply_sparse_noalloc(d, m, n, _ptr(A), _ld(A), seed, nnz, _ptr(Msk), _ld(Msk),
+                                                 _stream(stream))
+    _check("bqrrp_sketch_apply_sparse_noalloc", rc)
     return Msk
 
 
