@@ -1,6 +1,6 @@
 #!/usr/bin/env python
 """Benchmark: FP64 BQRRP on B300, canonical GFLOP/s (2mn^2 - 2n^3/3 per solve,
-the GEQRF count the paper uses, Sec. 1.3) next to the library's own unpivoted
+the GEQRF count the paper uses, Sec. 1.4) next to the library's own unpivoted
 blocked Householder QR on the same input, with p50/p99 solve latency.
 
 Default workload: one m = n = 16384 matrix with iid N(0,1) entries (the
@@ -44,6 +44,26 @@ def canonical_flops(m, n):
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
 
 
+def rank_seed(base, rank):
+    """Each replica factors its own matrix (independent problems)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Max of a per-rank float over all ranks (the timed region's length)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_step, steps, world, max_total_ms):
+    """Whole-job throughput: all ranks' canonical FLOPs over the slowest rank's time."""
+    return flops_per_step * steps * world / (max_total_ms * 1e-3) / 1e9
+
+
 def parse():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
@@ -61,6 +81,9 @@ def parse():
     p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
     p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
     p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
+    p.add_argument("--only", choices=["factor", "gemm"], default="factor",
+                   help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape)")
+    p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
     a = p.parse_args()
     a.m = a.m or a.n
     a.d = a.d or int(math.ceil(1.25 * a.b))
@@ -185,6 +208,36 @@ def run_reference(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ GEMM alone
+def run_gemm(a):
+    import torch
+
+    from paper_2507_00976_b300 import binding as B
+    M, N, K = a.gemm
+    g = torch.Generator(device="cuda")
+    g.manual_seed(a.seed)
+    A = torch.randn((K, M), generator=g, dtype=torch.float64, device="cuda").t()
+    Bm = torch.randn((N, K), generator=g, dtype=torch.float64, device="cuda").t()
+    C = torch.randn((N, M), generator=g, dtype=torch.float64, device="cuda").t()
+    ws = torch.empty(B.bqrrp_dgemm_workspace(M, N, K), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        B.bqrrp_dgemm("N", "N", -1.0, A, Bm, 1.0, C, workspace=ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        B.bqrrp_dgemm("N", "N", -1.0, A, Bm, 1.0, C, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+    print(json.dumps({"metric": "FP64 GEMM TFLOP/s (C -= A B)", "value": tf, "unit": "TFLOP/s", "ms_per_step": ms,
+                      "steps": a.steps, "warmup": a.warmup, "config": {"M": M, "N": N, "K": K},
+                      "frac_of_peak": tf / FP64_PEAK_TFLOPS}), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = parse()
@@ -193,6 +246,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, world, rank)
+        return
+    if a.only == "gemm":
+        run_gemm(a)
         return
 
     import torch
@@ -213,7 +269,7 @@ def main():
         torch.cuda.synchronize()
 
     m, n, b, d = a.m, a.n, a.b, a.d
-    seed = a.seed + 1000 * rank
+    seed = rank_seed(a.seed, rank)
     if a.family == "gaussian":
         A0 = W.gaussian_torch(m, n, seed)
     else:
@@ -262,13 +318,9 @@ def main():
     B.bqrrp_profile_enable(False)
     prof = B.bqrrp_profile_read()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     flops = canonical_flops(m, n)
-    value = flops * a.steps * world / (tot_ms * 1e-3) / 1e9
+    value = job_gflops(flops, a.steps, world, tot_ms)
 
     # ---------------- the library's own unpivoted QR on the same input
     qr = None
@@ -313,12 +365,8 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             ems.append(e0.elapsed_time(e1))
-        tot = sum(ems)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": flops * k_e2e * world / (tot * 1e-3) / 1e9, "unit": "GFLOP/s",
+        tot = max_over_ranks(sum(ems), dist, "cuda")
+        e2e = {"value": job_gflops(flops, k_e2e, world, tot), "unit": "GFLOP/s",
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * 16, "steps": k_e2e,
                "entry_point": "bqrrp_factor_host (pinned host buffers)"}
 

@@ -39,11 +39,11 @@ extern "C" {
 #define BQRRP_ETIMEOUT 4    /* a grid-wide barrier gave up waiting             */
 #define BQRRP_EUNSUPPORTED 5 /* shape outside the supported range             */
 
-/* Sketching operator kinds (Alg. 1 sample step, Sec. 4.2). */
+/* Sketching operator kinds (Alg. 1 sample step, Sec. 3.2). */
 #define BQRRP_SKETCH_DENSE 0   /* d x m, entries +-1 from Philox4x32-10          */
 #define BQRRP_SKETCH_SPARSE 1  /* d x m, nnz entries +-1 per column              */
 
-/* Panel factorizations for qr_tall (Sec. 2.3 / Sec. 4.5). */
+/* Panel factorizations for qr_tall (Sec. 2.3 / Sec. 3.5). */
 #define BQRRP_PANEL_CHOLQR 0   /* Alg. 3: preconditioned CholQR + reconstruction */
 #define BQRRP_PANEL_HQR 1      /* Householder QR of the panel                    */
 
@@ -56,11 +56,11 @@ typedef struct bqrrp_opts {
 
 /*
  * bqrrp_factor -- column-pivoted QR  A*P = Q*R  by BQRRP (Alg. 1 with Alg. 2
- * as qrcp_wide and Alg. 3 as qr_tall; Sec. 4 for the storage layout).
+ * as qrcp_wide and Alg. 3 as qr_tall; Sec. 3 for the storage layout).
  *
  *  m, n      rows and columns of A; 0 <= n <= m (m < n returns -1).
  *  A         device, m x n, column-major, leading dimension lda >= max(1,m).
- *            In: the matrix.  Out (GEQP3 format, Sec. 1.2): rows 0..rank-1 of
+ *            In: the matrix.  Out (GEQP3 format, Sec. 1.3): rows 0..rank-1 of
  *            the upper trapezoid hold R; below the diagonal of columns
  *            0..rank-1 the Householder vectors v_i (v_i(i) = 1 implicit).
  *            When rank < n the rows rank..m-1 of columns rank..n-1 are

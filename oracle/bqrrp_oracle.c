@@ -10,11 +10,11 @@
  * column-major arrays, with no blocking, fusion or reordering.
  *
  * Conventions: column-major, A(i,j) = A[i + j*lda], 0-based indices inside,
- * 1-based permutation vector on output (GEQP3 format, Sec. 1.2).
+ * 1-based permutation vector on output (GEQP3 format, Sec. 1.3).
  *
  * Readings of the paper that this file commits to (each is also a pin in the
  * tests):
- *  - the sketching operator is d x m (Sec. 4.2; Alg. 1 writes d x n);
+ *  - the sketching operator is d x m (Sec. 3.2; Alg. 1 writes d x n);
  *  - its entries are +-1 drawn from Philox4x32-10 (dense) or a sparse-sign
  *    operator with nnz nonzeros per column, both with unit scale (the paper
  *    says the variance is inessential, Alg. 1 footnote);
@@ -72,7 +72,7 @@ void bqrrp_ref_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sketching operators (Alg. 1 sample step; Sec. 4.2).  S is d x m, ld = d.   */
+/* Sketching operators (Alg. 1 sample step; Sec. 3.2).  S is d x m, ld = d.   */
 /* ------------------------------------------------------------------------ */
 
 /* Dense +-1: key = (seed lo, seed hi); for column j and row r the counter is
@@ -139,7 +139,7 @@ void bqrrp_ref_sketch_apply(int64_t d, int64_t m, int64_t n, const double* S,
 
 /* ------------------------------------------------------------------------ */
 /* Householder reflector in the LAPACK dlarfg convention (GEQRF/GEQP3 output */
-/* format of Sec. 1.2): H = I - tau*v*v^T, v(0) = 1, H*[alpha; x] = [beta;0].*/
+/* format of Sec. 1.3): H = I - tau*v*v^T, v(0) = 1, H*[alpha; x] = [beta;0].*/
 /* ------------------------------------------------------------------------ */
 static double house(int64_t len, double* x /* x[0]=alpha, x[1..] tail */, double* tau)
 {
@@ -363,7 +363,7 @@ void bqrrp_ref_orhr_col(int64_t rows, int64_t k, double* Q, int64_t ldq, double*
 }
 
 /* ------------------------------------------------------------------------ */
-/* BQRRP (Alg. 1), CholQR panel (Alg. 3) or Householder panel (Sec. 4.5).    */
+/* BQRRP (Alg. 1), CholQR panel (Alg. 3) or Householder panel (Sec. 3.5).    */
 /* ------------------------------------------------------------------------ */
 
 static int has_nonfinite(int64_t rows, int64_t cols, const double* X, int64_t ld)

@@ -312,6 +312,10 @@ def bqrrp_dgemm(transa, transb, alpha, A, B, beta, C, workspace=None, stream=Non
     return C
 
 
+def bqrrp_dgemm_workspace(M, N, K):
+    return int(lib().bqrrp_dgemm_workspace(M, N, K))
+
+
 def bqrrp_probe_fp64_peak(iters=2000, stream=None):
     return float(lib().bqrrp_probe_fp64_peak(iters, _stream(stream)))
 

@@ -429,7 +429,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         const i64 nc = n - cend;
         if (o.panel_kind == BQRRP_PANEL_HQR) {
             // Householder QR of all w panel columns, reflectors applied to the
-            // whole trailing block; only the first k are kept (Sec. 4.5).
+            // whole trailing block; only the first k are kept (Sec. 3.5).
             pr.begin(P_PANEL);
             BQ_TRY(geqrf_blocked(c, rows, N, Ap, lda, tau + s, B.Vqr, B.Tqr, B.W, B.W2, 64, w));
             if (k < w) {

@@ -3,7 +3,7 @@
 // Alg. 2's LU yields a swap sequence ipiv of s = min(N, d) steps with
 // ipiv[j] >= j, so the permutation J^sk it encodes moves at most 2s of the N
 // columns.  Instead of the paper's full out-of-place copy of M (Alg. 5 with
-// pointer ping-pong, Sec. 5.2), the moved positions are listed once and only
+// pointer ping-pong, Sec. 4.2), the moved positions are listed once and only
 // those columns are staged out (gather) and written back (scatter):
 // 2 * 2s * m * 16 bytes per iteration instead of m * N * 16, and no m x n
 // second buffer.  The result equals Alg. 5's out(:, t) = in(:, J[t]).

@@ -2,7 +2,7 @@
 
 This module holds input generation only -- none of the factorization's
 arithmetic -- so that the CUDA path and the CPU oracle can be fed the very same
-bytes.  Families (paper Sec. 1.3 and Sec. 6):
+bytes.  Families (paper Sec. 1.4 and Sec. 6):
 
 * ``gaussian``: iid N(0,1) entries (the paper's performance matrices);
 * ``spectrum``: U diag(sigma) V^T with U, V orthonormal from the QR of seeded

@@ -1,6 +1,6 @@
 """Numpy checkers for GEQP3-format factorizations (test code only).
 
-Everything here is written from the output-format definition of Sec. 1.2:
+Everything here is written from the output-format definition of Sec. 1.3:
 Q = H_1 H_2 ... H_l with H_i = I - tau_i v_i v_i^T, v_i(i) = 1, v_i(:i) = 0 and
 v_i(i+1:) stored below the diagonal; R in the upper trapezoid; J 1-based.
 """
