@@ -81,8 +81,9 @@ def parse():
     p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
     p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
     p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
-    p.add_argument("--only", choices=["factor", "gemm"], default="factor",
-                   help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape)")
+    p.add_argument("--only", choices=["factor", "gemm", "geqrf"], default="factor",
+                   help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape); "
+                        "geqrf: time the library's own unpivoted QR alone on the m x n input")
     p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
     a = p.parse_args()
     a.m = a.m or a.n
@@ -238,6 +239,35 @@ def run_gemm(a):
                       "frac_of_peak": tf / FP64_PEAK_TFLOPS}), flush=True)
 
 
+def run_geqrf(a):
+    import torch
+
+    import paper_2507_00976_b300 as bq
+    from paper_2507_00976_b300 import binding as B
+    from paper_2507_00976_b300 import workloads as W
+    m, n = a.m, a.n
+    A0 = W.gaussian_torch(m, n, a.seed)
+    A = bq.colmajor_empty(m, n)
+    tau = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = torch.empty(B.bqrrp_geqrf_workspace(m, n, 0), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = []
+    for i in range(a.warmup + a.steps):
+        A.copy_(A0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bqrrp_geqrf(A, 0, tau=tau, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= a.warmup:
+            ms.append(e0.elapsed_time(e1))
+    t = statistics.mean(ms)
+    print(json.dumps({"metric": "own unpivoted QR GFLOP/s (2mn^2-2n^3/3)", "value": canonical_flops(m, n) / (t * 1e-3) / 1e9,
+                      "unit": "GFLOP/s", "ms_per_step": t, "steps": a.steps, "warmup": a.warmup,
+                      "config": {"m": m, "n": n}}), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = parse()
@@ -249,6 +279,9 @@ def main():
         return
     if a.only == "gemm":
         run_gemm(a)
+        return
+    if a.only == "geqrf":
+        run_geqrf(a)
         return
 
     import torch

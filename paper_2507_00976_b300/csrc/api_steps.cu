@@ -52,13 +52,14 @@ int finish(const Ctx& c) {
 }
 
 struct QrcpWs {
-    double *X, *stage, *V, *T, *W, *W2, *tau;
+    double *X, *Ub, *stage, *V, *T, *W, *W2, *tau;
     i64 *pos, *src, *cnt;
 };
 
 void carve_qrcp(Arena& ar, i64 d, i64 N, QrcpWs* q) {
     const i64 mm = imax(1, imin(N, 2 * imin(d, N)));
     q->X = ar.take<double>((size_t)d * N);
+    q->Ub = ar.take<double>((size_t)d * imin(d, N));
     q->stage = ar.take<double>((size_t)d * mm);
     q->V = ar.take<double>((size_t)d * 64);
     q->T = ar.take<double>(64 * 64);
@@ -125,10 +126,7 @@ int bqrrp_qrcp_wide(int64_t d, int64_t N, double* Msk, int64_t ldsk, int64_t* Js
     const i64 steps = imin(N, d);
     BQ_TRY(getrf_pivots(c, N, d, q.X, d, ipiv));
     BQ_TRY(piv_transform_moved(c, N, steps, ipiv, Jsk, &c.st->sk_nonfinite, q.pos, q.src, q.cnt));
-    const i64 mm = imin(N, 2 * steps);
-    BQ_TRY(gather_cols(c, d, Msk, ldsk, q.pos, q.src, q.cnt, mm, q.stage, d));
-    BQ_TRY(geqrf_blocked(c, d, N, Msk, ldsk, q.tau, q.V, q.T, q.W, q.W2, 64));
-    BQ_TRY(set_zero_below(c, d, N, Msk, ldsk));
+    BQ_TRY(rsk_from_lu(c, d, N, q.X, d, Msk, ldsk, q.Ub, q.tau, q.V, q.T, q.W, q.W2));
     return finish(c);
 }
 

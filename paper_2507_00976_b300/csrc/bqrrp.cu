@@ -151,19 +151,25 @@ __global__ void plus_one_kernel(i64 n, const i64* J, i64* jpvt) {
 
 // tri_rank (Sec. 2.2, reading): k = largest j <= w with |Rsk(t,t)| > 10 d u r00
 // for all t < j, r00 = |Rsk(0,0)| of the first iteration.
-__global__ void tri_rank_kernel(DevStatus* st, const double* Rsk, i64 ldr, i64 w, i64 d, int first) {
-    if (threadIdx.x != 0) return;
-    if (first) st->r00 = fabs(Rsk[0]);
-    const double r00 = st->r00;
+__global__ void __launch_bounds__(1024) tri_rank_kernel(DevStatus* st, const double* Rsk, i64 ldr, i64 w, i64 d,
+                                                        int first) {
+    __shared__ double r00s;
+    __shared__ int firstbad;
+    if (threadIdx.x == 0) {
+        if (first) st->r00 = fabs(Rsk[0]);
+        r00s = st->r00;
+        firstbad = INT_MAX;
+    }
+    __syncthreads();
+    const double r00 = r00s;
     const double thr = 10.0 * (double)d * kUnitRoundoff * r00;
-    i64 k = 0;
-    if (r00 > 0.0 && isfinite(r00))
-        while (k < w) {
-            const double v = Rsk[k + k * ldr];
-            if (!isfinite(v) || !(fabs(v) > thr)) break;
-            ++k;
-        }
-    st->k = k;
+    const bool scale_ok = r00 > 0.0 && isfinite(r00);
+    for (i64 t = threadIdx.x; t < w; t += blockDim.x) {
+        const double v = Rsk[t + t * ldr];
+        if (!isfinite(v) || !(fabs(v) > thr)) atomicMin(&firstbad, (int)t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->k = scale_ok ? (firstbad < w ? (i64)firstbad : w) : 0;
 }
 
 // st->zero_col <- 1 if any entry of the column is nonzero (early-exit test)
@@ -218,7 +224,7 @@ inline unsigned gblocks(const Ctx& c, i64 total) { return (unsigned)imax(1, imin
 // ------------------------------------------------------------------ workspace plan
 struct Bufs {
     DevStatus* st;
-    double *Msk, *Xlu, *stage, *Ypan, *Vqr, *Tqr, *W, *W2, *G, *U, *Tb, *R11, *Z, *D, *sktau, *splitk, *coop;
+    double *Msk, *Xlu, *Ub, *stage, *Ypan, *Vqr, *Tqr, *W, *W2, *G, *U, *Tb, *R11, *Z, *D, *sktau, *splitk, *coop;
     i64 *ipiv, *Jsk, *pos, *src, *cnt, *J, *Jstage;
     char* sparse_ws;
     size_t sparse_bytes, splitk_elems, coop_elems;
@@ -234,6 +240,7 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
     B->st = ar.take<DevStatus>(1);
     B->Msk = ar.take<double>((size_t)d * n);
     B->Xlu = ar.take<double>((size_t)d * n);
+    B->Ub = ar.take<double>((size_t)d * imin(d, n));
     B->stage = ar.take<double>((size_t)B->ldst * B->max_moved);
     B->Ypan = ar.take<double>((size_t)m * bb);
     B->Vqr = ar.take<double>((size_t)imax(m, d) * 64);
@@ -406,10 +413,8 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         // ---- gather + Householder QR of the sketch, tri_rank
         pr.begin(P_SKQR);
         const i64 mm = imin(N, 2 * steps);
-        BQ_TRY(gather_cols(c, d, Ssk, d, B.pos, B.src, B.cnt, mm, B.stage, d));
-        BQ_TRY(geqrf_blocked(c, d, N, Ssk, d, B.sktau, B.Vqr, B.Tqr, B.W, B.W2, 64));
-        BQ_TRY(set_zero_below(c, d, N, Ssk, d));
-        tri_rank_kernel<<<1, 32, 0, c.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
+        BQ_TRY(rsk_from_lu(c, d, N, B.Xlu, d, Ssk, d, B.Ub, B.sktau, B.Vqr, B.Tqr, B.W, B.W2));
+        tri_rank_kernel<<<1, 1024, 0, c.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
         BQ_LAUNCH_CHECK();
         pr.flops(P_SKQR, geqrf_flops((double)d, (double)N));
 

@@ -138,10 +138,15 @@ __host__ __device__ inline double sketch_dense_entry(uint64_t seed, i64 r, i64 j
 }
 
 // ------------------------------------------------------------------ grid barrier
-// Sense-counting barrier for cooperative launches (all CTAs co-resident).
-// Every wait is bounded: after `kSpinLimit` polls the CTA records a timeout in
-// the status block and the barrier returns false; callers then exit.
-constexpr unsigned long long kSpinLimit = 1ull << 26;
+// Barrier for cooperative launches (all CTAs co-resident).  The arrival
+// counter only grows within a launch (the host zeroes it before every
+// cooperative launch): arrival number a of a grid of n CTAs belongs to epoch
+// a / n and waits until the counter reaches (a / n + 1) * n.  Arrival is a
+// release, polling an acquire (thread 0 of each CTA, bracketed by
+// __syncthreads).  Every wait is bounded: after kSpinLimit polls the CTA
+// records a timeout in the status block and the barrier returns false;
+// callers then exit.
+constexpr unsigned long long kSpinLimit = 1ull << 28;   // polls of ~20 ns: a few seconds
 
 __device__ inline unsigned int ld_acquire_u32(const unsigned int* p) {
     unsigned int v;
@@ -155,26 +160,17 @@ __device__ inline bool grid_barrier(DevStatus* st, unsigned int nblocks) {
     if (threadIdx.x == 0) {
         int ok = 1;
         unsigned int* cnt = &st->bar.count;
-        unsigned int* gen = &st->bar.gen;
-        const unsigned int g = ld_acquire_u32(gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(cnt, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(cnt, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (ld_acquire_u32(gen) == g) {
-                if (++spins > kSpinLimit || *((volatile int*)&st->err_timeout)) {
-                    atomicExch(&st->err_timeout, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        unsigned int a;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(a) : "l"(cnt) : "memory");
+        const unsigned int target = (a / nblocks + 1) * nblocks;
+        unsigned long long spins = 0;
+        while ((int)(ld_acquire_u32(cnt) - target) < 0) {
+            if (++spins > kSpinLimit || ((spins & 1023) == 0 && *((volatile int*)&st->err_timeout))) {
+                atomicExch(&st->err_timeout, 1);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -225,6 +221,8 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* X, i64 ldx, i64* ipiv); // 
 int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* tau, double* V,
                   double* T, double* W, double* W2, i64 nb, i64 kstop = -1);
 int coop_scratch_elems(i64 nb, int grid, size_t* elems);
+int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 ldsk, double* Ub, double* tau,
+                double* V, double* T, double* W, double* W2);
 
 // perm.cu
 int piv_transform_moved(const Ctx& c, i64 N, i64 steps, const i64* ipiv, i64* Jsk, const int* identity_flag,

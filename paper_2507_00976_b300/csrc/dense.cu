@@ -20,7 +20,7 @@ constexpr int NBD = 64;   // diagonal block size
 // unit != 0; then only the strictly upper part of R is read).  One thread per
 // row of X, the triangle of R in shared memory.
 template <int NB>
-__global__ void __launch_bounds__(128) trsm_small_kernel(i64 rows, int nb, View R, View X, int unit) {
+__global__ void __launch_bounds__(64) trsm_small_kernel(i64 rows, int nb, View R, View X, int unit) {
     __shared__ double Rs[NB][NB + 1];
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int t = e % NB, j = e / NB;
@@ -46,6 +46,40 @@ __global__ void __launch_bounds__(128) trsm_small_kernel(i64 rows, int nb, View 
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if (j < nb) *X.at(i, j) = x[j];
+}
+
+// Same solve with one warp per row for short, wide problems: lane l holds
+// x[j] for j = l and l + 32; column j's inner product is split across lanes
+// and combined with a fixed shuffle tree, so a row costs ~nb shuffle rounds
+// instead of an nb^2/2-long dependent DFMA chain on one thread.
+__global__ void __launch_bounds__(256) trsm_warp_kernel(i64 rows, int nb, View R, View X, int unit) {
+    __shared__ double Rs[NBD][NBD + 1];
+    for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
+        const int t = e % NBD, j = e / NBD;
+        double v = 0.0;
+        if (t < nb && j < nb && t <= j) v = (t == j && unit) ? 1.0 : *R.at(t, j);
+        Rs[t][j] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const i64 i = (i64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= rows) return;
+    double x0 = (lane < nb) ? *X.at(i, lane) : 0.0;
+    double x1 = (lane + 32 < nb) ? *X.at(i, lane + 32) : 0.0;
+    for (int j = 0; j < nb; ++j) {
+        double p = 0.0;
+        if (lane < j) p = x0 * Rs[lane][j];
+        if (lane + 32 < j) p = fma(x1, Rs[lane + 32][j], p);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (j < 32) {
+            if (lane == j) x0 = unit ? (x0 - p) : (x0 - p) / Rs[j][j];
+        } else {
+            if (lane == j - 32) x1 = unit ? (x1 - p) : (x1 - p) / Rs[j][j];
+        }
+    }
+    if (lane < nb) *X.at(i, lane) = x0;
+    if (lane + 32 < nb) *X.at(i, lane + 32) = x1;
 }
 
 // Upper Cholesky of one nb x nb diagonal block in place (G = R^T R), reading
@@ -166,8 +200,13 @@ int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit) {
     if (rows <= 0 || k <= 0) return 0;
     for (i64 jb = 0; jb < k; jb += NBD) {
         const int nb = (int)imin(NBD, k - jb);
-        const int blocks = (int)cdiv(rows, 128);
-        trsm_small_kernel<NBD><<<blocks, 128, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb), unit ? 1 : 0);
+        if (rows <= 4096) {
+            trsm_warp_kernel<<<(unsigned)cdiv(rows, 8), 256, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb),
+                                                                         unit ? 1 : 0);
+        } else {
+            trsm_small_kernel<NBD><<<(unsigned)cdiv(rows, 64), 64, 0, c.stream>>>(rows, nb, R.sub(jb, jb),
+                                                                                X.sub(0, jb), unit ? 1 : 0);
+        }
         BQ_LAUNCH_CHECK();
         if (jb + nb < k) {
             // X(:, jb+nb:k) -= X(:, jb:jb+nb) * R(jb:jb+nb, jb+nb:k)

@@ -176,9 +176,9 @@ int launch(const Ctx& c, GemmArgs a) {
     int splits = 1;
     const i64 tiles = tm * tn;
     const i64 target = 4LL * c.dev.sms;
-    if (tiles < target && a.K >= 4 * 128 && c.splitk != nullptr) {
+    if (tiles < target && a.K >= 128 && c.splitk != nullptr) {
         i64 s = cdiv(target, tiles);
-        s = imin(s, a.K / 128);
+        s = imin(s, a.K / 64);
         s = imin(s, 64);
         const i64 fit = (i64)(c.splitk_elems / (size_t)(a.M * a.N));
         s = imin(s, fit);

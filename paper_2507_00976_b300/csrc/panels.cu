@@ -17,6 +17,8 @@
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -125,13 +127,22 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         // (3)
         if (!grid_barrier(a.st, G)) return;
         // (4) winner over all CTAs (fixed rule: largest value, then smallest index)
-        Best w{-1.0, -1};
-        for (int q = tid; q < G; q += NT) {
-            Best y{__ldcg(&a.cand_v[par * G + q]), (i64)__ldcg(&a.cand_t[par * G + q])};
-            if (y.t >= 0) w = better(w, y);
+        if (tid < 32) {
+            Best w{-1.0, -1};
+#pragma unroll 5
+            for (int q = tid; q < G; q += 32) {
+                Best y{__ldcg(&a.cand_v[par * G + q]), (i64)__ldcg(&a.cand_t[par * G + q])};
+                if (y.t >= 0) w = better(w, y);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                Best y;
+                y.v = __shfl_down_sync(0xffffffffu, w.v, o);
+                y.t = __shfl_down_sync(0xffffffffu, w.t, o);
+                w = better(w, y);
+            }
+            if (tid == 0) s_p = w.t;
         }
-        w = block_best(w);
-        if (tid == 0) s_p = w.t;
         __syncthreads();
         const i64 p = s_p;
         // locate the winning CTA from the row index
@@ -167,12 +178,15 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
     }
 }
 
-// Apply the panel's interchanges to sketch rows [r0, d): swap columns jb+j and
-// ipiv[jb+j] in order.  One thread per row.
-__global__ void lu_swap_rows_kernel(i64 r0, i64 d, i64 jb, int steps, const i64* __restrict__ ipiv, double* Sk,
+// Apply the panel's interchanges to every sketch row outside the panel rows
+// [jb, jb+pw): swap columns jb+j and ipiv[jb+j] in order (LAPACK applies them to
+// the L part on the left and the trailing part on the right alike).  One
+// thread per row.
+__global__ void lu_swap_rows_kernel(i64 pw, i64 d, i64 jb, int steps, const i64* __restrict__ ipiv, double* Sk,
                                     i64 ldsk) {
-    const i64 r = r0 + (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d) return;
+    const i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= d - pw) return;
+    const i64 r = (q < jb) ? q : q + pw;
     for (int j = 0; j < steps; ++j) {
         const i64 a = jb + j, p = ipiv[jb + j];
         if (p != a) {
@@ -205,6 +219,7 @@ struct HhArgs {
 __global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
     extern __shared__ double slab[];   // [pw][Rp]
     __shared__ double red[NT / 32];
+    __shared__ double red4[4][64];
     __shared__ double wv[64];
     __shared__ double s_tau, s_beta, s_scal;
     __shared__ double Ts[64][65];
@@ -244,6 +259,7 @@ __global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
         // (3) reflector (every CTA computes the same numbers in the same order)
         if (warp == 0) {
             double xs = 0.0;
+#pragma unroll 5
             for (int q = lane; q < G; q += 32) xs += __ldcg(&a.part1[q]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) xs += __shfl_down_sync(0xffffffffu, xs, o);
@@ -287,13 +303,20 @@ __global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
             if (lane == 0) a.part2[(size_t)g * pw + c] = acc;
         }
         if (!grid_barrier(a.st, G)) return;
-        // (7) reduce partial dots in a fixed order, then update owned rows
-        for (int c = j + 1 + warp; c < pw; c += NT / 32) {
+        // (7) reduce partial dots in a fixed order: thread (group g4, column cl)
+        // sums sources q = g4, g4 + 4, ... with many loads in flight, then the
+        // four group sums are added in group order.
+        {
+            const int cl = tid & 63, g4 = tid >> 6;
+            const int c = j + 1 + cl;
             double acc = 0.0;
-            for (int q = lane; q < G; q += 32) acc += __ldcg(&a.part2[(size_t)q * pw + c]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) wv[c] = acc * tau;
+            if (c < pw) {
+#pragma unroll 8
+                for (int q = g4; q < G; q += 4) acc += __ldcg(&a.part2[(size_t)q * pw + c]);
+            }
+            red4[g4][cl] = acc;
+            __syncthreads();
+            if (tid < pw - j - 1) wv[j + 1 + tid] = (((red4[0][tid] + red4[1][tid]) + red4[2][tid]) + red4[3][tid]) * tau;
         }
         __syncthreads();
         for (int e = tid; e < (pw - j - 1) * (nloc - rv > 0 ? nloc - rv : 0); e += NT) {
@@ -343,12 +366,22 @@ __global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
     if (g != 0) return;
     // T by the larft recurrence: T(j,j) = tau_j, T(0:j,j) = -tau_j T(0:j,0:j) G(0:j,j)
     for (int e = tid; e < 64 * 65; e += NT) (&Ts[0][0])[e] = 0.0;
+    // Gram into shared memory (the slab is free now when it is large enough)
+    double* Gs = slab;
+    const bool gsm = (size_t)pw * pw <= (size_t)pw * a.Rp;
+    if (gsm)
+        for (int e = tid; e < pw * pw; e += NT) Gs[e] = __ldcg(&a.gsum[e]);
+    __shared__ double taus[64];
+    for (int j = tid; j < pw; j += NT) taus[j] = (j < jmax) ? __ldcg(&a.tau[j]) : 0.0;
     __syncthreads();
     for (int j = 0; j < pw; ++j) {
-        const double tj = (j < jmax) ? __ldcg(&a.tau[j]) : 0.0;
+        const double tj = taus[j];
         for (int i = tid; i < j; i += NT) {
             double z = 0.0;
-            for (int l = i; l < j; ++l) z = fma(Ts[i][l], __ldcg(&a.gsum[l + j * pw]), z);
+            if (gsm)
+                for (int l = i; l < j; ++l) z = fma(Ts[i][l], Gs[l + j * pw], z);
+            else
+                for (int l = i; l < j; ++l) z = fma(Ts[i][l], __ldcg(&a.gsum[l + j * pw]), z);
             Ts[i][j] = -tj * z;
         }
         if (tid == 0) Ts[j][j] = tj;
@@ -358,6 +391,166 @@ __global__ void __launch_bounds__(NT) hh_panel_kernel(HhArgs a) {
         const int i = e % pw, j = e / pw;
         a.T[i + j * a.ldt] = Ts[i][j];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Householder panel on one thread-block cluster (short panels, e.g. the d-row
+// sketch): same arithmetic and reduction order as hh_panel_kernel, but the
+// per-CTA partial sums are read through distributed shared memory and the two
+// exchanges per column use the hardware cluster barrier.
+namespace cg = cooperative_groups;
+
+__global__ void __launch_bounds__(NT) hh_panel_cluster_kernel(HhArgs a) {
+    extern __shared__ double slab[];   // [pw][Rp], then the Gram partial [pw*pw]
+    __shared__ double red[NT / 32];
+    __shared__ double wv[64];
+    __shared__ double part2_s[64];
+    __shared__ double part1_s, alpha_s;
+    __shared__ double s_tau, s_beta, s_scal;
+    __shared__ double Ts[64][65];
+    cg::cluster_group cl = cg::this_cluster();
+    const int G = (int)cl.num_blocks(), g = (int)cl.block_rank(), tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const i64 r0 = (i64)g * a.R;
+    const i64 r1 = (r0 + a.R < a.rows) ? r0 + a.R : a.rows;
+    const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
+    const int pw = a.pw;
+    double* gram = slab + (size_t)pw * a.Rp;
+
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int rl = e % nloc, c = e / nloc;
+        slab[c * a.Rp + rl] = a.A[(r0 + rl) + c * a.lda];
+    }
+    __syncthreads();
+    const int jmax = (a.rows < pw) ? (int)a.rows : pw;
+    for (int j = 0; j < jmax; ++j) {
+        double s = 0.0;
+        const int rb = (j + 1 > r0) ? (int)(j + 1 - r0) : 0;
+        for (int rl = rb + tid; rl < nloc; rl += NT) {
+            const double x = slab[j * a.Rp + rl];
+            s = fma(x, x, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NT / 32; ++q) t += red[q];
+            part1_s = t;
+            if (j >= r0 && j < r1) alpha_s = slab[j * a.Rp + (j - r0)];
+        }
+        cl.sync();
+        if (warp == 0) {
+            double xs = 0.0;
+            for (int q = lane; q < G; q += 32) xs += *cl.map_shared_rank(&part1_s, q);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) xs += __shfl_down_sync(0xffffffffu, xs, o);
+            if (lane == 0) {
+                const double al = *cl.map_shared_rank(&alpha_s, (int)(j / a.R));
+                if (xs == 0.0) {
+                    s_tau = 0.0; s_beta = al; s_scal = 1.0;
+                } else {
+                    const double nrm = sqrt(fma(al, al, xs));
+                    const double be = (al >= 0.0) ? -nrm : nrm;
+                    s_tau = (be - al) / be;
+                    s_beta = be;
+                    s_scal = 1.0 / (al - be);
+                }
+                if (g == 0) a.tau[j] = s_tau;
+            }
+        }
+        __syncthreads();
+        const double tau = s_tau;
+        if (tau != 0.0) {
+            const double scal = s_scal;
+            for (int rl = rb + tid; rl < nloc; rl += NT) slab[j * a.Rp + rl] *= scal;
+            if (tid == 0 && j >= r0 && j < r1) slab[j * a.Rp + (j - r0)] = s_beta;
+        }
+        __syncthreads();
+        if (tau == 0.0 || j + 1 >= pw) {
+            cl.sync();   // keep the two-exchanges-per-column rhythm on every CTA
+            continue;
+        }
+        const int rv = (j > r0) ? (int)(j - r0) : 0;
+        for (int c = j + 1 + warp; c < pw; c += NT / 32) {
+            double acc = 0.0;
+            for (int rl = rv + lane; rl < nloc; rl += 32) {
+                const i64 r = r0 + rl;
+                const double v = (r == j) ? 1.0 : slab[j * a.Rp + rl];
+                acc = fma(v, slab[c * a.Rp + rl], acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) part2_s[c] = acc;
+        }
+        cl.sync();
+        for (int c = j + 1 + warp; c < pw; c += NT / 32) {
+            double acc = 0.0;
+            for (int q = lane; q < G; q += 32) acc += *cl.map_shared_rank(&part2_s[c], q);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) wv[c] = acc * tau;
+        }
+        __syncthreads();
+        const int span = nloc - rv;
+        for (int e = tid; span > 0 && e < (pw - j - 1) * span; e += NT) {
+            const int rl = rv + e % span, c = j + 1 + e / span;
+            const i64 r = r0 + rl;
+            const double v = (r == j) ? 1.0 : slab[j * a.Rp + rl];
+            slab[c * a.Rp + rl] = fma(-wv[c], v, slab[c * a.Rp + rl]);
+        }
+        __syncthreads();
+    }
+    if (g == 0)
+        for (int j = jmax + tid; j < pw; j += NT) a.tau[j] = 0.0;
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int rl = e % nloc, c = e / nloc;
+        const i64 r = r0 + rl;
+        const double x = slab[c * a.Rp + rl];
+        a.A[r + c * a.lda] = x;
+        a.V[r + c * a.ldv] = (c >= jmax) ? 0.0 : (r > c ? x : (r == c ? 1.0 : 0.0));
+    }
+    for (int e = tid; e < pw * pw; e += NT) {
+        const int i = e % pw, j = e / pw;
+        double acc = 0.0;
+        if (i <= j && j < jmax) {
+            const int rs = (j > r0) ? (int)(j - r0) : 0;
+            for (int rl = rs; rl < nloc; ++rl) {
+                const i64 r = r0 + rl;
+                const double vi = (r > i) ? slab[i * a.Rp + rl] : (r == i ? 1.0 : 0.0);
+                const double vj = (r > j) ? slab[j * a.Rp + rl] : (r == j ? 1.0 : 0.0);
+                acc = fma(vi, vj, acc);
+            }
+        }
+        gram[e] = acc;
+    }
+    cl.sync();
+    if (g == 0) {
+        for (int e = tid; e < 64 * 65; e += NT) (&Ts[0][0])[e] = 0.0;
+        // reduce the Gram partials in rank order into this CTA's slab
+        for (int e = tid; e < pw * pw; e += NT) {
+            double acc = gram[e];
+            for (int q = 1; q < G; ++q) acc += *cl.map_shared_rank(&gram[e], q);
+            gram[e] = acc;
+        }
+        __syncthreads();
+        for (int j = 0; j < pw; ++j) {
+            const double tj = (j < jmax) ? a.tau[j] : 0.0;
+            for (int i = tid; i < j; i += NT) {
+                double z = 0.0;
+                for (int l = i; l < j; ++l) z = fma(Ts[i][l], gram[l + j * pw], z);
+                Ts[i][j] = -tj * z;
+            }
+            if (tid == 0) Ts[j][j] = tj;
+            __syncthreads();
+        }
+        for (int e = tid; e < pw * pw; e += NT) {
+            const int i = e % pw, j = e / pw;
+            a.T[i + j * a.ldt] = Ts[i][j];
+        }
+    }
+    cl.sync();   // peers' shared memory stays alive until rank 0 has read it
 }
 
 int coop_grid(const void* kernel, size_t smem, const Ctx& c, int want) {
@@ -381,6 +574,11 @@ int coop_scratch_elems(i64 nb, int grid, size_t* elems) {
 
 static int launch_coop(const Ctx& c, const void* kernel, int grid, size_t smem, void* args) {
     void* kargs[] = {args};
+    // the barrier's arrival counter starts from zero in every launch
+    if (cudaMemsetAsync(&c.st->bar, 0, sizeof(GridBar), c.stream) != cudaSuccess) {
+        set_error("cooperative launch: resetting the barrier failed");
+        return BQRRP_ECUDA;
+    }
     count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(NT), kargs, smem, c.stream);
     if (e != cudaSuccess) {
@@ -440,18 +638,68 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
         a.cur_row = c.coop + 4 * G + 2 * (size_t)G * pw;
         BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));
         const i64 below = d - (jb + pw);
-        if (below > 0) {
-            lu_swap_rows_kernel<<<(unsigned)cdiv(below, 128), 128, 0, c.stream>>>(jb + pw, d, jb, st, ipiv, Sk, ldsk);
+        if (d - pw > 0) {
+            lu_swap_rows_kernel<<<(unsigned)cdiv(d - pw, 128), 128, 0, c.stream>>>(pw, d, jb, st, ipiv, Sk, ldsk);
             BQ_LAUNCH_CHECK();
         }
-        if (jb + st >= steps) break;
         if (below > 0) {
-            // U12^T = Sk(jb+pw:d, jb:jb+pw) * L11^{-T}; L11^T = unit upper part of Sk(jb:jb+pw, jb:jb+pw)
-            BQ_TRY(trsm_ru(c, below, pw, Skv.sub(jb, jb), Skv.sub(jb + pw, jb), true));
+            // U12^T = Sk(jb+pw:d, jb:jb+st) * L11^{-T}; L11^T = unit upper part of Sk(jb:jb+st, jb:jb+st).
+            // Needed even after the last pivot step (N < d): R^sk is formed from the complete U.
+            BQ_TRY(trsm_ru(c, below, st, Skv.sub(jb, jb), Skv.sub(jb + pw, jb), true));
             // trailing: Sk(jb+pw:d, jb+pw:N) -= U12^T * L21^T
-            BQ_TRY(dgemm(c, false, false, below, N - jb - pw, pw, -1.0, Sk + (jb + pw) + jb * ldsk, ldsk,
-                         Sk + jb + (jb + pw) * ldsk, ldsk, 1.0, Sk + (jb + pw) + (jb + pw) * ldsk, ldsk));
+            if (jb + st < steps)
+                BQ_TRY(dgemm(c, false, false, below, N - jb - pw, pw, -1.0, Sk + (jb + pw) + jb * ldsk, ldsk,
+                             Sk + jb + (jb + pw) * ldsk, ldsk, 1.0, Sk + (jb + pw) + (jb + pw) * ldsk, ldsk));
         }
+        if (jb + st >= steps) break;
+    }
+    return 0;
+}
+
+constexpr i64 kClusterRowsMax = 16 * 280;   // 16 CTAs x 280 rows x 64 columns fit shared memory
+
+// Householder panel (prow x pw) on one cluster of up to 16 CTAs.  Returns 0 on
+// success, -1 if the cluster cannot be launched (the caller falls back to the
+// cooperative grid kernel), or an error code.
+static int hh_panel_cluster(const Ctx& c, i64 prow, int pw, double* Ap, i64 lda, double* tau, double* V, i64 ldv,
+                            double* T, i64 ldt) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
+        attr_set = true;
+    }
+    int C = (int)imin(16, imax(1, cdiv(prow, 32)));
+    i64 R = cdiv(prow, C);
+    C = (int)cdiv(prow, R);
+    const size_t smem = ((size_t)pw * (size_t)(R | 1) + (size_t)pw * pw) * sizeof(double);
+    if (smem > (size_t)kMaxSmemHh) return -1;
+    HhArgs a{};
+    a.rows = prow; a.lda = lda; a.ldv = ldv; a.ldt = ldt; a.pw = pw; a.R = (int)R; a.Rp = (int)(R | 1);
+    a.A = Ap; a.tau = tau; a.V = V; a.T = T; a.st = c.st;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launch();
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, hh_panel_cluster_kernel, a);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear the launch error; the grid kernel takes over
+        static bool logged = false;
+        if (!logged && getenv("BQRRP_LOG")) {
+            fprintf(stderr, "bqrrp: cluster launch (%d CTAs, %zu B smem) failed: %s; using the grid kernel\n", C,
+                    smem, cudaGetErrorString(e));
+            logged = true;
+        }
+        return -1;
     }
     return 0;
 }
@@ -480,6 +728,12 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
     for (i64 jb = 0; jb < kk; jb += nb) {
         const int pw = (int)imin(nb, kk - jb);
         const i64 prow = rows - jb;
+        if (prow <= kClusterRowsMax) {
+            const int rc = hh_panel_cluster(c, prow, pw, A + jb + jb * lda, lda, tau + jb, V, rows, T, nb);
+            if (rc == 0) goto trailing;
+            if (rc != -1) return rc;   // -1: cluster launch not possible, use the grid kernel
+        }
+        {
         int G = (int)imin(cdiv(prow, 32), Gmax_all);
         i64 R = cdiv(prow, G);
         size_t smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
@@ -505,6 +759,8 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
         a.gpart = c.coop + G + 8 + (size_t)G * pw;
         a.gsum = a.gpart + (size_t)G * pw * pw;
         BQ_TRY(launch_coop(c, (const void*)hh_panel_kernel, G, smem, &a));
+        }
+    trailing:
         const i64 nc = cols - jb - pw;
         if (nc > 0) {
             double* C = A + jb + (jb + pw) * lda;
@@ -512,6 +768,51 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
             BQ_TRY(dgemm(c, true, false, pw, nc, pw, 1.0, T, nb, W, nb, 0.0, W2, nb));
             BQ_TRY(dgemm(c, false, false, prow, nc, pw, -1.0, V, rows, W2, nb, 1.0, C, lda));
         }
+    }
+    return 0;
+}
+
+namespace {
+// From the LU factors held in X (Sk layout, d x N, ld ldx, all interchanges
+// applied): U^T (d x s lower trapezoid, s = min(N, d)) into Ub, and X itself
+// becomes L^T (s x N unit upper trapezoid).
+__global__ void lu_split_kernel(i64 d, i64 s, i64 N, double* X, i64 ldx, double* Ub, i64 ldu) {
+    const i64 total = d * N;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 j = e % d, t = e / d;
+        const double x = X[j + t * ldx];
+        if (t < s) Ub[j + t * ldu] = (j >= t) ? x : 0.0;
+        if (j < s) X[j + t * ldx] = (t > j) ? x : (t == j ? 1.0 : 0.0);
+    }
+}
+
+__global__ void zero_rows_kernel(i64 r0, i64 r1, i64 N, double* X, i64 ldx) {
+    const i64 h = r1 - r0;
+    const i64 total = h * N;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x)
+        X[r0 + e % h + (e / h) * ldx] = 0.0;
+}
+}  // namespace
+
+// R^sk of Alg. 2 from the LU factors: the permuted sketch is U^T L^T, so with
+// U^T = Q1 R1 (Householder QR of a d x s matrix) its R factor is R1 L^T.  This
+// is the R of GEQRF on the permuted sketch up to row signs (and rounding); the
+// row signs cancel in everything BQRRP derives from R^sk (R11, Y, T) and leave
+// the next LU's pivots unchanged.  Writes R^sk (zeros below the diagonal) into
+// Sk (d x N, ld ldsk); X (the LU factors) is consumed.
+int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 ldsk, double* Ub, double* tau,
+                double* V, double* T, double* W, double* W2) {
+    const i64 s = imin(N, d);
+    if (s <= 0) return 0;
+    const unsigned blocks = (unsigned)imax(1, imin(cdiv(d * N, 256), 8LL * c.dev.sms));
+    lu_split_kernel<<<blocks, 256, 0, c.stream>>>(d, s, N, X, ldx, Ub, d);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
+    BQ_TRY(set_zero_below(c, s, s, Ub, d));
+    BQ_TRY(dgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk));
+    if (s < d) {
+        zero_rows_kernel<<<blocks, 256, 0, c.stream>>>(s, d, N, Sk, ldsk);
+        BQ_LAUNCH_CHECK();
     }
     return 0;
 }

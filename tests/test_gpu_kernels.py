@@ -114,8 +114,13 @@ def test_qrcp_wide_pivots_bitexact_and_rsk(d, N):
     Ro, _ = oracle.geqrf(Msk0[:, J_o])
     Ro = np.triu(Ro)
     R = np_(Md)
-    assert np.allclose(np.tril(R, -1), 0)
-    assert np.linalg.norm(R - Ro) <= 1e-13 * np.sqrt(d * N) * np.linalg.norm(Msk0)
+    assert np.all(np.tril(R, -1) == 0)
+    # R^sk is unique up to row signs (the GPU forms it from the LU factors as
+    # R(U^T) L^T; the signs cancel in everything derived from it)
+    k = min(d, N)
+    sg = np.ones(d)
+    sg[:k] = np.sign(np.diag(R)[:k] * np.diag(Ro)[:k])
+    assert np.linalg.norm(sg[:, None] * R - Ro) <= 1e-12 * np.sqrt(d * N) * np.linalg.norm(Msk0)
 
 
 def test_qrcp_wide_nonfinite_sketch_gives_identity_pivots():
