@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
     p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")
     p.add_argument("--panel", choices=["cholqr", "hqr"], default="cholqr")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                   help="mixed: sketch and trailing-update products on the bf16 tensor cores (exact slices)")
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
     p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
@@ -94,12 +96,13 @@ def parse():
 def workload_name(a):
     fam = "iid N(0,1)" if a.family == "gaussian" else "U diag(sigma) V^T, sigma geometric 1..1e-12"
     sk = "dense Philox +-1" if a.sketch == "dense" else "sparse-sign (8 nnz/col)"
-    return f"FP64 BQRRP m={a.m} n={a.n} b={a.b} d={a.d}, {fam}, {sk} sketch, {a.panel} panel"
+    prec = "FP64" if a.precision == "fp64" else "mixed-precision (bf16 tensor-core slices, FP64 accuracy)"
+    return f"{prec} BQRRP m={a.m} n={a.n} b={a.b} d={a.d}, {fam}, {sk} sketch, {a.panel} panel"
 
 
 def config(a, world):
     return {"workload": workload_name(a), "m": a.m, "n": a.n, "b": a.b, "d": a.d, "family": a.family,
-            "sketch": a.sketch, "panel": a.panel, "seed": a.seed,
+            "sketch": a.sketch, "panel": a.panel, "precision": a.precision, "seed": a.seed,
             "l2": f"inputs larger than L2 (A is {a.m * a.n * 8 / 1e9:.2f} GB, L2 126 MB)",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -311,7 +314,8 @@ def main():
     jpvt = torch.empty(n, dtype=torch.int64, device="cuda")
     tau = torch.empty(n, dtype=torch.float64, device="cuda")
     opts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
-                       B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR)
+                       B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR,
+                       B.PRECISION_FP64 if a.precision == "fp64" else B.PRECISION_MIXED)
     ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     probe = B.bqrrp_probe_fp64_peak(4000)

@@ -47,11 +47,19 @@ extern "C" {
 #define BQRRP_PANEL_CHOLQR 0   /* Alg. 3: preconditioned CholQR + reconstruction */
 #define BQRRP_PANEL_HQR 1      /* Householder QR of the panel                    */
 
+/* Arithmetic of the dense products (sketch S*A and the trailing update). */
+#define BQRRP_PRECISION_FP64 0   /* FP64 SIMT throughout                            */
+#define BQRRP_PRECISION_MIXED 1  /* sketch and trailing-update products on the bf16
+                                    tensor cores through exact 6-bit slices (see
+                                    bqrrp_dgemm_ozaki); LU, sketch QR, panel, tau, R
+                                    in FP64                                          */
+
 typedef struct bqrrp_opts {
     int sketch_kind;     /* BQRRP_SKETCH_DENSE (default) or BQRRP_SKETCH_SPARSE */
     int64_t sketch_nnz;  /* nonzeros per column of a sparse sketch (default 8)  */
     int panel_kind;      /* BQRRP_PANEL_CHOLQR (default) or BQRRP_PANEL_HQR    */
-    int64_t reserved[5]; /* must be zero                                        */
+    int64_t precision;   /* BQRRP_PRECISION_FP64 (default) or _MIXED            */
+    int64_t reserved[4]; /* must be zero                                        */
 } bqrrp_opts;
 
 /*
@@ -217,6 +225,35 @@ int bqrrp_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, doubl
                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                 double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream);
 size_t bqrrp_dgemm_workspace(int64_t M, int64_t N, int64_t K);
+
+/*
+ * bqrrp_dgemm_ozaki -- the same product as bqrrp_dgemm formed on the bf16
+ * tensor cores: each row of op(A) and column of op(B) is scaled by a power of
+ * two and cut into nine signed 6-bit integer slices (exact in bf16); the 53
+ * slice products with p + q <= 9 are summed exactly in FP32 within K chunks of
+ * 256 and recombined in FP64.  The error is a few units of 2^-53 times
+ * max|op(A)(i,:)| * max|op(B)(:,j)| per term -- FP64 accuracy in the normwise
+ * sense.  This is the "Ozaki-split" trailing update of the mixed-precision
+ * form (the paper's apply_trans_q, Sec. 2.4, computed differently; the
+ * splitting itself has no counterpart in the paper).  Needs
+ * bqrrp_dgemm_ozaki_workspace() bytes of workspace.
+ */
+int bqrrp_dgemm_ozaki(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                      double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_dgemm_ozaki_workspace(int64_t M, int64_t N, int64_t K);
+
+/*
+ * bqrrp_sketch_apply_tc -- Msk = S*A with the dense +-1 operator (as
+ * bqrrp_sketch_apply, kind dense) on the bf16 tensor cores: S is one exact
+ * slice and A is cut into nine 6-bit slices per column, so the nine products
+ * S*A_q give S*A to FP64 accuracy (Alg. 1 sketching step).  Needs
+ * bqrrp_sketch_apply_tc_workspace() bytes.
+ */
+int bqrrp_sketch_apply_tc(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda, uint64_t seed,
+                          double* Msk, int64_t ldsk, void* workspace, size_t workspace_bytes,
+                          void* stream);
+size_t bqrrp_sketch_apply_tc_workspace(int64_t d, int64_t m, int64_t n);
 
 /*
  * bqrrp_probe_fp64_peak -- measurement helper: runs an FP64 fused-multiply-add

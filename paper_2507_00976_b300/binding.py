@@ -24,6 +24,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "bqrrp.h")
 OK, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 SKETCH_DENSE, SKETCH_SPARSE = 0, 1
 PANEL_CHOLQR, PANEL_HQR = 0, 1
+PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -36,7 +37,7 @@ _lib = None
 
 class Opts(ctypes.Structure):
     _fields_ = [("sketch_kind", ctypes.c_int), ("sketch_nnz", _i64), ("panel_kind", ctypes.c_int),
-                ("reserved", _i64 * 5)]
+                ("precision", _i64), ("reserved", _i64 * 4)]
 
 
 NPHASES = 8
@@ -78,6 +79,11 @@ _SIGS = {
                      _sz, _vp], ctypes.c_int),
     "bqrrp_dgemm_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_probe_fp64_peak": ([ctypes.c_int, _vp], _d),
+    "bqrrp_dgemm_ozaki": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64,
+                           _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_dgemm_ozaki_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_sketch_apply_tc": ([_i64, _i64, _i64, _vp, _i64, _u64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_sketch_apply_tc_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_profile_enable": ([ctypes.c_int], None),
     "bqrrp_profile_reset": ([], None),
     "bqrrp_profile_read": ([ctypes.POINTER(Profile)], ctypes.c_int),
@@ -157,11 +163,12 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
 
 
-def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR):
+def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR, precision=PRECISION_FP64):
     o = Opts()
     o.sketch_kind = sketch_kind
     o.sketch_nnz = nnz
     o.panel_kind = panel_kind
+    o.precision = precision
     return o
 
 
@@ -312,6 +319,29 @@ def bqrrp_dgemm(transa, transb, alpha, A, B, beta, C, workspace=None, stream=Non
     return C
 
 
+def bqrrp_dgemm_ozaki(transa, transb, alpha, A, B, beta, C, stream=None):
+    """C = alpha op(A) op(B) + beta C formed from exact bf16 slices on the tensor cores."""
+    M, N = C.shape
+    K = A.shape[0] if transa.upper() == "T" else A.shape[1]
+    ws = _workspace(lib().bqrrp_dgemm_ozaki_workspace(M, N, K), C.device)
+    rc = lib().bqrrp_dgemm_ozaki(transa.encode(), transb.encode(), M, N, K, alpha, _ptr(A), _ld(A), _ptr(B), _ld(B),
+                                 beta, _ptr(C), _ld(C), _ptr(ws), ws.numel(), _stream(stream))
+    _check("bqrrp_dgemm_ozaki", rc)
+    return C
+
+
+def bqrrp_sketch_apply_tc(A, d, seed, Msk=None, stream=None):
+    """Dense +-1 sketch S*A on the bf16 tensor cores (exact slices)."""
+    m, n = A.shape
+    if Msk is None:
+        Msk = colmajor_empty(d, n, device=A.device)
+    ws = _workspace(lib().bqrrp_sketch_apply_tc_workspace(d, m, n), A.device)
+    rc = lib().bqrrp_sketch_apply_tc(d, m, n, _ptr(A), _ld(A), seed, _ptr(Msk), _ld(Msk), _ptr(ws), ws.numel(),
+                                     _stream(stream))
+    _check("bqrrp_sketch_apply_tc", rc)
+    return Msk
+
+
 def bqrrp_dgemm_workspace(M, N, K):
     return int(lib().bqrrp_dgemm_workspace(M, N, K))
 
@@ -342,7 +372,7 @@ def bqrrp_launch_counter():
 
 
 # ----------------------------------------------------------------- convenience
-def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", stream=None):
+def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64", stream=None):
     """Factor a copy of A (any 2-D float64 tensor/array); returns
     (F column-major with R and reflectors, jpvt, tau, rank) as device tensors."""
     torch = _torch()
@@ -351,6 +381,7 @@ def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", stream=None):
     jpvt = torch.empty(max(n, 1), dtype=torch.int64, device=F.device)
     tau = torch.empty(max(n, 1), dtype=torch.float64, device=F.device)
     opts = make_opts(SKETCH_DENSE if sketch == "dense" else SKETCH_SPARSE, nnz,
-                     PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR)
+                     PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR,
+                     PRECISION_FP64 if precision == "fp64" else PRECISION_MIXED)
     rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
     return F, jpvt[:n], tau[:n], rank

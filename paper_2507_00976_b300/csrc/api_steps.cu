@@ -298,6 +298,57 @@ int bqrrp_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, doubl
     return dgemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+size_t bqrrp_dgemm_ozaki_workspace(int64_t M, int64_t N, int64_t K) {
+    if (M < 0 || N < 0 || K < 0) return 0;
+    return ozaki_ws_bytes(M, N, K, 9) + 256;
+}
+
+int bqrrp_dgemm_ozaki(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    set_error("");
+    const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+    if (!ta && transa != 'N' && transa != 'n') return -1;
+    if (!tb && transb != 'N' && transb != 'n') return -2;
+    if (M < 0) return -3;
+    if (N < 0) return -4;
+    if (K < 0) return -5;
+    if (lda < imax(1, ta ? K : M)) return -8;
+    if (ldb < imax(1, tb ? N : K)) return -10;
+    if (ldc < imax(1, M)) return -13;
+    if (M == 0 || N == 0) return 0;
+    if (workspace_bytes < bqrrp_dgemm_ozaki_workspace(M, N, K)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    Ctx c{};
+    BQ_TRY(current_device(&c.dev));
+    c.stream = (cudaStream_t)stream;
+    char* base = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    return ozaki_gemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, base,
+                      workspace_bytes - (size_t)(base - (char*)workspace));
+}
+
+size_t bqrrp_sketch_apply_tc_workspace(int64_t d, int64_t m, int64_t n) {
+    if (d < 0 || m < 0 || n < 0) return 0;
+    return ozaki_ws_bytes(d, n, m, 1) + 256;
+}
+
+int bqrrp_sketch_apply_tc(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda, uint64_t seed, double* Msk,
+                          int64_t ldsk, void* workspace, size_t workspace_bytes, void* stream) {
+    set_error("");
+    if (d < 0) return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (lda < imax(1, m)) return -5;
+    if (ldsk < imax(1, d)) return -8;
+    if (d == 0 || n == 0) return 0;
+    if (m > (int64_t(1) << 17)) { set_error("sketch_apply_tc: m > 2^17 is not supported"); return BQRRP_EUNSUPPORTED; }
+    if (workspace_bytes < bqrrp_sketch_apply_tc_workspace(d, m, n)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    Ctx c{};
+    BQ_TRY(current_device(&c.dev));
+    c.stream = (cudaStream_t)stream;
+    char* base = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    return ozaki_sketch(c, d, m, n, seed, A, lda, Msk, ldsk, base, workspace_bytes - (size_t)(base - (char*)workspace));
+}
+
 double bqrrp_probe_fp64_peak(int iters, void* stream) {
     set_error("");
     Device dev;

@@ -14,6 +14,7 @@
 //   sketch  : Msk(0:w, c:) -= (Rsk11 R11^-1) R12      (Duersch-Gu update)
 // All arithmetic runs in the library's kernels; the host only sequences
 // launches and reads k.
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cstdarg>
@@ -227,7 +228,8 @@ struct Bufs {
     double *Msk, *Xlu, *Ub, *stage, *Ypan, *Vqr, *Tqr, *W, *W2, *G, *U, *Tb, *R11, *Z, *D, *sktau, *splitk, *coop;
     i64 *ipiv, *Jsk, *pos, *src, *cnt, *J, *Jstage;
     char* sparse_ws;
-    size_t sparse_bytes, splitk_elems, coop_elems;
+    char* oz_ws;
+    size_t sparse_bytes, splitk_elems, coop_elems, oz_bytes;
     i64 max_moved, ldst, bb, wrows;
 };
 
@@ -265,6 +267,16 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
     B->cnt = ar.take<i64>(4);
     B->J = ar.take<i64>((size_t)n);
     B->Jstage = ar.take<i64>((size_t)B->max_moved);
+    B->oz_bytes = 0;
+    B->oz_ws = nullptr;
+    if (o.precision == BQRRP_PRECISION_MIXED) {
+        size_t z = ozaki_ws_bytes(bb, n, m, 9);                 // W = Y^T C
+        z = std::max(z, ozaki_ws_bytes(m, n, bb, 9));           // C -= Y W2
+        z = std::max(z, ozaki_ws_bytes(bb, n, bb, 9));          // W2 = T^T W
+        if (o.sketch_kind == BQRRP_SKETCH_DENSE) z = std::max(z, ozaki_ws_bytes(d, n, m, 1));   // S A
+        B->oz_bytes = z;
+        B->oz_ws = ar.take<char>(z);
+    }
     B->sparse_bytes = 0;
     B->sparse_ws = nullptr;
     if (o.sketch_kind == BQRRP_SKETCH_SPARSE) {
@@ -282,6 +294,7 @@ bqrrp_opts defaults(const bqrrp_opts* o) {
         r.sketch_kind = o->sketch_kind;
         r.sketch_nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
         r.panel_kind = o->panel_kind;
+        r.precision = o->precision;
     }
     return r;
 }
@@ -294,7 +307,8 @@ int check_opts(const bqrrp_opts* o, i64 d) {
         const i64 nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
         if (nnz > d || nnz > 64) return 1;
     }
-    for (int i = 0; i < 5; ++i)
+    if (o->precision != BQRRP_PRECISION_FP64 && o->precision != BQRRP_PRECISION_MIXED) return 1;
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i] != 0) return 1;
     return 0;
 }
@@ -383,7 +397,10 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
     // Alg. 1: sketch Msk = S * A (d x n)
     pr.begin(P_SKETCH);
     if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
-        BQ_TRY(sketch_dense_gemm(c, d, m, n, seed, A, lda, B.Msk, d));
+        if (o.precision == BQRRP_PRECISION_MIXED)
+            BQ_TRY(ozaki_sketch(c, d, m, n, seed, A, lda, B.Msk, d, B.oz_ws, B.oz_bytes));
+        else
+            BQ_TRY(sketch_dense_gemm(c, d, m, n, seed, A, lda, B.Msk, d));
         pr.flops(P_SKETCH, 2.0 * d * m * n);
     } else {
         BQ_TRY(sketch_sparse_apply(c, d, m, n, seed, o.sketch_nnz, A, lda, B.Msk, d, B.sparse_ws, B.sparse_bytes));
@@ -458,9 +475,18 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
                 pr.begin(P_TRAIL);
                 double* C = A + s + cend * lda;
                 const i64 keep = (k == w) ? rows : k;
-                BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
-                BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
-                BQ_TRY(dgemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+                if (o.precision == BQRRP_PRECISION_MIXED) {
+                    BQ_TRY(ozaki_gemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows,
+                                      B.oz_ws, B.oz_bytes));
+                    BQ_TRY(ozaki_gemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows,
+                                      B.oz_ws, B.oz_bytes));
+                    BQ_TRY(ozaki_gemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda,
+                                      B.oz_ws, B.oz_bytes));
+                } else {
+                    BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
+                    BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
+                    BQ_TRY(dgemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+                }
                 pr.flops(P_TRAIL, 2.0 * (double)k * nc * (double)rows + 2.0 * (double)k * k * nc +
                                       2.0 * (double)keep * nc * k);
             }

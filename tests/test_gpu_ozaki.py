@@ -1,0 +1,131 @@
+"""The mixed-precision form: FP64-accurate products on the bf16 tensor cores
+(exact 6-bit slices, FP32 sums that stay below 2^24, FP64 recombination),
+through the C ABI.
+
+Bar: integer data, whose slice products are exact, must come out bit-exact.
+General data must stay within 4 K 2^-53 max|op(A)(i,:)| max|op(B)(:,j)| of the
+exact product: that is the splitting's error model (truncation below 2^-54 of
+the row / column maxima, plus the FP64 recombination).  The factorization in
+mixed precision is held to the same bar as the FP64 form.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2507_00976_b300 as bq
+from checks import metrics, trailing_norms, upper_r
+from gpu_util import np_
+from paper_2507_00976_b300 import binding as B
+from paper_2507_00976_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+def dev(x):
+    return bq.to_colmajor(x)
+
+
+def ops(ta, tb, A, Bm):
+    return (A.T if ta == "T" else A), (Bm.T if tb == "T" else Bm)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("M,N,K", [(64, 32, 32), (65, 33, 17), (300, 200, 1000), (7, 513, 2049), (1, 1, 1)])
+def test_ozaki_exact_on_integer_data(ta, tb, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.integers(-(1 << 19), 1 << 19, size=(K, M) if ta == "T" else (M, K)).astype(np.float64)
+    Bm = rng.integers(-(1 << 19), 1 << 19, size=(N, K) if tb == "T" else (K, N)).astype(np.float64)
+    C = dev(np.zeros((M, N)))
+    bq.binding.bqrrp_dgemm_ozaki(ta, tb, 1.0, dev(A), dev(Bm), 0.0, C)
+    oA, oB = ops(ta, tb, A, Bm)
+    ref = (oA.astype(np.int64) @ oB.astype(np.int64)).astype(np.float64)   # |entries| < 2^53: exact
+    assert np.array_equal(np_(C), ref)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+@pytest.mark.parametrize("M,N,K", [(128, 96, 512), (257, 130, 1000), (64, 2048, 16384), (1000, 1000, 64)])
+def test_ozaki_within_fp64_error_model(ta, tb, M, N, K):
+    rng = np.random.default_rng(3 * M + N + K)
+    A = rng.standard_normal((K, M) if ta == "T" else (M, K))
+    Bm = rng.standard_normal((N, K) if tb == "T" else (K, N))
+    C0 = rng.standard_normal((M, N))
+    C = dev(C0)
+    bq.binding.bqrrp_dgemm_ozaki(ta, tb, -0.75, dev(A), dev(Bm), 1.5, C)
+    oA, oB = ops(ta, tb, A, Bm)
+    ref = -0.75 * (oA @ oB) + 1.5 * C0
+    amax = np.abs(oA).max(axis=1)[:, None]
+    bmax = np.abs(oB).max(axis=0)[None, :]
+    # splitting error (below 2^-54 of the row/column maxima per term, ten groups)
+    # plus the FP64 rounding of the reference product itself
+    bound = 8 * K * U * 0.75 * amax * bmax + 4 * U * (0.75 * (np.abs(oA) @ np.abs(oB)) + np.abs(1.5 * C0))
+    assert np.all(np.abs(np_(C) - ref) <= bound)
+
+
+def test_ozaki_wide_dynamic_range_rows_and_columns():
+    rng = np.random.default_rng(7)
+    M, N, K = 96, 80, 700
+    A = rng.standard_normal((M, K)) * (10.0 ** rng.integers(-100, 100, size=M))[:, None]
+    Bm = rng.standard_normal((K, N)) * (10.0 ** rng.integers(-100, 100, size=N))[None, :]
+    A[5] = 0.0                                           # an all-zero row
+    C = dev(np.zeros((M, N)))
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
+    ref = A @ Bm
+    scale = np.abs(A).max(axis=1)[:, None] * np.abs(Bm).max(axis=0)[None, :]
+    assert np.all(np.abs(np_(C) - ref) <= 8 * K * U * scale)
+    assert np.all(np_(C)[5] == 0.0)
+
+
+def test_ozaki_beta_zero_ignores_nan():
+    A = np.ones((70, 5))
+    Bm = np.ones((5, 90))
+    C = dev(np.full((70, 90), np.nan))
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
+    assert np.all(np_(C) == 5.0)
+
+
+@pytest.mark.parametrize("d,m,n", [(160, 2000, 1000), (37, 333, 21), (640, 4097, 65)])
+def test_sketch_tc_exact_on_integer_data(d, m, n):
+    rng = np.random.default_rng(d + m)
+    A = rng.integers(-40, 40, size=(m, n)).astype(np.float64)
+    Msk = bq.binding.bqrrp_sketch_apply_tc(dev(A), d, 5)
+    ref = oracle.sketch_apply(oracle.sketch_operator(d, m, 5), A)
+    assert np.array_equal(np_(Msk), ref)
+
+
+def test_sketch_tc_gaussian_within_fp64_bound():
+    d, m, n = 160, 2000, 1000
+    A = W.gaussian(m, n, 3)
+    Msk = np_(bq.binding.bqrrp_sketch_apply_tc(dev(A), d, 11))
+    ref = oracle.sketch_apply(oracle.sketch_operator(d, m, 11), A)
+    bound = 4 * m * U * np.abs(A).max(axis=0)[None, :] + 2 * m * U * np.abs(A).sum(axis=0)[None, :]
+    assert np.all(np.abs(Msk - ref) <= bound)
+
+
+def _factor_mixed(A, b, d, seed, **kw):
+    F, jpvt, tau, rank = bq.factor(A, b, d, seed, precision="mixed", **kw)
+    torch.cuda.synchronize()
+    return np_(F), np_(jpvt), np_(tau), rank
+
+
+@pytest.mark.parametrize("case", ["c1", "ragged", "lowrank", "hqr"])
+def test_mixed_factorization_meets_the_fp64_bar(case):
+    if case == "c1":
+        A, b, d, kw = W.c1_matrix(), 128, 160, {}
+    elif case == "ragged":
+        A, b, d, kw = W.gaussian(777, 500, 9), 64, 80, {}
+    elif case == "lowrank":
+        A, b, d, kw = W.low_rank(1000, 600, 150, 4), 64, 80, {}
+    else:
+        A, b, d, kw = W.gaussian(900, 700, 12), 96, 120, {"panel": "hqr"}
+    fo = oracle.bqrrp(A, b, d, 1, panel=kw.get("panel", "cholqr"))
+    F, jpvt, tau, rank = _factor_mixed(A, b, d, 1, **kw)
+    assert rank == fo.rank
+    if all(t["margin"] > 1e-6 for t in fo.trace):
+        assert np.array_equal(jpvt[:rank], fo.jpvt[:rank])
+    res, orth, ok = metrics(A, F, jpvt, tau, rank)
+    assert ok and res <= 1e-12 and orth <= 1e-12, (res, orth)
+    bounds = list(range(0, A.shape[1], b))
+    assert np.all(trailing_norms(F, rank, bounds) <= 1.1 * trailing_norms(fo.A, fo.rank, bounds)
+                  + 1e-13 * np.linalg.norm(A))
