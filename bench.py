@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
     p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
     p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
+    p.add_argument("--skip-mixed", action="store_true",
+                   help="with --precision fp64, do not also time the mixed-precision form on the same input")
     p.add_argument("--only", choices=["factor", "gemm", "geqrf"], default="factor",
                    help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape); "
                         "geqrf: time the library's own unpivoted QR alone on the m x n input")
@@ -210,6 +212,34 @@ def run_reference(a, world, rank):
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_own_qr(A, A0, precision, reps):
+    """Event-timed runs of the library's own unpivoted QR on copies of A0."""
+    import torch
+
+    from paper_2507_00976_b300 import binding as B
+    m, n = A.shape
+    tau = torch.empty(n, dtype=torch.float64, device="cuda")
+    if precision == "mixed":
+        ws = torch.empty(B.bqrrp_geqrf_mixed_workspace(m, n), dtype=torch.uint8, device="cuda")
+    else:
+        ws = torch.empty(B.bqrrp_geqrf_workspace(m, n, 0), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        A.copy_(A0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if precision == "mixed":
+            B.bqrrp_geqrf_mixed(A, tau=tau, workspace=ws)
+        else:
+            B.bqrrp_geqrf(A, 0, tau=tau, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
 
 
 # ------------------------------------------------------------------ GEMM alone
@@ -362,23 +392,40 @@ def main():
     # ---------------- the library's own unpivoted QR on the same input
     qr = None
     if not a.skip_qr:
-        qtau = torch.empty(n, dtype=torch.float64, device="cuda")
-        qws = torch.empty(B.bqrrp_geqrf_workspace(m, n, 0), dtype=torch.uint8, device="cuda")
-        qms = []
-        for i in range(a.steps + 1):
+        qms = time_own_qr(A, A0, a.precision, a.steps + 1)[1:]
+        qr_gf = flops / (statistics.mean(qms) * 1e-3) / 1e9
+        qr = {"gflops": qr_gf, "ms_mean": statistics.mean(qms), "ms_best": min(qms),
+              "bqrrp_over_qr": (flops / (statistics.mean(step_ms) * 1e-3) / 1e9) / qr_gf,
+              "precision": a.precision}
+
+    # ---------------- the mixed-precision form on the same input (FP64 headline runs)
+    mixed = None
+    if a.precision == "fp64" and not a.skip_mixed:
+        mopts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
+                            B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR, B.PRECISION_MIXED)
+        del ws
+        torch.cuda.empty_cache()
+        ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, mopts), dtype=torch.uint8, device="cuda")
+        mms = []
+        for i in range(3):
             A.copy_(A0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            B.bqrrp_geqrf(A, 0, tau=qtau, workspace=qws)
+            mrank = B.bqrrp_factor(A, b, d, 1, jpvt, tau, opts=mopts, workspace=ws)
             e1.record(stream)
             torch.cuda.synchronize()
             if i > 0:
-                qms.append(e0.elapsed_time(e1))
-        qr_gf = flops / (statistics.mean(qms) * 1e-3) / 1e9
-        qr = {"gflops": qr_gf, "ms_mean": statistics.mean(qms), "ms_best": min(qms),
-              "bqrrp_over_qr": (flops / (statistics.mean(step_ms) * 1e-3) / 1e9) / qr_gf}
-        del qws
+                mms.append(e0.elapsed_time(e1))
+        mgf = flops / (statistics.mean(mms) * 1e-3) / 1e9
+        mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank,
+                 "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
+                 "arith": "FP64-accurate products on bf16 tensor cores (9 exact 6-bit slices, 53 pair products); "
+                          "LU, sketch QR, panel, tau, R in FP64"}
+        if not a.skip_qr:
+            mq = time_own_qr(A, A0, "mixed", 3)[1:]
+            mixed["own_qr_gflops"] = flops / (statistics.mean(mq) * 1e-3) / 1e9
+            mixed["bqrrp_over_qr"] = mgf / mixed["own_qr_gflops"]
 
     # ---------------- end to end through the host-buffer entry point
     e2e = None
@@ -440,6 +487,7 @@ def main():
         "best_gflops": flops / (lat[0] * 1e-3) / 1e9,
         "own_qr": qr, "rank": ranks[0], "gpu_launches": launches, "wall_s": t_wall,
         "roofline": roofline, "phases": phases, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        "mixed_precision": mixed,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -214,6 +214,13 @@ int bqrrp_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau, int64
                 void* workspace, size_t workspace_bytes, void* stream);
 size_t bqrrp_geqrf_workspace(int64_t m, int64_t n, int64_t nb);
 
+/* The same unpivoted QR with the trailing-update products on the bf16 tensor
+ * cores (exact slices, FP64 accuracy; see bqrrp_dgemm_ozaki): the baseline the
+ * mixed-precision BQRRP is compared with. */
+int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
+                      void* workspace, size_t workspace_bytes, void* stream);
+size_t bqrrp_geqrf_mixed_workspace(int64_t m, int64_t n);
+
 /*
  * bqrrp_dgemm -- C = alpha*op(A)*op(B) + beta*C with the library's FP64 SIMT
  * GEMM (the kernel behind the trailing update of Alg. 1).  transa/transb:

@@ -75,6 +75,8 @@ _SIGS = {
     "bqrrp_cholqr_panel_workspace": ([_i64, _i64], _sz),
     "bqrrp_geqrf": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_geqrf_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_geqrf_mixed": ([_i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "bqrrp_geqrf_mixed_workspace": ([_i64, _i64], _sz),
     "bqrrp_dgemm": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _d, _vp, _i64, _vp, _i64, _d, _vp, _i64, _vp,
                      _sz, _vp], ctypes.c_int),
     "bqrrp_dgemm_workspace": ([_i64, _i64, _i64], _sz),
@@ -306,6 +308,24 @@ def bqrrp_geqrf(A, nb=0, tau=None, workspace=None, stream=None):
 
 def bqrrp_geqrf_workspace(m, n, nb=0):
     return int(lib().bqrrp_geqrf_workspace(m, n, nb))
+
+
+def bqrrp_geqrf_mixed_workspace(m, n):
+    return int(lib().bqrrp_geqrf_mixed_workspace(m, n))
+
+
+def bqrrp_geqrf_mixed(A, tau=None, workspace=None, stream=None):
+    """Own unpivoted QR with tensor-core (exact-slice) trailing updates."""
+    torch = _torch()
+    m, n = A.shape
+    if tau is None:
+        tau = torch.zeros(max(min(m, n), 1), dtype=torch.float64, device=A.device)
+    if workspace is None:
+        workspace = _workspace(lib().bqrrp_geqrf_mixed_workspace(m, n), A.device)
+    rc = lib().bqrrp_geqrf_mixed(m, n, _ptr(A), _ld(A), _ptr(tau), _ptr(workspace), workspace.numel(),
+                                 _stream(stream))
+    _check("bqrrp_geqrf_mixed", rc)
+    return tau
 
 
 def bqrrp_dgemm(transa, transb, alpha, A, B, beta, C, workspace=None, stream=None):

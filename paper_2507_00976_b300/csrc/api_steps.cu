@@ -267,6 +267,39 @@ int bqrrp_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau, int64
     return finish(c);
 }
 
+size_t bqrrp_geqrf_mixed_workspace(int64_t m, int64_t n) {
+    if (m < 0 || n < 0) return 0;
+    return bqrrp_geqrf_workspace(m, n, 0) + ozaki_ws_bytes(64, imax(n, 1), imax(m, 1), 9) + 512;
+}
+
+int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    set_error("");
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (lda < imax(1, m)) return -4;
+    if (m == 0 || n == 0) return 0;
+    if (!A) return -3;
+    if (!tau) return -5;
+    if (workspace_bytes < bqrrp_geqrf_mixed_workspace(m, n)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    Arena ar;
+    Ctx c{};
+    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false));
+    double* V = ar.take<double>((size_t)m * 64);
+    double* T = ar.take<double>(64 * 64);
+    double* W = ar.take<double>((size_t)64 * n);
+    double* W2 = ar.take<double>((size_t)64 * n);
+    const size_t oz = ozaki_ws_bytes(64, n, m, 9);
+    c.oz_ws = ar.take<char>(oz);
+    c.oz_bytes = oz;
+    c.mixed = true;
+    if (!ar.ok()) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    init_status_small<<<1, 1, 0, c.stream>>>(c.st);
+    BQ_LAUNCH_CHECK();
+    BQ_TRY(geqrf_blocked(c, m, n, A, lda, tau, V, T, W, W2, 64));
+    return finish(c);
+}
+
 size_t bqrrp_dgemm_workspace(int64_t M, int64_t N, int64_t K) {
     (void)M; (void)N; (void)K;
     Arena ar;

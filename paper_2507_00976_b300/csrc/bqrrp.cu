@@ -274,6 +274,9 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
         z = std::max(z, ozaki_ws_bytes(m, n, bb, 9));           // C -= Y W2
         z = std::max(z, ozaki_ws_bytes(bb, n, bb, 9));          // W2 = T^T W
         if (o.sketch_kind == BQRRP_SKETCH_DENSE) z = std::max(z, ozaki_ws_bytes(d, n, m, 1));   // S A
+        z = std::max(z, ozaki_ws_bytes(d, n, 64, 9));           // LU trailing updates
+        z = std::max(z, ozaki_ws_bytes(d, n, d, 9));            // R^sk = R1 L^T
+        z = std::max(z, ozaki_ws_bytes(64, n, m, 9));           // Householder panel updates (HQR panel)
         B->oz_bytes = z;
         B->oz_ws = ar.take<char>(z);
     }
@@ -462,8 +465,12 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         } else {
             // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
             pr.begin(P_PANEL);
-            BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
-                                      tau + s));
+            {
+                Ctx cp = c;
+                cp.mixed = false;   // Gram, Cholesky, reconstruction, tau and R stay in FP64
+                BQ_TRY(cholqr_panel_steps(cp, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D,
+                                          B.bb, tau + s));
+            }
             {
                 const double r = (double)rows, kk = (double)k;
                 // TRSM, Gram, TRSM, reconstruction (rows k^2 each) + Cholesky, T, R11 (k^3 terms)
@@ -497,7 +504,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         pr.begin(P_SKUPD);
         BQ_TRY(copy_triu(c, w, w, Ssk, d, B.Z, B.bb));
         BQ_TRY(trsm_ru(c, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
-        BQ_TRY(dgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
+        BQ_TRY(pgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
         pr.flops(P_SKUPD, (double)w * w * w + 2.0 * (double)w * w * nc);
     }
     pr.begin(P_OTHER);
@@ -593,6 +600,9 @@ int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_
     c.splitk_elems = B.splitk_elems;
     c.coop = B.coop;
     c.coop_elems = B.coop_elems;
+    c.mixed = (o.precision == BQRRP_PRECISION_MIXED);
+    c.oz_ws = B.oz_ws;
+    c.oz_bytes = B.oz_bytes;
     i64 r = 0;
     PhaseRec pr;
     {

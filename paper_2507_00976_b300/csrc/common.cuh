@@ -187,12 +187,20 @@ struct Ctx {
     // cooperative-kernel scratch
     double* coop;           // partial buffers
     size_t coop_elems;
+    // mixed precision: large products go to the bf16-slice tensor-core GEMM
+    bool mixed = false;
+    void* oz_ws = nullptr;
+    size_t oz_bytes = 0;
 };
 
 // gemm.cu
 int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
           const double* B, i64 ldb, double beta, double* C, i64 ldc);
 int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, double beta, View C);
+// FP64-accurate product: the tensor-core slice GEMM when c.mixed and the
+// problem is large enough (and its workspace fits), else the FP64 SIMT GEMM.
+int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
+          const double* B, i64 ldb, double beta, double* C, i64 ldc);
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,
                       i64 ldsk);
 

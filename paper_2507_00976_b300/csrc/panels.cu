@@ -648,7 +648,7 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
             BQ_TRY(trsm_ru(c, below, st, Skv.sub(jb, jb), Skv.sub(jb + pw, jb), true));
             // trailing: Sk(jb+pw:d, jb+pw:N) -= U12^T * L21^T
             if (jb + st < steps)
-                BQ_TRY(dgemm(c, false, false, below, N - jb - pw, pw, -1.0, Sk + (jb + pw) + jb * ldsk, ldsk,
+                BQ_TRY(pgemm(c, false, false, below, N - jb - pw, pw, -1.0, Sk + (jb + pw) + jb * ldsk, ldsk,
                              Sk + jb + (jb + pw) * ldsk, ldsk, 1.0, Sk + (jb + pw) + (jb + pw) * ldsk, ldsk));
         }
         if (jb + st >= steps) break;
@@ -764,9 +764,9 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
         const i64 nc = cols - jb - pw;
         if (nc > 0) {
             double* C = A + jb + (jb + pw) * lda;
-            BQ_TRY(dgemm(c, true, false, pw, nc, prow, 1.0, V, rows, C, lda, 0.0, W, nb));
+            BQ_TRY(pgemm(c, true, false, pw, nc, prow, 1.0, V, rows, C, lda, 0.0, W, nb));
             BQ_TRY(dgemm(c, true, false, pw, nc, pw, 1.0, T, nb, W, nb, 0.0, W2, nb));
-            BQ_TRY(dgemm(c, false, false, prow, nc, pw, -1.0, V, rows, W2, nb, 1.0, C, lda));
+            BQ_TRY(pgemm(c, false, false, prow, nc, pw, -1.0, V, rows, W2, nb, 1.0, C, lda));
         }
     }
     return 0;
@@ -809,7 +809,7 @@ int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 
     BQ_LAUNCH_CHECK();
     BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
     BQ_TRY(set_zero_below(c, s, s, Ub, d));
-    BQ_TRY(dgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk));
+    BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk));
     if (s < d) {
         zero_rows_kernel<<<blocks, 256, 0, c.stream>>>(s, d, N, Sk, ldsk);
         BQ_LAUNCH_CHECK();

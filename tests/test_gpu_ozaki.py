@@ -129,3 +129,16 @@ def test_mixed_factorization_meets_the_fp64_bar(case):
     bounds = list(range(0, A.shape[1], b))
     assert np.all(trailing_norms(F, rank, bounds) <= 1.1 * trailing_norms(fo.A, fo.rank, bounds)
                   + 1e-13 * np.linalg.norm(A))
+
+
+@pytest.mark.parametrize("m,n", [(300, 200), (2049, 130), (1000, 1000), (5000, 300)])
+def test_own_qr_mixed_matches_oracle(m, n):
+    A = W.gaussian(m, n, m + 2 * n)
+    Ad = dev(A)
+    tau = np_(bq.binding.bqrrp_geqrf_mixed(Ad))
+    F = np_(Ad)
+    Fo, tau_o = oracle.geqrf(A)
+    k = min(m, n)
+    nrm = np.linalg.norm(A)
+    assert np.linalg.norm(np.triu(F)[:k] - np.triu(Fo)[:k]) <= 1e-13 * np.sqrt(m * n) * nrm
+    assert np.max(np.abs(tau[:k] - tau_o)) <= 1e-12
