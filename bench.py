@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
     p.add_argument("--skip-mixed", action="store_true",
                    help="with --precision fp64, do not also time the mixed-precision form on the same input")
-    p.add_argument("--only", choices=["factor", "gemm", "geqrf"], default="factor",
+    p.add_argument("--only", choices=["factor", "gemm", "ozaki", "geqrf"], default="factor",
                    help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape); "
                         "geqrf: time the library's own unpivoted QR alone on the m x n input")
     p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
@@ -255,21 +255,30 @@ def run_gemm(a):
     C = torch.randn((N, M), generator=g, dtype=torch.float64, device="cuda").t()
     ws = torch.empty(B.bqrrp_dgemm_workspace(M, N, K), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    if a.only == "ozaki":
+        run = lambda: B.bqrrp_dgemm_ozaki("N", "N", -1.0, A, Bm, 1.0, C)
+    else:
+        run = lambda: B.bqrrp_dgemm("N", "N", -1.0, A, Bm, 1.0, C, workspace=ws)
     for _ in range(a.warmup):
-        B.bqrrp_dgemm("N", "N", -1.0, A, Bm, 1.0, C, workspace=ws)
+        run()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
-        B.bqrrp_dgemm("N", "N", -1.0, A, Bm, 1.0, C, workspace=ws)
+        run()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.steps
     tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
-    print(json.dumps({"metric": "FP64 GEMM TFLOP/s (C -= A B)", "value": tf, "unit": "TFLOP/s", "ms_per_step": ms,
-                      "steps": a.steps, "warmup": a.warmup, "config": {"M": M, "N": N, "K": K},
-                      "frac_of_peak": tf / FP64_PEAK_TFLOPS}), flush=True)
+    name = "FP64 GEMM TFLOP/s (C -= A B)" if a.only == "gemm" else \
+        "FP64-accurate GEMM on bf16 tensor cores, FP64-equivalent TFLOP/s (C -= A B)"
+    line = {"metric": name, "value": tf, "unit": "TFLOP/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
+            "config": {"M": M, "N": N, "K": K}, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}
+    if a.only == "ozaki":
+        # 53 bf16 slice products per FP64 product
+        line["bf16_tensor_tflops"] = 53 * tf
+    print(json.dumps(line), flush=True)
 
 
 def run_geqrf(a):
@@ -310,7 +319,7 @@ def main():
     if a.impl == "reference":
         run_reference(a, world, rank)
         return
-    if a.only == "gemm":
+    if a.only in ("gemm", "ozaki"):
         run_gemm(a)
         return
     if a.only == "geqrf":

@@ -251,15 +251,23 @@ __global__ void __launch_bounds__(ONT, 1) ozaki_mma_kernel(OzArgs p) {
             __syncthreads();
             buf ^= 1;
         }
-        // flush the exact group sums into FP64 (weights 2^-6t)
+        // flush the exact group sums (integers below 2^24) into FP64 with weights
+        // 2^-6t.  Groups t <= 4 and t >= 5 are first combined exactly in 64-bit
+        // integers by Horner steps of 2^6 (each below 2^53), so the FP64 pipe
+        // sees two conversions and two FMAs per element instead of one per group.
 #pragma unroll
-        for (int t = 0; t < NG; ++t) {
-            const double w = ldexp(1.0, -6 * t);
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int r = 0; r < 4; ++r) {
+                long long hi = 0, lo = 0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc64[j][r] = fma((double)acc[t][j][r], w, acc64[j][r]);
-        }
+                for (int t = 0; t < NG && t <= 4; ++t) hi = hi * 64 + (long long)__float2int_rz(acc[t][j][r]);
+#pragma unroll
+                for (int t = 5; t < NG; ++t) lo = lo * 64 + (long long)__float2int_rz(acc[t][j][r]);
+                const int nhi = (NG < 5) ? NG : 5;
+                acc64[j][r] = fma((double)hi, ldexp(1.0, -6 * (nhi - 1)), acc64[j][r]);
+                if (NG > 5) acc64[j][r] = fma((double)lo, ldexp(1.0, -6 * (NG - 1)), acc64[j][r]);
+            }
     }
     // epilogue: C = alpha 2^(ea_i + eb_j - 12) acc + beta C
     const int g = lane >> 2, tq = lane & 3;
