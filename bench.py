@@ -38,6 +38,31 @@ SM_MAX_MHZ = 2032.0
 # FP64: 2 DFMA per clock per SM (the measured DFMA rate is 1.82-1.97 per clock
 # per SM; tcgen05 has no f64 kind), 2 FLOP per DFMA.
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# the FP64-accurate tensor-core product runs 53 bf16 slice products per FP64 product
+OZ_PRODUCTS = 53
+
+
+def bf16_peak():
+    """Measured cuBLAS bf16 throughput of this part (sustained: the slice GEMMs run
+    inside a seconds-long factorization) and where the number came from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["bf16_tflops_sustained"]), "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1400.0, "fallback (sustained bf16 of an earlier B300 measurement)"
+
+
+def mixed_roofline(fp64eq_tflops):
+    """Tensor roofline of the slice GEMM: bf16 work = 53 x the FP64-equivalent rate."""
+    if not fp64eq_tflops:
+        return None
+    peak, src = bf16_peak()
+    ach = OZ_PRODUCTS * fp64eq_tflops
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "kernel": "ozaki_mma_kernel (bf16 slice products of the trailing update, "
+            "mma.sync m16n8k16)", "fp64_equivalent_tflops": fp64eq_tflops, "peak_source": src}
 
 
 def canonical_flops(m, n):
@@ -277,7 +302,8 @@ def run_gemm(a):
             "config": {"M": M, "N": N, "K": K}, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}
     if a.only == "ozaki":
         # 53 bf16 slice products per FP64 product
-        line["bf16_tensor_tflops"] = 53 * tf
+        line["bf16_tensor_tflops"] = OZ_PRODUCTS * tf
+        line["roofline"] = mixed_roofline(tf)
     print(json.dumps(line), flush=True)
 
 
@@ -416,7 +442,9 @@ def main():
         torch.cuda.empty_cache()
         ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, mopts), dtype=torch.uint8, device="cuda")
         mms = []
+        B.bqrrp_profile_reset()
         for i in range(3):
+            B.bqrrp_profile_enable(i > 0)
             A.copy_(A0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -426,8 +454,12 @@ def main():
             torch.cuda.synchronize()
             if i > 0:
                 mms.append(e0.elapsed_time(e1))
+        B.bqrrp_profile_enable(False)
+        mprof = B.bqrrp_profile_read()
+        mtr_ms, mtr_fl = mprof["trailing"]
         mgf = flops / (statistics.mean(mms) * 1e-3) / 1e9
-        mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank,
+        mtf = mtr_fl / (mtr_ms * 1e-3) / 1e12 if mtr_ms > 0 else None
+        mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
                  "arith": "FP64-accurate products on bf16 tensor cores (9 exact 6-bit slices, 53 pair products); "
                           "LU, sketch QR, panel, tau, R in FP64"}
@@ -477,11 +509,14 @@ def main():
         phases[name] = {"ms_per_step": ms / max(1, prof["calls"]),
                         "share": ms / max(1e-9, sum(prof[p][0] for p in B.PHASES)),
                         "tflops": (fl / (ms * 1e-3) / 1e12) if ms > 0 and fl > 0 else None}
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
-                "kernel": "dgemm_kernel (FP64 SIMT GEMMs of the trailing block-reflector update)",
-                "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
-                "dfma_probe_tflops": probe}
+    if a.precision == "mixed":
+        roofline = mixed_roofline(achieved)
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                    "kernel": "dgemm_kernel (FP64 SIMT GEMMs of the trailing block-reflector update)",
+                    "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
+                    "dfma_probe_tflops": probe}
     cpu = None
     if not a.skip_cpu and world == 1:
         gf, sample, cores = cpu_sample(a)
