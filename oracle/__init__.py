@@ -64,6 +64,10 @@ def lib():
             L.bqrrp_ref_factor.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, _u64, ctypes.c_int, _i64,
                                            ctypes.c_int, _ip, _dp, _ip, _dp, _i64, _i64, _dp]
             L.bqrrp_ref_factor.restype = ctypes.c_int
+            L.bqrrp_ref_trunc_rank.argtypes = [_i64, _i64, _dp, _i64, _i64, ctypes.c_double, ctypes.c_double]
+            L.bqrrp_ref_trunc_rank.restype = _i64
+            L.bqrrp_ref_fro_norm.argtypes = [_i64, _i64, _dp, _i64]
+            L.bqrrp_ref_fro_norm.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -223,3 +227,44 @@ def bqrrp_status(A, b, d, seed=0, sketch_kind=0, nnz=8, lda=None):
     return lib().bqrrp_ref_factor(m, n, _p(A), lda if lda is not None else max(m, 1), b, d, seed,
                                   int(sketch_kind), nnz, 0, _p(jpvt, _ip), _p(tau), ctypes.byref(rank),
                                   None, 0, 0, None)
+
+
+def fro_norm(A):
+    """||A||_F as a plain sum of squares."""
+    A = _f(A)
+    m, n = A.shape
+    return lib().bqrrp_ref_fro_norm(m, n, _p(A), max(m, 1))
+
+
+def trunc_rank(F, rank, anorm, tol):
+    """Rank-revealing truncation on a factored A (GEQP3 storage): the smallest i
+    with ||R(i:rank, i:n)||_F <= tol * anorm (the Sec. 6 residual measure as a
+    rule; rows at and below ``rank`` count as zero)."""
+    F = _f(F)
+    m, n = F.shape
+    return int(lib().bqrrp_ref_trunc_rank(m, n, _p(F), max(m, 1), int(rank), float(anorm), float(tol)))
+
+
+class BatchedResult:
+    """Per-matrix results of ``bqrrp_batched``: lists ``F``, ``jpvt``, ``tau``,
+    ``rank``, ``trunc_rank`` and ``trace`` (each entry as for ``bqrrp``)."""
+
+    def __init__(self):
+        self.F, self.jpvt, self.tau, self.rank, self.trunc_rank, self.trace = [], [], [], [], [], []
+
+
+def bqrrp_batched(mats, bs, ds, seeds, tol):
+    """Many independent BQRRP factorizations (Alg. 1 with the Alg. 3 panel),
+    each with its own block size, sketch size and seed, followed by the
+    truncation rule.  A plain loop over ``bqrrp``: the batched workload has no
+    arithmetic of its own beyond the truncation post-pass."""
+    out = BatchedResult()
+    for A, b, d, sd in zip(mats, bs, ds, seeds):
+        f = bqrrp(A, int(b), int(d), int(sd))
+        out.F.append(f.A)
+        out.jpvt.append(f.jpvt)
+        out.tau.append(f.tau)
+        out.rank.append(f.rank)
+        out.trace.append(f.trace)
+        out.trunc_rank.append(trunc_rank(f.A, f.rank, fro_norm(A), tol))
+    return out

@@ -29,7 +29,11 @@
  *    which is what makes Q_curr * R11 reproduce the panel);
  *  - the Householder reconstruction is the modified-LU construction of
  *    Ballard et al. (cited as BD2015, Alg. 5): Qc - [S;0] = Y*U with S chosen
- *    during elimination, T = -U*S*Y1^{-T}, D = S.
+ *    during elimination, T = -U*S*Y1^{-T}, D = S;
+ *  - the rank-revealing truncation of the batched and serving workloads (not
+ *    in the paper) is a post-pass on the computed R: the smallest i with
+ *    ||R(i:, i:)||_F <= tol * ||A||_F, the residual measure of Sec. 6, with the
+ *    rows at and below the factorization's rank counted as zero.
  *
  * Parity status: every routine here is pinned by tests/test_oracle_*.py
  * (library cross-checks, closed forms, brute force, invariants) except the
@@ -633,4 +637,40 @@ done:
     free(S); free(Msk); free(X); free(tmp); free(ipiv); free(Jsk); free(J); free(Jt);
     free(Pre); free(G); free(Rc); free(T); free(D); free(R11); free(Z); free(scratch); free(sktau);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rank-revealing truncation (the error measure of Sec. 6 used as a rule).    */
+/* ------------------------------------------------------------------------ */
+
+/* Smallest i in [0, rank] with ||R(i:rank, i:n)||_F <= tol * anorm, where R is
+ * the upper trapezoid of the factored A (rows 0 .. rank-1; rows at and below
+ * the rank are counted as zero).  Since R(r, c) = 0 for c < r, the block norm
+ * is the sum over rows r >= i of ||R(r, r:n)||^2, accumulated here from the
+ * last row upwards. */
+int64_t bqrrp_ref_trunc_rank(int64_t m, int64_t n, const double* A, int64_t lda, int64_t rank,
+                             double anorm, double tol)
+{
+    (void)m;
+    double thr = tol * anorm;
+    double thr2 = thr * thr;
+    double tail = 0.0;          /* ||R(i:rank, i:n)||_F^2 for the current i */
+    int64_t best = rank;
+    for (int64_t i = rank - 1; i >= 0; --i) {
+        double row = 0.0;
+        for (int64_t c = i; c < n; ++c) row += AT(A, i, c, lda) * AT(A, i, c, lda);
+        tail += row;
+        if (tail <= thr2) best = i;
+        else break;
+    }
+    return best;
+}
+
+/* Frobenius norm by a plain sum of squares in column order. */
+double bqrrp_ref_fro_norm(int64_t m, int64_t n, const double* A, int64_t lda)
+{
+    double acc = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) acc += AT(A, i, j, lda) * AT(A, i, j, lda);
+    return sqrt(acc);
 }

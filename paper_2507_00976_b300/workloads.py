@@ -11,7 +11,10 @@ bytes.  Families (paper Sec. 1.4 and Sec. 6):
   U, V from numpy PCG64 seed 0;
 * ``kahan``: the Kahan matrix of Sec. 6 (alpha = sin(theta), beta = -cos(theta),
   plus eps*p*diag(n, ..., 1));
-* ``low_rank``: exact rank-r products of two Gaussian factors.
+* ``low_rank``: exact rank-r products of two Gaussian factors;
+* ``batched_shapes`` / ``batched_matrix``: the many-small-matrices workload
+  (m log-uniform in [64, 1024], n log-uniform in [32, m],
+  sigma_k = 10^(-8(k-1)/(n-1))), and ``batch_offsets`` for its packed layout.
 
 Large matrices are generated on the GPU with torch (untimed test tooling).
 """
@@ -69,6 +72,41 @@ def kahan(n, p=1000.0, theta=1.2):
     return np.asfortranarray(D[:, None] * U + eps * p * np.diag(np.arange(n, 0, -1, dtype=np.float64)))
 
 
+def batched_shapes(count, seed, m_lo=64, m_hi=1024, n_lo=32):
+    """``count`` shapes: m log-uniform in [m_lo, m_hi], then n log-uniform in
+    [n_lo, m] (both rounded down to integers, n clamped to [n_lo, m])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = np.floor(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), count))).astype(np.int64)
+    m = np.clip(m, m_lo, m_hi)
+    u = rng.uniform(0.0, 1.0, count)
+    n = np.floor(np.exp(np.log(n_lo) + u * (np.log(m) - np.log(n_lo)))).astype(np.int64)
+    n = np.clip(n, n_lo, m)
+    return m, n
+
+
+def batched_sigma(n, decades=8.0):
+    """sigma_k = 10^(-decades (k-1)/(n-1)), k = 1..n."""
+    return geometric_sigma(n, -decades)
+
+
+def batched_matrix(m, n, seed, decades=8.0):
+    """One matrix of the batched workload: U diag(sigma) V^T, sigma geometric
+    over ``decades`` decades."""
+    return spectrum(m, n, batched_sigma(n, decades), seed)
+
+
+def batch_offsets(m, n):
+    """Packed layout of a batch: matrix i (column-major, lda = m_i) starts at
+    element offset sum_{j<i} m_j n_j of A; its jpvt and tau start at
+    sum_{j<i} n_j.  Returns (offA, offJ, totalA, totalJ)."""
+    m = np.asarray(m, dtype=np.int64)
+    n = np.asarray(n, dtype=np.int64)
+    sizes = m * n
+    offA = np.concatenate([[0], np.cumsum(sizes)[:-1]]) if len(m) else np.zeros(0, np.int64)
+    offJ = np.concatenate([[0], np.cumsum(n)[:-1]]) if len(m) else np.zeros(0, np.int64)
+    return offA.astype(np.int64), offJ.astype(np.int64), int(sizes.sum()), int(n.sum())
+
+
 # --------------------------- device generators ---------------------------
 
 def gaussian_torch(m, n, seed, device="cuda"):
@@ -91,3 +129,21 @@ def spectrum_torch(m, n, sigma, seed, device="cuda"):
     A = (U * sig[None, :]) @ V.t()
     del U, V
     return A.t().contiguous().t()
+
+
+def batched_torch(m, n, seed, decades=8.0, device="cuda"):
+    """The batched workload packed on the device (``batch_offsets`` layout):
+    matrix i is U diag(sigma) V^T with U, V from torch QR of N(0,1) blocks drawn
+    from a generator seeded with seed + i.  Returns a 1-D float64 tensor."""
+    import torch
+    offA, _, total, _ = batch_offsets(m, n)
+    out = torch.empty(max(total, 1), dtype=torch.float64, device=device)
+    g = torch.Generator(device=device)
+    for i, (mi, ni) in enumerate(zip(m.tolist(), n.tolist())):
+        g.manual_seed(int(seed) + i)
+        sig = torch.as_tensor(batched_sigma(ni, decades), device=device)
+        U, _ = torch.linalg.qr(torch.randn((mi, ni), generator=g, dtype=torch.float64, device=device))
+        V, _ = torch.linalg.qr(torch.randn((ni, ni), generator=g, dtype=torch.float64, device=device))
+        Ai = (U * sig[None, :]) @ V.t()
+        out[offA[i]:offA[i] + mi * ni].copy_(Ai.t().reshape(-1))
+    return out
