@@ -114,6 +114,12 @@ def parse():
                    help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape); "
                         "geqrf: time the library's own unpivoted QR alone on the m x n input")
     p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
+    p.add_argument("--workload", choices=["single", "batched"], default="single",
+                   help="batched: 4096 independent matrices (m log-uniform in [64, 1024], n log-uniform in "
+                        "[32, m], sigma_k = 10^(-8(k-1)/(n-1))), autotuned b and d, one CUDA graph per step")
+    p.add_argument("--batch", type=int, default=4096)
+    p.add_argument("--batch-b", type=int, default=0,
+                   help="batched: fixed block size for every matrix instead of the autotuner (d = ceil(1.25 b))")
     a = p.parse_args()
     a.m = a.m or a.n
     a.d = a.d or int(math.ceil(1.25 * a.b))
@@ -337,6 +343,194 @@ def run_geqrf(a):
 
 
 # ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ batched workload
+def batched_cpu_sample(m, n, b, d, seeds, budget_s=15.0):
+    """The oracle, as it stands, on matrices of the batch taken in order until
+    about budget_s of CPU time; returns (GFLOP/s, description, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2507_00976_b300 import workloads as W
+    done, fl, t_tot = 0, 0.0, 0.0
+    for i in range(len(m)):
+        A = W.batched_matrix(int(m[i]), int(n[i]), 7000 + i)
+        t0 = time.perf_counter()
+        oracle.bqrrp(A, int(b[i]), int(d[i]), int(seeds[i]))
+        t_tot += time.perf_counter() - t0
+        fl += canonical_flops(int(m[i]), int(n[i]))
+        done += 1
+        if t_tot >= budget_s:
+            break
+    return fl / t_tot / 1e9, (f"oracle BQRRP on the first {done} matrices of the batch (same shapes, b, d), "
+                              f"1 thread, {t_tot:.1f} s"), 1
+
+
+def run_batched(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2507_00976_b300 import binding as B
+    from paper_2507_00976_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    seed = rank_seed(a.seed, rank)
+    m, n = W.batched_shapes(a.batch, seed)
+    seeds = (np.arange(a.batch, dtype=np.uint64) + np.uint64(seed * 100000))
+    tol = 1e-8
+    A0 = W.batched_torch(m, n, seed)
+    flops = float(sum(canonical_flops(int(x), int(y)) for x, y in zip(m, n)))
+    tot_j = int(n.sum())
+    t_tune = time.perf_counter()
+    if a.batch_b > 0:
+        b = np.full(a.batch, a.batch_b, dtype=np.int64)
+        d = np.full(a.batch, int(math.ceil(1.25 * a.batch_b)), dtype=np.int64)
+        tuned_ms = None
+    else:
+        b, d, tuned_ms = B.bqrrp_batch_autotune(m, n, seeds, A0, tol)
+    t_tune = time.perf_counter() - t_tune
+    plan = B.BatchPlan(m, n, b, d, seeds, tol)
+    A = torch.empty_like(A0)
+    jpvt = torch.empty(tot_j, dtype=torch.int64, device="cuda")
+    tau = torch.empty(tot_j, dtype=torch.float64, device="cuda")
+    rk = torch.empty(a.batch, dtype=torch.int64, device="cuda")
+    tr = torch.empty(a.batch, dtype=torch.int64, device="cuda")
+    info = torch.empty(a.batch, dtype=torch.int32, device="cuda")
+    ws = torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        A.copy_(A0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.factor(A, jpvt, tau, rk, tr, info, workspace=ws, use_graph=True)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(max(3, a.warmup)):
+        one_step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    l0 = B.bqrrp_launch_counter()
+    t0 = time.perf_counter()
+    evs = [one_step() for _ in range(a.steps)]
+    barrier()
+    t_wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = (B.bqrrp_launch_counter() - l0) or plan.launches() * a.steps   # graph replays count no launches
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    tot_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = job_gflops(flops, a.steps, world, tot_ms)
+    ranks, truncs, infos = rk.cpu().numpy(), tr.cpu().numpy(), info.cpu().numpy()
+
+    # one profiled eager step: per-phase device time and algorithmic FLOPs
+    A.copy_(A0)
+    B.bqrrp_profile_reset()
+    B.bqrrp_profile_enable(True)
+    plan.factor(A, jpvt, tau, rk, tr, info, workspace=ws, use_graph=False)
+    B.bqrrp_profile_enable(False)
+    prof = B.bqrrp_profile_read()
+    tot_p = sum(prof[p][0] for p in B.PHASES) or 1e-9
+    phases = {}
+    for name in B.PHASES:
+        ms, fl = prof[name]
+        phases[name] = {"ms_per_step": ms, "share": ms / tot_p,
+                        "tflops": (fl / (ms * 1e-3) / 1e12) if ms > 0 and fl > 0 else None}
+    dom = max(B.PHASES, key=lambda p: prof[p][0])
+    dms, dfl = prof[dom]
+    kern = {"sketch": "bat_sketch_kernel", "lupp": "bat_qrcp_kernel", "permute": "bat_perm_kernel",
+            "panel": "bat_panel_kernel", "trailing": "bat_trailing_kernel", "sketch_update": "bat_skupdate_kernel",
+            "other": "bat_init_kernel / bat_finish_kernel"}.get(dom, dom)
+    ach = dfl / (dms * 1e-3) / 1e12 if dms > 0 and dfl > 0 else None
+    roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+                "kernel": f"{kern} (dominant phase '{dom}', {dms:.1f} ms of {tot_p:.1f} ms in an eager profiled step)",
+                "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
+                "whole_step_tflops": flops / (statistics.mean(step_ms) * 1e-3) / 1e12}
+
+    # end to end: pinned host A in, factor, A / jpvt / tau / rank / truncation out
+    e2e = None
+    if not a.skip_e2e:
+        Ah0 = torch.empty(A0.numel(), dtype=torch.float64).pin_memory()
+        Ah0.copy_(A0)
+        Ah = torch.empty_like(Ah0).pin_memory()
+        jh = torch.empty(tot_j, dtype=torch.int64).pin_memory()
+        th = torch.empty(tot_j, dtype=torch.float64).pin_memory()
+        rh = torch.empty(a.batch, dtype=torch.int64).pin_memory()
+        trh = torch.empty(a.batch, dtype=torch.int64).pin_memory()
+        ems = []
+        for _ in range(max(1, min(a.steps, 3))):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.copy_(Ah0, non_blocking=True)
+            plan.factor(A, jpvt, tau, rk, tr, info, workspace=ws, use_graph=True)
+            Ah.copy_(A, non_blocking=True)
+            jh.copy_(jpvt, non_blocking=True)
+            th.copy_(tau, non_blocking=True)
+            rh.copy_(rk, non_blocking=True)
+            trh.copy_(tr, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ems.append(e0.elapsed_time(e1))
+        tot_e = max_over_ranks(sum(ems), dist, "cuda")
+        e2e = {"value": job_gflops(flops, len(ems), world, tot_e), "unit": "GFLOP/s",
+               "h2d_bytes_per_step": A0.numel() * 8,
+               "d2h_bytes_per_step": A0.numel() * 8 + tot_j * 16 + a.batch * 16, "steps": len(ems),
+               "entry_point": "bqrrp_batch_factor with pinned host copies in the timed region"}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.skip_cpu and world == 1:
+        gf, sample, cores = batched_cpu_sample(m, n, b, d, seeds)
+        cpu = {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+    lat = sorted(step_ms)
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    classes = {}
+    for lo, hi in [(0, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 1 << 30)]:
+        sel = (n >= lo) & (n < hi)
+        if sel.any():
+            classes[f"n in [{lo},{hi})"] = {"count": int(sel.sum()), "b": sorted(set(b[sel].tolist())),
+                                           "d": sorted(set(d[sel].tolist()))}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": max(3, a.warmup), "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched FP64 BQRRP: {a.batch} matrices, m log-uniform in [64, 1024], n log-uniform "
+                               f"in [32, m], U diag(sigma) V^T with sigma_k = 10^(-8(k-1)/(n-1)), dense Philox +-1 "
+                               f"sketch, CholQR panel, truncation at ||R22||_F <= 1e-8 ||A||_F, one CUDA graph per "
+                               f"step", "batch": a.batch, "trunc_tol": tol, "seed": a.seed,
+                   "total_canonical_gflop": flops / 1e9, "matrix_bytes": A0.numel() * 8,
+                   "l2": f"inputs larger than L2 (the batch is {A0.numel() * 8 / 1e9:.2f} GB, L2 126 MB)",
+                   "block_sizes": "fixed" if a.batch_b > 0 else "autotuned", "classes": classes,
+                   "autotune_s": t_tune, "autotune_best_ms": tuned_ms,
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "latency_ms": {"p50": statistics.median(lat), "p99": p99, "best": lat[0]},
+        "own_qr": None, "gpu_launches": launches, "launches_per_step": plan.launches(), "wall_s": t_wall,
+        "ranks": {"full_rank": int((ranks == n).sum()), "info_nonzero": int((infos != 0).sum()),
+                  "trunc_rank_mean": float(truncs.mean()), "n_mean": float(n.mean())},
+        "roofline": roofline, "phases": phases, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,6 +538,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, world, rank)
+        return
+    if a.workload == "batched":
+        run_batched(a, world, rank, local)
         return
     if a.only in ("gemm", "ozaki"):
         run_gemm(a)

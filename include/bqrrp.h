@@ -290,6 +290,87 @@ void bqrrp_profile_enable(int on);
 void bqrrp_profile_reset(void);
 int bqrrp_profile_read(bqrrp_profile* out);
 
+/* ------------------------------------------------------------------------
+ * Batched BQRRP: many independent FP64 matrices factored together.
+ *
+ * Each matrix i (m_i x n_i, m_i >= n_i) is factored exactly as bqrrp_factor
+ * does with the dense Philox +-1 sketch and the Alg. 3 CholQR panel, with its
+ * own block size b_i, sketch size d_i and seed_i; the paper (Alg. 1) treats one
+ * matrix, and the batch adds no arithmetic.  The matrices advance block by
+ * block in lock step: each phase of a block iteration is one persistent kernel
+ * over the whole batch, whose thread blocks take work items (a matrix or a
+ * tile of one) from a queue ordered largest first.  A matrix that finishes
+ * early (Sec. 3.7) is skipped by the later launches.
+ *
+ * Packed layout (both the caller and the library use it):
+ *  - A: matrix i starts at element offA_i = sum_{j<i} m_j n_j, column-major,
+ *    lda = m_i.  On exit it holds R and the reflectors (GEQP3 format).
+ *  - jpvt (int64), tau (double): matrix i starts at offJ_i = sum_{j<i} n_j;
+ *    n_i entries each; jpvt is 1-based on exit, tau beyond the rank is 0.
+ *  - rank, trunc_rank (int64), info (int32): one entry per matrix.
+ *
+ * Truncation (not in the paper; the residual measure of Sec. 6 used as a
+ * rule): trunc_rank_i = the smallest t in [0, rank_i] with
+ * ||R(t:rank_i, t:n_i)||_F <= trunc_tol * ||A_i||_F.
+ *
+ * Limits: n_i <= 4096, m_i <= 2^24, 1 <= b_i <= 128, b_i <= d_i <= 256;
+ * otherwise bqrrp_batch_plan_create returns -5 / -6 (b, d) or
+ * BQRRP_EUNSUPPORTED.  A matrix holding NaN/Inf is left untouched with
+ * info_i = BQRRP_ENUMERIC, rank_i = 0, identity jpvt and tau = 0.
+ * ------------------------------------------------------------------------ */
+typedef struct bqrrp_batch_plan_s* bqrrp_batch_plan;
+
+/* Build a plan on the host for the current device: the per-matrix records,
+ * the work queues of every launch and the workspace layout.  m, n, b, d,
+ * seed: HOST arrays of `batch` entries.  *plan receives a handle owned by the
+ * caller (free with bqrrp_batch_plan_destroy).  Synchronous; no device
+ * memory is touched. */
+int bqrrp_batch_plan_create(bqrrp_batch_plan* plan, int64_t batch, const int64_t* m, const int64_t* n,
+                            const int64_t* b, const int64_t* d, const uint64_t* seed, double trunc_tol);
+
+/* Device workspace bytes the plan needs (256-byte aligned workspace). */
+size_t bqrrp_batch_workspace_bytes(bqrrp_batch_plan plan);
+
+/* Factor the whole batch (device pointers; trunc_rank and info may be NULL).
+ * The first call with a given workspace uploads the plan into it
+ * (synchronous copy); later calls reuse it, so the workspace must not be
+ * modified between calls.  use_graph != 0 captures the launch sequence into a
+ * CUDA graph on the first call (on a private stream of the plan) and replays it
+ * on `stream` while (A, jpvt, tau, rank, trunc_rank, info, workspace) stay the
+ * same.  Asynchronous on
+ * `stream` otherwise; allocates nothing.  Errors: -1 bad plan, -2 null output,
+ * BQRRP_ENOMEM short workspace, BQRRP_ECUDA. */
+int bqrrp_batch_factor(bqrrp_batch_plan plan, double* A, int64_t* jpvt, double* tau, int64_t* rank,
+                       int64_t* trunc_rank, int32_t* info, void* workspace, size_t workspace_bytes, void* stream,
+                       int use_graph);
+
+/* Release a plan (and its captured graph).  NULL is ignored. */
+void bqrrp_batch_plan_destroy(bqrrp_batch_plan plan);
+
+/* Number of kernel launches one bqrrp_batch_factor call issues. */
+int bqrrp_batch_launches(bqrrp_batch_plan plan);
+
+/* Algorithmic FLOPs of one bqrrp_batch_factor call in profiler phase `phase`
+ * (-1: all phases), counted as if every block kept all its columns.  With the
+ * profiler on (bqrrp_profile_enable), a call without graph capture records
+ * each launch's device time and adds per-phase times and these FLOPs to the
+ * profile, synchronizing `stream`; phase 1 then covers all of Alg. 2 (LU,
+ * piv_transform, gather, Householder QR, tri_rank), which runs as one kernel. */
+double bqrrp_batch_flops(bqrrp_batch_plan plan, int phase);
+
+/* Autotuner: choose b_i = min(beta_c, n_i) with beta_c from {16, 32, 64, 128}
+ * per size class c of n_i
+ * ([0,64), [64,128), ..., [1024, inf)) by timing each class alone on the
+ * device, then d_i = ceil(gamma * b_i) with gamma from {1.25, 1.5} by timing
+ * the whole batch.  A (device, packed as above) is read only: every trial
+ * factors a copy held in the workspace.  m, n, seed, b_out, d_out: HOST
+ * arrays; best_ms (host, nullable) receives the best whole-batch time.
+ * Synchronizes `stream`.  workspace: bqrrp_batch_autotune_workspace_bytes(). */
+size_t bqrrp_batch_autotune_workspace_bytes(int64_t batch, const int64_t* m, const int64_t* n);
+int bqrrp_batch_autotune(int64_t batch, const int64_t* m, const int64_t* n, const uint64_t* seed, const double* A,
+                         double trunc_tol, void* workspace, size_t workspace_bytes, void* stream, int64_t* b_out,
+                         int64_t* d_out, double* best_ms);
+
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bqrrp_launch_counter(void);
 

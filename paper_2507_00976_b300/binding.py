@@ -86,6 +86,15 @@ _SIGS = {
     "bqrrp_dgemm_ozaki_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_sketch_apply_tc": ([_i64, _i64, _i64, _vp, _i64, _u64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_sketch_apply_tc_workspace": ([_i64, _i64, _i64], _sz),
+    "bqrrp_batch_plan_create": ([ctypes.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _d], ctypes.c_int),
+    "bqrrp_batch_workspace_bytes": ([_vp], _sz),
+    "bqrrp_batch_factor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_int], ctypes.c_int),
+    "bqrrp_batch_plan_destroy": ([_vp], None),
+    "bqrrp_batch_launches": ([_vp], ctypes.c_int),
+    "bqrrp_batch_flops": ([_vp, ctypes.c_int], _d),
+    "bqrrp_batch_autotune_workspace_bytes": ([_i64, _vp, _vp], _sz),
+    "bqrrp_batch_autotune": ([_i64, _vp, _vp, _vp, _vp, _d, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(_d)],
+                             ctypes.c_int),
     "bqrrp_profile_enable": ([ctypes.c_int], None),
     "bqrrp_profile_reset": ([], None),
     "bqrrp_profile_read": ([ctypes.POINTER(Profile)], ctypes.c_int),
@@ -405,3 +414,107 @@ def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64
                      PRECISION_FP64 if precision == "fp64" else PRECISION_MIXED)
     rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
     return F, jpvt[:n], tau[:n], rank
+
+
+# ----------------------------------------------------------------- batched BQRRP
+def _host_i64(x):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int64))
+
+
+def _host_u64(x):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class BatchPlan:
+    """Owner of a ``bqrrp_batch_plan`` handle (host arrays m, n, b, d, seed;
+    the packed layout of ``workloads.batch_offsets``)."""
+
+    def __init__(self, m, n, b, d, seeds, trunc_tol=1e-8):
+        self.m, self.n, self.b, self.d = _host_i64(m), _host_i64(n), _host_i64(b), _host_i64(d)
+        self.seeds = _host_u64(seeds)
+        self.batch = len(self.m)
+        self.trunc_tol = float(trunc_tol)
+        h = _vp()
+        rc = lib().bqrrp_batch_plan_create(ctypes.byref(h), self.batch, _np_ptr(self.m), _np_ptr(self.n),
+                                           _np_ptr(self.b), _np_ptr(self.d), _np_ptr(self.seeds), self.trunc_tol)
+        _check("bqrrp_batch_plan_create", rc)
+        self.handle = h
+        self.workspace = None
+
+    def workspace_bytes(self):
+        return int(lib().bqrrp_batch_workspace_bytes(self.handle))
+
+    def launches(self):
+        return int(lib().bqrrp_batch_launches(self.handle))
+
+    def flops(self, phase=-1):
+        return float(lib().bqrrp_batch_flops(self.handle, int(phase)))
+
+    def factor(self, A, jpvt, tau, rank, trunc_rank=None, info=None, workspace=None, use_graph=False, stream=None):
+        """A: packed float64 (in/out); jpvt int64, tau float64 (sum n); rank,
+        trunc_rank int64 and info int32 (one per matrix).  Device tensors."""
+        if workspace is None:
+            if self.workspace is None:
+                self.workspace = _workspace(self.workspace_bytes(), A.device)
+            workspace = self.workspace
+        rc = lib().bqrrp_batch_factor(self.handle, _ptr(A), _ptr(jpvt), _ptr(tau), _ptr(rank), _ptr(trunc_rank),
+                                      _ptr(info), _ptr(workspace), workspace.numel(), _stream(stream),
+                                      1 if use_graph else 0)
+        _check("bqrrp_batch_factor", rc)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().bqrrp_batch_plan_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bqrrp_batch_autotune(m, n, seeds, A, trunc_tol=1e-8, stream=None):
+    """Pick b and d per matrix by timing on the device (A packed, read only).
+    Returns (b, d, best_ms) with b, d numpy int64 arrays."""
+    import numpy as np
+    m, n, sd = _host_i64(m), _host_i64(n), _host_u64(seeds)
+    batch = len(m)
+    nbytes = int(lib().bqrrp_batch_autotune_workspace_bytes(batch, _np_ptr(m), _np_ptr(n)))
+    ws = _workspace(nbytes, A.device)
+    b = np.zeros(batch, dtype=np.int64)
+    d = np.zeros(batch, dtype=np.int64)
+    best = _d(0.0)
+    rc = lib().bqrrp_batch_autotune(batch, _np_ptr(m), _np_ptr(n), _np_ptr(sd), _ptr(A), float(trunc_tol), _ptr(ws),
+                                    ws.numel(), _stream(stream), _np_ptr(b), _np_ptr(d), ctypes.byref(best))
+    _check("bqrrp_batch_autotune", rc)
+    del ws
+    return b, d, best.value
+
+
+def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False, stream=None):
+    """Factor a copy of a packed batch.  Returns (F packed, jpvt, tau, rank,
+    trunc_rank, info) as device tensors."""
+    torch = _torch()
+    import numpy as np
+    F = torch.as_tensor(A_packed, dtype=torch.float64).to("cuda").clone()
+    tot_j = int(np.sum(np.asarray(n, dtype=np.int64)))
+    nb = len(m)
+    jpvt = torch.empty(max(tot_j, 1), dtype=torch.int64, device=F.device)
+    tau = torch.empty(max(tot_j, 1), dtype=torch.float64, device=F.device)
+    rank = torch.empty(max(nb, 1), dtype=torch.int64, device=F.device)
+    trunc = torch.empty(max(nb, 1), dtype=torch.int64, device=F.device)
+    info = torch.empty(max(nb, 1), dtype=torch.int32, device=F.device)
+    plan = BatchPlan(m, n, b, d, seeds, trunc_tol)
+    try:
+        plan.factor(F, jpvt, tau, rank, trunc, info, use_graph=use_graph, stream=stream)
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    finally:
+        plan.close()
+    return F, jpvt, tau, rank[:nb], trunc[:nb], info[:nb]

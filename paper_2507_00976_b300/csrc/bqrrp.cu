@@ -56,6 +56,20 @@ Profiler g_prof;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+bool profile_on() {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    return g_prof.on;
+}
+
+void profile_add(const double* ms, const double* flops) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (int i = 0; i < BQRRP_NPHASES; ++i) {
+        g_prof.ms[i] += ms[i];
+        g_prof.flops[i] += flops[i];
+    }
+    g_prof.calls += 1;
+}
+
 // Per-call recorder (only active when the profiler is on).
 struct PhaseRec {
     bool on = false;

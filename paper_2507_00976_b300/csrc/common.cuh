@@ -35,6 +35,10 @@ const char* get_error();
     } while (0)
 
 void count_launch();
+// Phase profiler (bqrrp_profile_*): whether it is on, and adding one call's
+// per-phase device milliseconds and algorithmic FLOPs to its totals.
+bool profile_on();
+void profile_add(const double* ms, const double* flops);
 
 #define BQ_LAUNCH_CHECK()                                                          \
     do {                                                                           \

@@ -58,3 +58,15 @@ def test_argument_errors_follow_info_convention():
     assert L.bqrrp_sketch_operator(4, 4, 0, 1, 9, None, 4, None) == -5
     assert L.bqrrp_dgemm(b"X", b"N", 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None, 0, None) == -1
     assert L.bqrrp_geqrf(4, 4, None, 2, None, 0, None, 0, None) == -4
+
+
+def test_batched_plan_rejects_bad_shapes_before_touching_a_device():
+    """bqrrp_batch_plan_create validates every matrix on the host first."""
+    import numpy as np
+    one = np.array([1], dtype=np.int64)
+    cases = [((5, 8, 4, 5), -3), ((50, 8, 200, 250), -5), ((50, 8, 16, 8), -6),
+             ((9000, 5000, 16, 20), B.EUNSUPPORTED)]
+    for (m, n, b, d), code in cases:
+        with pytest.raises(B.BqrrpError) as e:
+            B.BatchPlan(np.array([m]), np.array([n]), np.array([b]), np.array([d]), one)
+        assert e.value.code == code
