@@ -114,10 +114,13 @@ def parse():
                    help="gemm: time the library's FP64 GEMM alone (C -= A B, the trailing-update shape); "
                         "geqrf: time the library's own unpivoted QR alone on the m x n input")
     p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
-    p.add_argument("--workload", choices=["single", "batched"], default="single",
+    p.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                    help="batched: 4096 independent matrices (m log-uniform in [64, 1024], n log-uniform in "
                         "[32, m], sigma_k = 10^(-8(k-1)/(n-1))), autotuned b and d, one CUDA graph per step")
     p.add_argument("--batch", type=int, default=4096)
+    p.add_argument("--requests", type=int, default=200,
+                   help="serving: requests per load level (a bounded sample of the 20000-request stream)")
+    p.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.2])
     p.add_argument("--batch-b", type=int, default=0,
                    help="batched: fixed block size for every matrix instead of the autotuner (d = ceil(1.25 b))")
     a = p.parse_args()
@@ -531,6 +534,133 @@ def run_batched(a, world, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ serving workload
+SERVING_SHAPES = [(256, 256, 64, 80), (1024, 512, 64, 80), (4096, 2048, 256, 320), (8192, 4096, 512, 640)]
+SERVING_WEIGHTS = [0.5, 0.3, 0.15, 0.05]
+
+
+def run_serving(a, world, rank, local):
+    """Poisson-arrival stream of factorization requests of mixed shapes through
+    the library's request loop (bqrrp_server_*), at several offered loads."""
+    import numpy as np
+    import torch
+
+    from paper_2507_00976_b300 import binding as B
+    from paper_2507_00976_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    seed = rank_seed(a.seed, rank)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tol = 1e-8
+    # a pool of distinct inputs per shape (pinned host memory), spectra
+    # geometric from 1 down to a decay drawn uniformly in exponent from [1e-14, 1e-4]
+    per_shape = [6, 4, 3, 2]
+    inputs = []
+    for si, ((m, n, b, d), k) in enumerate(zip(SERVING_SHAPES, per_shape)):
+        lst = []
+        for j in range(k):
+            decay = 10.0 ** rng.uniform(-14.0, -4.0)
+            sig = decay ** (np.arange(n) / (n - 1))
+            Ad = W.spectrum_torch(m, n, sig, seed * 100 + si * 10 + j)
+            Ah = torch.empty((n, m), dtype=torch.float64).pin_memory()
+            Ah.copy_(Ad.t())
+            del Ad
+            lst.append(Ah)
+        inputs.append(lst)
+    torch.cuda.empty_cache()
+    outs = []
+    for (m, n, b, d) in SERVING_SHAPES:
+        outs.append((torch.empty((n, m), dtype=torch.float64).pin_memory(),
+                     torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory()))
+    budget = 120 << 30
+    S = B.Server(budget, 8 << 30, trunc_tol=tol, small_max_elems=1 << 20)
+
+    def draw(count, rng_):
+        kinds = rng_.choice(len(SERVING_SHAPES), size=count, p=SERVING_WEIGHTS)
+        picks = [int(rng_.integers(len(inputs[k]))) for k in kinds]
+        return list(zip(kinds.tolist(), picks))
+
+    def run(stream, gaps):
+        """Submit stream[i] at cumulative time sum(gaps[:i+1]) after start; returns completions."""
+        t_base = S.clock()
+        done, sub_t = [], {}
+        arrival = t_base
+        for i, (k, j) in enumerate(stream):
+            arrival += gaps[i]
+            while S.clock() < arrival:
+                done += S.poll(256, 0.0)
+                time.sleep(min(0.0005, max(0.0, arrival - S.clock())))
+            m, n, b, d = SERVING_SHAPES[k]
+            Ao, jo, to = outs[k]
+            rid = len(sub_t) + 1_000_000 * run.calls
+            sub_t[rid] = (arrival, k)
+            S.submit(rid, m, n, b, d, 7 + i, inputs[k][j], Ao, jo, to)
+        S.drain()
+        done += S.poll(100000, 0.0)
+        run.calls += 1
+        return done, sub_t
+
+    run.calls = 0
+    # warm-up: one of each shape
+    run([(k, 0) for k in range(len(SERVING_SHAPES))], [0.0] * len(SERVING_SHAPES))
+    l0 = B.bqrrp_launch_counter()
+    # capacity: the sample offered all at once
+    base_stream = draw(a.requests, rng)
+    done, sub = run(base_stream, [0.0] * len(base_stream))
+    span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
+    capacity = len(done) / span
+    flops_per_req = float(np.mean([canonical_flops(*SERVING_SHAPES[k][:2]) for k, _ in base_stream]))
+    loads = {}
+    for load in a.loads:
+        lam = load * capacity
+        gaps = rng.exponential(1.0 / lam, size=len(base_stream))
+        gaps[0] = 0.0
+        done, sub = run(draw(len(base_stream), rng), gaps)
+        lat = np.array([(c["t_done"] - sub[c["id"]][0]) * 1e3 for c in done])
+        kinds = np.array([sub[c["id"]][1] for c in done])
+        fl = sum(canonical_flops(*SERVING_SHAPES[sub[c["id"]][1]][:2]) for c in done)
+        t0 = min(sub[c["id"]][0] for c in done)
+        t1 = max(c["t_done"] for c in done)
+        per_shape = {}
+        for k, (m, n, _, _) in enumerate(SERVING_SHAPES):
+            sel = kinds == k
+            if sel.any():
+                per_shape[f"{m}x{n}"] = {"count": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                                         "p99_ms": float(np.percentile(lat[sel], 99))}
+        loads[str(load)] = {"offered_req_per_s": lam, "completed": len(done),
+                            "gflops": fl / (t1 - t0) / 1e9, "p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99)),
+                            "status_nonzero": int(sum(1 for c in done if c["status"] != 0)),
+                            "per_shape": per_shape}
+    st = S.stats()
+    launches = B.bqrrp_launch_counter() - l0
+    S.close()
+    if rank != 0:
+        return
+    hi = loads[str(max(a.loads))]
+    mid = loads[str(sorted(a.loads)[len(a.loads) // 2])]
+    line = {
+        "metric": METRIC, "value": hi["gflops"], "unit": "GFLOP/s", "n_gpus": world, "steps": len(a.loads),
+        "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serving loop: Poisson arrivals of FP64 factorization requests, shapes 256x256 / "
+                               "1024x512 / 4096x2048 / 8192x4096 with weights 0.5/0.3/0.15/0.05, spectra geometric "
+                               "from 1 to a decay uniform in exponent on [1e-14, 1e-4], truncation 1e-8, admission by "
+                               "a 120 GB HBM budget, continuous batching of the small shapes",
+                   "requests_per_load": len(base_stream), "sample": f"{len(base_stream)} requests per load level "
+                   f"(a bounded sample of the 20000-request stream)", "hbm_budget_bytes": budget,
+                   "block_sizes": {f"{m}x{n}": [b, d] for m, n, b, d in SERVING_SHAPES},
+                   "capacity_req_per_s": capacity, "mean_gflop_per_request": flops_per_req / 1e9,
+                   "parallelism": "single"},
+        "latency_ms": {"p50": mid["p50_ms"], "p99": mid["p99_ms"], "at_load": sorted(a.loads)[len(a.loads) // 2]},
+        "loads": loads, "server": st, "e2e": {"value": hi["gflops"], "unit": "GFLOP/s",
+                                             "note": "every request is copied host->device at admission and its "
+                                                     "R, reflectors, jpvt and tau device->host at completion"},
+        "gpu_launches": launches, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -541,6 +671,9 @@ def main():
         return
     if a.workload == "batched":
         run_batched(a, world, rank, local)
+        return
+    if a.workload == "serving":
+        run_serving(a, world, rank, local)
         return
     if a.only in ("gemm", "ozaki"):
         run_gemm(a)

@@ -371,6 +371,79 @@ int bqrrp_batch_autotune(int64_t batch, const int64_t* m, const int64_t* n, cons
                          double trunc_tol, void* workspace, size_t workspace_bytes, void* stream, int64_t* b_out,
                          int64_t* d_out, double* best_ms);
 
+/* ------------------------------------------------------------------------
+ * Request loop (serving layer; the paper factors one matrix per call).
+ *
+ * A server owns one device pool of hbm_budget_bytes, allocated once at
+ * creation: a request arena (hbm_budget_bytes - workspace_bytes) that holds
+ * every admitted request's state (its matrix, factored in place, jpvt, tau)
+ * from admission until its results are copied back, and a workspace arena
+ * (workspace_bytes) for the job that is running.  A worker thread admits
+ * submitted requests first-come-first-served whenever their state fits, then
+ * alternates between two lanes on one CUDA stream:
+ *  - small requests (m*n <= small_max_elems) are factored together in one
+ *    batched call (bqrrp_batch_* kernels, each request addressed in place);
+ *    requests arriving meanwhile join the next batch;
+ *  - larger requests run one at a time through the single-matrix path.
+ * Each completed request reports its rank and its truncation rank (smallest t
+ * with ||R(t:rank, t:n)||_F <= trunc_tol * ||A||_F) and four timestamps in
+ * seconds on the server's clock (bqrrp_server_clock).
+ * flags: BQRRP_SERVER_DRYRUN replaces all GPU work by a sleep of
+ * (2mn^2 - 2n^3/3) / (dry_gflops * 1e9) seconds and allocates no device
+ * memory (host-side tests of admission and batching).
+ * ------------------------------------------------------------------------ */
+#define BQRRP_SERVER_DRYRUN 1
+
+typedef struct bqrrp_request {
+    uint64_t id;              /* caller's tag, echoed in the completion                  */
+    int64_t m, n, b, d;       /* shape (m >= n >= 1), block size, sketch rows            */
+    uint64_t seed;            /* sketch seed                                              */
+    const double* A_host;     /* m x n column-major (lda = m), HOST; read at admission   */
+    double* A_out_host;       /* nullable HOST m x n: R above the diagonal, reflectors below */
+    int64_t* jpvt_out_host;   /* nullable HOST n: 1-based column permutation              */
+    double* tau_out_host;     /* nullable HOST n: reflector scalars                       */
+} bqrrp_request;
+
+typedef struct bqrrp_completion {
+    uint64_t id;
+    int32_t status;           /* 0, or a BQRRP_E* code (BQRRP_ENUMERIC: NaN/Inf input)    */
+    int32_t lane;             /* 0 small (batched), 1 large (single-matrix)               */
+    int64_t rank, trunc_rank;
+    double t_submit, t_admit, t_start, t_done;
+} bqrrp_completion;
+
+typedef struct bqrrp_server_stats {
+    int64_t submitted, completed, batches, max_batch, large_runs;
+    int64_t peak_request_bytes;   /* most request-arena bytes ever held at once            */
+    int64_t request_arena_bytes;
+    int64_t in_use_bytes;
+} bqrrp_server_stats;
+
+typedef struct bqrrp_server_s* bqrrp_server;
+
+/* Create a server on the current device (hbm_budget_bytes >= workspace_bytes
+ * + 1 MiB).  Errors: -1 null out, -2 sizes, -4 tolerance, BQRRP_ENOMEM when the
+ * pool cannot be allocated. */
+int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t workspace_bytes, double trunc_tol,
+                        int64_t small_max_elems, int flags, double dry_gflops);
+/* Queue a request (the descriptor is copied; the host buffers must stay valid
+ * until its completion is returned).  Small-lane requests need b <= 128,
+ * d <= 256, n <= 4096.  Returns -2 on a bad request, BQRRP_ENOMEM when its
+ * state can never fit in the request arena. */
+int bqrrp_server_submit(bqrrp_server srv, const bqrrp_request* req);
+/* Move up to max_out completions into out (waiting up to wait_s seconds for
+ * the first one); returns how many. */
+int bqrrp_server_poll(bqrrp_server srv, bqrrp_completion* out, int max_out, double wait_s);
+/* Block until every submitted request has completed. */
+int bqrrp_server_drain(bqrrp_server srv);
+/* Seconds since the server was created (the clock of the timestamps). */
+double bqrrp_server_clock(bqrrp_server srv);
+/* Message of the last job that failed on the server's worker ("" if none). */
+const char* bqrrp_server_last_error(bqrrp_server srv);
+int bqrrp_server_get_stats(bqrrp_server srv, bqrrp_server_stats* out);
+/* Stop the worker after the queued work, release the pool. */
+void bqrrp_server_destroy(bqrrp_server srv);
+
 /* Number of kernel launches the library has issued since it was loaded. */
 int64_t bqrrp_launch_counter(void);
 

@@ -48,6 +48,25 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", _d * NPHASES), ("flops", _d * NPHASES), ("calls", _i64)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("id", _u64), ("m", _i64), ("n", _i64), ("b", _i64), ("d", _i64), ("seed", _u64),
+                ("A_host", _vp), ("A_out_host", _vp), ("jpvt_out_host", _vp), ("tau_out_host", _vp)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", _u64), ("status", ctypes.c_int32), ("lane", ctypes.c_int32), ("rank", _i64),
+                ("trunc_rank", _i64), ("t_submit", _d), ("t_admit", _d), ("t_start", _d), ("t_done", _d)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("batches", _i64), ("max_batch", _i64),
+                ("large_runs", _i64), ("peak_request_bytes", _i64), ("request_arena_bytes", _i64),
+                ("in_use_bytes", _i64)]
+
+
+SERVER_DRYRUN = 1
+
+
 class BqrrpError(RuntimeError):
     def __init__(self, fn, code, msg):
         super().__init__(f"{fn} returned {code}: {msg}")
@@ -95,6 +114,14 @@ _SIGS = {
     "bqrrp_batch_autotune_workspace_bytes": ([_i64, _vp, _vp], _sz),
     "bqrrp_batch_autotune": ([_i64, _vp, _vp, _vp, _vp, _d, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(_d)],
                              ctypes.c_int),
+    "bqrrp_server_create": ([ctypes.POINTER(_vp), _sz, _sz, _d, _i64, ctypes.c_int, _d], ctypes.c_int),
+    "bqrrp_server_submit": ([_vp, ctypes.POINTER(Request)], ctypes.c_int),
+    "bqrrp_server_poll": ([_vp, ctypes.POINTER(Completion), ctypes.c_int, _d], ctypes.c_int),
+    "bqrrp_server_drain": ([_vp], ctypes.c_int),
+    "bqrrp_server_clock": ([_vp], _d),
+    "bqrrp_server_last_error": ([_vp], ctypes.c_char_p),
+    "bqrrp_server_get_stats": ([_vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "bqrrp_server_destroy": ([_vp], None),
     "bqrrp_profile_enable": ([ctypes.c_int], None),
     "bqrrp_profile_reset": ([], None),
     "bqrrp_profile_read": ([ctypes.POINTER(Profile)], ctypes.c_int),
@@ -518,3 +545,74 @@ def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False,
     finally:
         plan.close()
     return F, jpvt, tau, rank[:nb], trunc[:nb], info[:nb]
+
+
+# ----------------------------------------------------------------- request loop
+def _host_ptr(x):
+    """Address of a host buffer (numpy array or CPU torch tensor), or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Server:
+    """Owner of a ``bqrrp_server``.  Host buffers handed to ``submit`` are kept
+    alive here until their completion has been polled."""
+
+    def __init__(self, hbm_budget_bytes, workspace_bytes, trunc_tol=1e-8, small_max_elems=1 << 20, dry=False,
+                 dry_gflops=1000.0):
+        h = _vp()
+        rc = lib().bqrrp_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(workspace_bytes),
+                                       float(trunc_tol), int(small_max_elems), SERVER_DRYRUN if dry else 0,
+                                       float(dry_gflops))
+        _check("bqrrp_server_create", rc)
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, rid, m, n, b, d, seed, A_host=None, A_out=None, jpvt_out=None, tau_out=None):
+        r = Request()
+        r.id, r.m, r.n, r.b, r.d, r.seed = int(rid), int(m), int(n), int(b), int(d), int(seed)
+        r.A_host, r.A_out_host = _host_ptr(A_host), _host_ptr(A_out)
+        r.jpvt_out_host, r.tau_out_host = _host_ptr(jpvt_out), _host_ptr(tau_out)
+        self._keep[int(rid)] = (A_host, A_out, jpvt_out, tau_out)
+        rc = lib().bqrrp_server_submit(self.handle, ctypes.byref(r))
+        if rc != 0:
+            self._keep.pop(int(rid), None)
+        _check("bqrrp_server_submit", rc)
+
+    def poll(self, max_out=256, wait_s=0.0):
+        buf = (Completion * max_out)()
+        k = lib().bqrrp_server_poll(self.handle, buf, max_out, float(wait_s))
+        out = []
+        for i in range(k):
+            c = buf[i]
+            self._keep.pop(int(c.id), None)
+            out.append({f: getattr(c, f) for f, _ in Completion._fields_})
+        return out
+
+    def drain(self):
+        _check("bqrrp_server_drain", lib().bqrrp_server_drain(self.handle))
+
+    def clock(self):
+        return float(lib().bqrrp_server_clock(self.handle))
+
+    def last_error(self):
+        return lib().bqrrp_server_last_error(self.handle).decode()
+
+    def stats(self):
+        st = ServerStats()
+        _check("bqrrp_server_get_stats", lib().bqrrp_server_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().bqrrp_server_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -59,7 +59,8 @@ constexpr int RT = 32;           // rows per trailing-update chunk
 struct BatMat {                  // per matrix, written by the host, read-only on the device
     i64 m, n, b, d;
     i64 offA;                    // element offset of A (column-major, lda = m)
-    i64 offJ;                    // element offset of jpvt and tau
+    i64 offJ;                    // element offset of jpvt
+    i64 offT;                    // element offset of tau
     i64 offSk;                   // sketch d x n (ld d) in the double workspace
     i64 offW;                    // work d x n (ld d): LU copy, then R^sk
     i64 offY;                    // explicit Y, m x b (ld m)
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(BT) bat_init_kernel(BatArgs a, Slot sl, int sl
             __syncthreads();
         }
         int64_t* J = a.jpvt + M.offJ;
-        double* tau = a.tau + M.offJ;
+        double* tau = a.tau + M.offT;
         for (i64 j = threadIdx.x; j < M.n; j += BT) {
             J[j] = j;
             tau[j] = 0.0;
@@ -807,7 +808,7 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
             }
         }
         __syncthreads();
-        double* tau = a.tau + M.offJ + s;
+        double* tau = a.tau + M.offT + s;
         for (int j = threadIdx.x; j < k; j += BT) tau[j] = Tb[j + (i64)j * b];
 
         // ---- V = Y T^T (rows x k), so that the trailing update is
@@ -1133,8 +1134,11 @@ double launch_flops(BatchPlan::Kind kind, const BatMat& M, i64 it) {
 
 }  // namespace
 
-int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
-                      const uint64_t* seed, double tol) {
+// Plan with caller-chosen element offsets of every matrix in A (lda = m_i),
+// jpvt and tau (all three may be null: the packed layout).
+int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
+                         const uint64_t* seed, double tol, const i64* offA_in, const i64* offJ_in,
+                         const i64* offT_in) {
     if (!out) { set_error("plan pointer is null"); return -1; }
     *out = nullptr;
     if (batch < 0) { set_error("batch < 0"); return -2; }
@@ -1170,8 +1174,9 @@ int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, co
         M.b = b[i];
         M.d = d[i];
         M.seed = seed[i];
-        M.offA = offA;
-        M.offJ = offJ;
+        M.offA = offA_in ? offA_in[i] : offA;
+        M.offJ = offJ_in ? offJ_in[i] : offJ;
+        M.offT = offT_in ? offT_in[i] : offJ;
         offA += m[i] * n[i];
         offJ += n[i];
         const i64 nn = std::max<i64>(n[i], 1);
@@ -1254,7 +1259,9 @@ int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, co
         {(const void*)bat_panel_kernel, P->dsm_panel}, {(const void*)bat_trailing_kernel, P->dsm_trail},
         {(const void*)bat_skupdate_kernel, 0},    {(const void*)bat_finish_kernel, 0}};
     for (int q = 0; q < 8; ++q) {
-        if (ki[q].dsm > 48 * 1024) {
+        if (ki[q].dsm > 0) {
+            // always set: dynamic plus static shared memory may exceed the 48 KiB
+            // default even when the dynamic part alone does not
             cudaError_t e = cudaFuncSetAttribute(ki[q].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ki[q].dsm);
             if (e != cudaSuccess) {
                 set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -1273,6 +1280,11 @@ int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, co
     }
     *out = P;
     return 0;
+}
+
+int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
+                      const uint64_t* seed, double tol) {
+    return batch_plan_create_ex(out, batch, m, n, b, d, seed, tol, nullptr, nullptr, nullptr);
 }
 
 size_t batch_plan_bytes(const BatchPlan* P) { return P ? P->total : 0; }

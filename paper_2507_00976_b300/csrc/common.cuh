@@ -181,6 +181,15 @@ __device__ inline bool grid_barrier(DevStatus* st, unsigned int nblocks) {
     return s_ok != 0;
 }
 
+// ------------------------------------------------------------------ batched plans (batched.cu)
+struct BatchPlan;
+int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
+                         const uint64_t* seed, double tol, const i64* offA, const i64* offJ, const i64* offT);
+size_t batch_plan_bytes(const BatchPlan* P);
+int batch_factor(BatchPlan* P, double* A, int64_t* jpvt, double* tau, int64_t* rank, int64_t* trunc,
+                 int32_t* info, void* ws, size_t ws_bytes, cudaStream_t stream, int use_graph);
+void batch_plan_destroy(BatchPlan* P);
+
 // ------------------------------------------------------------------ launchers (internal API)
 struct Ctx {
     cudaStream_t stream;
