@@ -22,6 +22,8 @@
 // products S A_q.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace bq {
@@ -303,13 +305,37 @@ int launch_mma(const Ctx& c, OzArgs a, i64 Mp, i64 Np) {
     return 0;
 }
 
+// The tcgen05 kernel (ozaki_tc.cu) runs the slice products unless
+// BQRRP_OZAKI_MMA is set in the environment, which selects the mma.sync
+// kernel above (kept for side-by-side timing).
+bool use_tcgen05() {
+    static const bool tc = (getenv("BQRRP_OZAKI_MMA") == nullptr);
+    return tc;
+}
+
+// After a launch on a context without a status block: read the kernel's
+// timeout flag (one synchronization) and report it.
+int check_flag(const Ctx& c, int* flag) {
+    if (c.st) return 0;
+    int h = 0;
+    BQ_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    BQ_CUDA(cudaStreamSynchronize(c.stream));
+    if (h) { set_error("tensor-core slice GEMM: a pipeline wait timed out"); return BQRRP_ETIMEOUT; }
+    return 0;
+}
+
 }  // namespace
+
+int ozaki_tc_gemm(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
+                  i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err);
+int ozaki_tc_sketch(const Ctx& c, const __nv_bfloat16* Ss, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
+                    i64 N, const int* ea, const int* eb, double* C, i64 ldc, int* err);
 
 // Workspace (bytes) for ozaki_gemm / ozaki_sketch on these sizes.
 size_t ozaki_ws_bytes(i64 M, i64 N, i64 K, int sa) {
     const i64 Mp = rup(imax(M, 1), OBM), Np = rup(imax(N, 1), OBN), Kp = rup(imax(K, 1), OBK);
     return ((size_t)sa * Mp * Kp + (size_t)kSlices * Np * Kp) * sizeof(__nv_bfloat16) +
-           (size_t)(Mp + Np) * sizeof(int) + 1024;
+           (size_t)(Mp + Np) * sizeof(int) + 2048;
 }
 
 // C = alpha op(A) op(B) + beta C, FP64 in and out, products on the bf16 tensor cores.
@@ -326,6 +352,7 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
     __nv_bfloat16* Bs = ar.take<__nv_bfloat16>((size_t)kSlices * Np * Kp);
     int* ea = ar.take<int>((size_t)Mp);
     int* eb = ar.take<int>((size_t)Np);
+    int* flag = ar.take<int>(1);
     if (!ar.ok()) { set_error("ozaki_gemm: workspace too small"); return BQRRP_ENOMEM; }
     // exponents: rows of op(A), columns of op(B) (= rows of op(B)^T)
     row_exp_kernel<<<(unsigned)M, 256, 0, c.stream>>>(M, K, A, lda, ta ? 1 : 0, ea);
@@ -345,7 +372,11 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
     a.As = As; a.Bs = Bs; a.ea = ea; a.eb = eb;
     a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
     a.kc = 256;
-    return launch_mma<kSlices, kSlices, kTmax>(c, a, Mp, Np);
+    if (!use_tcgen05()) return launch_mma<kSlices, kSlices, kTmax>(c, a, Mp, Np);
+    int* err = c.st ? &c.st->err_timeout : flag;
+    if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
+    BQ_TRY(ozaki_tc_gemm(c, As, Mp, Bs, Np, Kp, M, N, ea, eb, alpha, beta, C, ldc, err));
+    return check_flag(c, flag);
 }
 
 int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
@@ -371,6 +402,7 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     __nv_bfloat16* Bs = ar.take<__nv_bfloat16>((size_t)kSlices * Np * Kp);
     int* ea = ar.take<int>((size_t)Mp);
     int* eb = ar.take<int>((size_t)Np);
+    int* flag = ar.take<int>(1);
     if (!ar.ok()) { set_error("ozaki_sketch: workspace too small"); return BQRRP_ENOMEM; }
     const unsigned blocks = (unsigned)imax(1, imin(cdiv(Mp * Kp, 256), 16LL * c.dev.sms));
     sketch_slice_kernel<<<blocks, 256, 0, c.stream>>>(d, m, Mp, Kp, seed, Ss);
@@ -388,7 +420,11 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     a.As = Ss; a.Bs = Bs; a.ea = ea; a.eb = eb;
     a.alpha = 1.0; a.beta = 0.0; a.C = Msk; a.ldc = ldsk;
     a.kc = (i64)1 << 17;
-    return launch_mma<1, kSlices, kSlices - 1>(c, a, Mp, Np);
+    if (!use_tcgen05()) return launch_mma<1, kSlices, kSlices - 1>(c, a, Mp, Np);
+    int* err = c.st ? &c.st->err_timeout : flag;
+    if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
+    BQ_TRY(ozaki_tc_sketch(c, Ss, Mp, Bs, Np, Kp, d, n, ea, eb, Msk, ldsk, err));
+    return check_flag(c, flag);
 }
 
 }  // namespace bq
