@@ -63,11 +63,11 @@ def mixed_roofline(fp64eq_tflops):
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "kernel": ("ozaki_mma_kernel (bf16 slice products, mma.sync m16n8k16)"
                                         if os.environ.get("BQRRP_OZAKI_MMA") else
-                                        "ozaki_tc_kernel (bf16 slice products: tcgen05.mma kind::f16 M=128 N=256, "
-                                        "TMA-fed 128B-swizzled smem, FP32 accumulators in TMEM)"),
+                                        "ozaki_tc_kernel (bf16 slice products: persistent, tcgen05.mma kind::f16 "
+                                        "M=128 N<=256 stacked planes, TMA-fed 128B-swizzled smem, FP32 accumulators "
+                                        "in TMEM)"),
             "fp64_equivalent_tflops": fp64eq_tflops, "peak_source": src,
-            "counting": "53 slice products per FP64 product (the stacked N=256 MMAs also form products that are "
-                        "discarded; they are not counted)"}
+            "counting": "53 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
 
 
 def canonical_flops(m, n):

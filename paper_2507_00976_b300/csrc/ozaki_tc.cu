@@ -2,7 +2,8 @@
 // the 5th-generation tensor cores: tcgen05.mma with operands staged in shared
 // memory by TMA and FP32 accumulators in tensor memory (TMEM).
 //
-// One CTA computes a 128 x 32 tile of C = alpha op(A) op(B) + beta C from the
+// Each tile of C = alpha op(A) op(B) + beta C is 128 x 32; one persistent CTA
+// per SM walks the tiles.  The operands are the
 // bf16 slice planes As[p][row][k] (p < SA) and Bs[q][col][k] (q < SB), both
 // K-contiguous.  Warp roles (320 threads):
 //   warp 0      TMA producer: per 64-deep k block, one 3-D load of all SB
@@ -13,9 +14,10 @@
 //               tcgen05.mma.kind::f16 with M = 128, N = 256, K = 16 whose
 //               accumulator starts at TMEM column 32 p multiplies A plane p by
 //               all eight at once and lands block q in columns 32 (p + q):
-//               the accumulator of group t = p + q.  Plane q = 8 adds one
-//               N = 32 MMA where p + 8 <= TMAX.  Groups above TMAX (columns
-//               up to 511) are computed and never read;
+//               the accumulator of group t = p + q.  The MMA for plane p
+//               takes only the planes with p + q <= TMAX (N = 32 per plane,
+//               at most eight); plane q = 8 adds one N = 32 MMA where
+//               p + 8 <= TMAX.  Exactly the 53 products are formed;
 //   warps 2-9   epilogue (two warps per 32-lane TMEM quarter, 16 columns
 //               each): zeroes the group accumulators before every K chunk
 //               (all MMAs accumulate) and after each chunk (Kc deep, every group sum an
@@ -100,10 +102,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t idesc_f16(int n) {
+__host__ __device__ constexpr uint32_t idesc_f16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
-constexpr uint32_t kIdesc256 = idesc_f16(8 * TC_N), kIdesc32 = idesc_f16(TC_N);
+constexpr uint32_t kIdesc32 = idesc_f16(TC_N);
 
 // D (TMEM) += A (smem) B (smem)
 __device__ __forceinline__ void mma_f16_acc(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc) {
@@ -141,6 +143,7 @@ struct TcArgs {
     i64 M, N;
     int KB;            // 64-deep k blocks
     int kbpc;          // k blocks per exact chunk
+    int mt, ntiles;    // row tiles, all tiles (tile = row tile + mt * column tile)
     const int* ea;
     const int* eb;
     double alpha, beta;
@@ -149,6 +152,17 @@ struct TcArgs {
     int* err;
 };
 
+// Planes of B multiplied by A plane pa in one MMA: q = 0 .. nq-1 with
+// pa + q <= TMAX, at most eight (the ninth plane gets its own MMA).
+template <int TMAX>
+__device__ __forceinline__ int stacked_planes(int pa) {
+    const int nq = TMAX - pa + 1;
+    return nq < 8 ? nq : 8;
+}
+
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...  The accumulators of a
+// tile are released as soon as the epilogue has read its last chunk, so the
+// final FP64 conversion and the stores of C overlap the next tile's MMAs.
 template <int SA, int SB, int TMAX>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
@@ -167,7 +181,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t bacc_full = beb + 8 * TC_NB, bacc_empty = bacc_full + 8, bdrain = bacc_empty + 8;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
     const int nchunks = (p.KB + p.kbpc - 1) / p.kbpc;
 
     if (threadIdx.x == 0) {
@@ -202,26 +215,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // stages loaded at least once (bit s) and the parity of their last load
             uint32_t used_a = 0, par_a = 0, used_b = 0, par_b = 0;
             bool ok = true;
-            for (int kb = 0; kb < p.KB && ok; ++kb) {
-                if (!(ok = mbar_wait(beb + 8 * sb, phb ^ 1, p.err))) break;
-                mbar_expect_tx(bfb + 8 * sb, BBYTES);
-                tma_load_3d(su32(sB + sb * BBYTES), &tmB, kb * TC_KB, n0, 0, bfb + 8 * sb);
-                used_b |= 1u << sb;
-                par_b = (par_b & ~(1u << sb)) | (phb << sb);
-                for (int pa = 0; pa < SA; ++pa) {
-                    if (!(ok = mbar_wait(bea + 8 * sa, pha ^ 1, p.err))) break;
-                    mbar_expect_tx(bfa + 8 * sa, TC_ABYTES);
-                    tma_load_3d(su32(sA + sa * TC_ABYTES), &tmA, kb * TC_KB, m0, pa, bfa + 8 * sa);
-                    used_a |= 1u << sa;
-                    par_a = (par_a & ~(1u << sa)) | (pha << sa);
-                    if (++sa == TC_NA) {
-                        sa = 0;
-                        pha ^= 1;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile % p.mt) * TC_M, n0 = (tile / p.mt) * TC_N;
+                for (int kb = 0; kb < p.KB && ok; ++kb) {
+                    if (!(ok = mbar_wait(beb + 8 * sb, phb ^ 1, p.err))) break;
+                    mbar_expect_tx(bfb + 8 * sb, BBYTES);
+                    tma_load_3d(su32(sB + sb * BBYTES), &tmB, kb * TC_KB, n0, 0, bfb + 8 * sb);
+                    used_b |= 1u << sb;
+                    par_b = (par_b & ~(1u << sb)) | (phb << sb);
+                    for (int pa = 0; pa < SA; ++pa) {
+                        if (!(ok = mbar_wait(bea + 8 * sa, pha ^ 1, p.err))) break;
+                        mbar_expect_tx(bfa + 8 * sa, TC_ABYTES);
+                        tma_load_3d(su32(sA + sa * TC_ABYTES), &tmA, kb * TC_KB, m0, pa, bfa + 8 * sa);
+                        used_a |= 1u << sa;
+                        par_a = (par_a & ~(1u << sa)) | (pha << sa);
+                        if (++sa == TC_NA) {
+                            sa = 0;
+                            pha ^= 1;
+                        }
                     }
-                }
-                if (++sb == TC_NB) {
-                    sb = 0;
-                    phb ^= 1;
+                    if (++sb == TC_NB) {
+                        sb = 0;
+                        phb ^= 1;
+                    }
                 }
             }
             // every issued copy has landed before the CTA may exit (the phase a
@@ -236,45 +252,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             int sa = 0, sb = 0;
             uint32_t pha = 0, phb = 0;
+            unsigned g = 0;                              // chunks issued so far (all tiles)
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                // the epilogue has zeroed the accumulators (before chunk 0, and
-                // after reading each chunk)
-                if (!(ok = mbar_wait(bacc_empty, (uint32_t)(c & 1), p.err))) break;
-                tc_fence_after();
-                const int kb0 = c * p.kbpc, kb1 = min(p.KB, kb0 + p.kbpc);
-                for (int kb = kb0; kb < kb1 && ok; ++kb) {
-                    if (!(ok = mbar_wait(bfb + 8 * sb, phb, p.err))) break;
+            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++g) {
+                    // the epilogue has zeroed the accumulators (initially, and
+                    // right after reading every chunk)
+                    if (!(ok = mbar_wait(bacc_empty, g & 1u, p.err))) break;
                     tc_fence_after();
-                    const uint32_t bbase = su32(sB + sb * BBYTES);
-                    for (int pa = 0; pa < SA; ++pa) {
-                        if (!(ok = mbar_wait(bfa + 8 * sa, pha, p.err))) break;
+                    const int kb0 = c * p.kbpc, kb1 = min(p.KB, kb0 + p.kbpc);
+                    for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                        if (!(ok = mbar_wait(bfb + 8 * sb, phb, p.err))) break;
                         tc_fence_after();
-                        const uint64_t ad = sdesc(su32(sA + sa * TC_ABYTES));
-                        const uint64_t b8 = sdesc(bbase);                      // planes 0..7 as N = 256
-                        const uint64_t b1 = sdesc(bbase + 8 * TC_BPLANE);      // plane 8
+                        const uint32_t bbase = su32(sB + sb * BBYTES);
+                        const uint64_t b8 = sdesc(bbase);                    // planes 0..7 stacked along N
+                        const uint64_t b1 = sdesc(bbase + 8 * TC_BPLANE);    // plane 8
+                        for (int pa = 0; pa < SA; ++pa) {
+                            if (!(ok = mbar_wait(bfa + 8 * sa, pha, p.err))) break;
+                            tc_fence_after();
+                            const uint64_t ad = sdesc(su32(sA + sa * TC_ABYTES));
+                            const int nq = stacked_planes<TMAX>(pa);
+                            const uint32_t idn = idesc_f16(nq * TC_N);
 #pragma unroll
-                        for (int ks = 0; ks < TC_KB / 16; ++ks) {
-                            // +32 bytes per 16-deep k step inside the swizzled 128-byte rows
-                            mma_f16_acc(tmem + (uint32_t)(pa * TC_N), ad + (uint64_t)(ks * 2), b8 + (uint64_t)(ks * 2),
-                                        kIdesc256);
-                            if (pa + 8 <= TMAX)
-                                mma_f16_acc(tmem + (uint32_t)((pa + 8) * TC_N), ad + (uint64_t)(ks * 2),
-                                            b1 + (uint64_t)(ks * 2), kIdesc32);
+                            for (int ks = 0; ks < TC_KB / 16; ++ks) {
+                                // +32 bytes per 16-deep k step inside the swizzled 128-byte rows
+                                mma_f16_acc(tmem + (uint32_t)(pa * TC_N), ad + (uint64_t)(ks * 2),
+                                            b8 + (uint64_t)(ks * 2), idn);
+                                if (pa + 8 <= TMAX)
+                                    mma_f16_acc(tmem + (uint32_t)((pa + 8) * TC_N), ad + (uint64_t)(ks * 2),
+                                                b1 + (uint64_t)(ks * 2), kIdesc32);
+                            }
+                            mma_commit(bea + 8 * sa);
+                            if (++sa == TC_NA) {
+                                sa = 0;
+                                pha ^= 1;
+                            }
                         }
-                        mma_commit(bea + 8 * sa);
-                        if (++sa == TC_NA) {
-                            sa = 0;
-                            pha ^= 1;
+                        mma_commit(beb + 8 * sb);
+                        if (++sb == TC_NB) {
+                            sb = 0;
+                            phb ^= 1;
                         }
                     }
-                    mma_commit(beb + 8 * sb);
-                    if (++sb == TC_NB) {
-                        sb = 0;
-                        phb ^= 1;
-                    }
+                    if (ok) mma_commit(bacc_full);
                 }
-                if (ok) mma_commit(bacc_full);
             }
             // wait for every issued MMA before TMEM is released
             mma_commit(bdrain);
@@ -286,57 +307,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         constexpr int HN = TC_N / 2;
         const int wq = warp & 3, h = (warp - 2) >> 2;
         const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(HN * h);
-        long long HI[HN], LO[HN];
-#pragma unroll
-        for (int j = 0; j < HN; ++j) {
-            HI[j] = 0;
-            LO[j] = 0;
-        }
-        // zero this warp's share of the group accumulators for chunk 0
+        // zero this warp's share of the group accumulators for the first chunk
 #pragma unroll
         for (int t = 0; t < NG; ++t) tmem_zero16(tl + (uint32_t)(t * TC_N));
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bacc_empty);
+        unsigned g = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            // lane 0 waits; the outcome is shared so that the warp-collective
-            // tcgen05.ld below always runs with the whole warp
-            int got = 0;
-            if (lane == 0) got = mbar_wait(bacc_full, (uint32_t)(c & 1), p.err) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, got, 0) != 0;
-            if (!ok) break;
-            tc_fence_after();
-#pragma unroll
-            for (int t = 0; t < NG; ++t) {
-                uint32_t v[HN];
-                tmem_ld16(tl + (uint32_t)(t * TC_N), v);
-#pragma unroll
-                for (int j = 0; j < HN; ++j) {
-                    const long long x = (long long)__float2int_rz(__uint_as_float(v[j]));
-                    if (t <= 4) HI[j] += x * (1ll << (6 * (4 - t)));
-                    else LO[j] += x * (1ll << (6 * (TMAX - t)));
-                }
-                if (c + 1 < nchunks) tmem_zero16(tl + (uint32_t)(t * TC_N));
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bacc_empty);
-        }
-        const i64 row = m0 + 32 * wq + lane;
-        if (ok && row < p.M) {
-            const int er = p.ea[row];
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            const int m0 = (tile % p.mt) * TC_M, n0 = (tile / p.mt) * TC_N;
+            long long HI[HN], LO[HN];
 #pragma unroll
             for (int j = 0; j < HN; ++j) {
-                const i64 col = n0 + HN * h + j;
-                if (col < p.N) {
-                    double v = ldexp((double)HI[j], -24);
-                    if (TMAX >= 5) v += ldexp((double)LO[j], -6 * TMAX);
-                    const double out = p.alpha * ldexp(v, er + p.eb[col] - 12);
-                    double* cp = p.C + row + col * p.ldc;
-                    *cp = (p.beta == 0.0) ? out : fma(p.beta, *cp, out);
+                HI[j] = 0;
+                LO[j] = 0;
+            }
+            for (int c = 0; c < nchunks && ok; ++c, ++g) {
+                // lane 0 waits; the outcome is shared so that the warp-collective
+                // tcgen05.ld below always runs with the whole warp
+                int got = 0;
+                if (lane == 0) got = mbar_wait(bacc_full, g & 1u, p.err) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+                if (!ok) break;
+                tc_fence_after();
+#pragma unroll
+                for (int t = 0; t < NG; ++t) {
+                    uint32_t v[HN];
+                    tmem_ld16(tl + (uint32_t)(t * TC_N), v);
+#pragma unroll
+                    for (int j = 0; j < HN; ++j) {
+                        const long long x = (long long)__float2int_rz(__uint_as_float(v[j]));
+                        if (t <= 4) HI[j] += x * (1ll << (6 * (4 - t)));
+                        else LO[j] += x * (1ll << (6 * (TMAX - t)));
+                    }
+                    tmem_zero16(tl + (uint32_t)(t * TC_N));
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bacc_empty);
+            }
+            // the accumulators are free again: convert and store while the next
+            // tile's MMAs run
+            const i64 row = m0 + 32 * wq + lane;
+            if (ok && row < p.M) {
+                const int er = p.ea[row];
+#pragma unroll
+                for (int j = 0; j < HN; ++j) {
+                    const i64 col = n0 + HN * h + j;
+                    if (col < p.N) {
+                        double v = ldexp((double)HI[j], -24);
+                        if (TMAX >= 5) v += ldexp((double)LO[j], -6 * TMAX);
+                        const double out = p.alpha * ldexp(v, er + p.eb[col] - 12);
+                        double* cp = p.C + row + col * p.ldc;
+                        *cp = (p.beta == 0.0) ? out : fma(p.beta, *cp, out);
+                    }
                 }
             }
         }
@@ -408,8 +435,11 @@ int launch_tc(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16
     a.C = C;
     a.ldc = ldc;
     a.err = err;
-    if (cdiv(N, TC_N) > 65535) { set_error("ozaki_tc: N too large"); return BQRRP_EUNSUPPORTED; }
-    dim3 grid((unsigned)cdiv(M, TC_M), (unsigned)cdiv(N, TC_N));
+    const i64 mt = cdiv(M, TC_M), tiles = mt * cdiv(N, TC_N);
+    if (tiles > (i64)1 << 30) { set_error("ozaki_tc: too many tiles"); return BQRRP_EUNSUPPORTED; }
+    a.mt = (int)mt;
+    a.ntiles = (int)tiles;
+    const unsigned grid = (unsigned)imin(tiles, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
     ozaki_tc_kernel<SA, SB, TMAX><<<grid, TC_THREADS, smem, c.stream>>>(tmA, tmB, a);
     BQ_LAUNCH_CHECK();
     return 0;
