@@ -874,15 +874,22 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
 // ------------------------------------------------------------------ trailing update
 // Item = (matrix, 64-column tile of A(:, c:)).  W = Y^T C (k x 64), then
 // C(0:keep, :) -= V(0:keep, :) W with V = Y T^T from the panel; keep = rows
-// when k = w, else k.  Shared memory: Yc (RT x kb, [row][col]) holds Y, then V
-// chunks; Cc (RT x CT); Ws (kb x CT, [i][j]).
+// when k = w, else k.  Shared memory: Yc (RT2 x kb, [row][col]) holds Y chunks
+// of RT rows, then V chunks of RT2 rows; Cc (RT x CT); Ws (kb x CT, [i][j]).
+// Register blocking, 4 x 4 outputs per thread and block:
+//  - W: the ceil(k/4) x 16 blocks are spread over the threads; when there are
+//    fewer blocks than threads, G = 256 / blocks groups split the rows of each
+//    chunk (group g takes rows g, g + G, ...) and their partial sums are added
+//    in group order (deterministic); with more blocks, a thread takes two;
+//  - update: thread (rb, jb) = (tid / 16, tid % 16) owns rows 4 rb .. 4 rb + 3
+//    of an RT2-row chunk and columns 4 jb .. 4 jb + 3.
+constexpr int RT2 = 64;
+
 __global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, int slot_id, int iter, int kb) {
     extern __shared__ double sm[];
     double* Yc = sm;
-    double* Cc = Yc + (size_t)RT * kb;
+    double* Cc = Yc + (size_t)RT2 * kb;
     double* Ws = Cc + (size_t)RT * CT;
-    const int jj = threadIdx.x % CT;
-    const int ig = threadIdx.x / CT;               // 0..3
     for (;;) {
         const Item it = next_item(a, sl, slot_id);
         if (it.mat < 0) break;
@@ -901,10 +908,25 @@ __global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, in
         const double* V = a.wsd + M.offV;
         double* C = a.A + M.offA + s + j0 * m;
 
-        // W = Y^T C
-        double acc[kMaxB / 4];
+        // ---- W = Y^T C
+        const int nblk = ((k + 3) / 4) * 16;
+        const int G = (nblk >= BT) ? 1 : BT / nblk;
+        const int g = (G == 1) ? 0 : (int)threadIdx.x / nblk;
+        int bi[2], bj[2];
 #pragma unroll
-        for (int q = 0; q < kMaxB / 4; ++q) acc[q] = 0.0;
+        for (int q = 0; q < 2; ++q) {
+            const int blk = (G == 1) ? (int)threadIdx.x + q * BT : (int)threadIdx.x % nblk;
+            const bool on = (q == 0 || G == 1) && g < G && blk < nblk && (G == 1 || q == 0);
+            bi[q] = on ? 4 * (blk / 16) : -1;
+            bj[q] = on ? 4 * (blk % 16) : -1;
+        }
+        double acc[2][4][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[q][u][v] = 0.0;
         for (i64 r0 = 0; r0 < rows; r0 += RT) {
             const int nr = (int)min((i64)RT, rows - r0);
             __syncthreads();
@@ -917,39 +939,76 @@ __global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, in
                 Cc[rr * CT + j] = (rr < nr && j < nc) ? C[(r0 + rr) + (i64)j * m] : 0.0;
             }
             __syncthreads();
-            for (int rr = 0; rr < nr; ++rr) {
-                const double cv = Cc[rr * CT + jj];
 #pragma unroll
-                for (int q = 0; q < kMaxB / 4; ++q)
-                    if (ig + 4 * q < k) acc[q] = fma(Yc[rr * kb + ig + 4 * q], cv, acc[q]);
+            for (int q = 0; q < 2; ++q) {
+                if (bi[q] < 0) continue;
+                for (int rr = g; rr < nr; rr += G) {
+                    double y[4], cv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) y[u] = Yc[rr * kb + bi[q] + u];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) cv[v] = Cc[rr * CT + bj[q] + v];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[q][u][v] = fma(y[u], cv[v], acc[q][u][v]);
+                }
             }
         }
+        // add the groups' partial sums into Ws in group order
+        for (int g2 = 0; g2 < G; ++g2) {
+            if (g == g2) {
 #pragma unroll
-        for (int q = 0; q < kMaxB / 4; ++q)
-            if (ig + 4 * q < k) Ws[(ig + 4 * q) * CT + jj] = acc[q];
-        // C(0:keep, :) -= V(0:keep, :) W
-        for (i64 r0 = 0; r0 < keep; r0 += RT) {
-            const int nr = (int)min((i64)RT, keep - r0);
+                for (int q = 0; q < 2; ++q) {
+                    if (bi[q] < 0) continue;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const int i = bi[q] + u;
+                            if (i < k) {
+                                double* wp = Ws + i * CT + bj[q] + v;
+                                *wp = (g2 == 0) ? acc[q][u][v] : *wp + acc[q][u][v];
+                            }
+                        }
+                }
+            }
             __syncthreads();
-            for (int e = threadIdx.x; e < RT * kb; e += BT) {
-                const int rr = e % RT, i = e / RT;
+        }
+        // ---- C(0:keep, :) -= V(0:keep, :) W
+        const int rb = threadIdx.x / 16, jb = threadIdx.x % 16;
+        for (i64 r0 = 0; r0 < keep; r0 += RT2) {
+            const int nr = (int)min((i64)RT2, keep - r0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < RT2 * kb; e += BT) {
+                const int rr = e % RT2, i = e / RT2;
                 Yc[rr * kb + i] = (rr < nr && i < k) ? V[(r0 + rr) + (i64)i * m] : 0.0;
             }
             __syncthreads();
-            double u[RT / 4];
+            double u4[4][4];
 #pragma unroll
-            for (int p = 0; p < RT / 4; ++p) u[p] = 0.0;
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) u4[u][v] = 0.0;
             for (int i = 0; i < k; ++i) {
-                const double wv = Ws[i * CT + jj];
+                double vv[4], wv[4];
 #pragma unroll
-                for (int p = 0; p < RT / 4; ++p) u[p] = fma(Yc[(ig + 4 * p) * kb + i], wv, u[p]);
+                for (int u = 0; u < 4; ++u) vv[u] = Yc[(4 * rb + u) * kb + i];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) wv[v] = Ws[i * CT + 4 * jb + v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) u4[u][v] = fma(vv[u], wv[v], u4[u][v]);
             }
-            if (jj < nc)
 #pragma unroll
-                for (int p = 0; p < RT / 4; ++p) {
-                    const int rr = ig + 4 * p;
-                    if (rr < nr) C[(r0 + rr) + (i64)jj * m] -= u[p];
-                }
+            for (int v = 0; v < 4; ++v) {
+                const int col = 4 * jb + v;
+                if (col < nc)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (4 * rb + u < nr) C[(r0 + 4 * rb + u) + (i64)col * m] -= u4[u][v];
+            }
         }
     }
 }
@@ -1251,7 +1310,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     const int kb = P->kb;
     P->dsm_perm = sizeof(double) * (size_t)maxmoved * RCH;
     P->dsm_panel = sizeof(double) * ((size_t)kb * kb + (size_t)RG * kb);
-    P->dsm_trail = sizeof(double) * ((size_t)RT * kb + (size_t)RT * CT + (size_t)kb * CT);
+    P->dsm_trail = sizeof(double) * ((size_t)RT2 * kb + (size_t)RT * CT + (size_t)kb * CT);
     struct KInfo { const void* fn; size_t dsm; };
     const KInfo ki[8] = {
         {(const void*)bat_init_kernel, 0},        {(const void*)bat_sketch_kernel, 0},
