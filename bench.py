@@ -102,7 +102,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--m", type=int, default=None)
-    p.add_argument("--b", type=int, default=512)
+    p.add_argument("--b", type=int, default=256,
+                   help="block size (the configuration sweeps 256, 512, 1024, 2048; 256 is the fastest at 16384^2)")
     p.add_argument("--d", type=int, default=None)
     p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
     p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")

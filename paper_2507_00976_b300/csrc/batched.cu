@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -180,13 +181,11 @@ __device__ void row_trsm_upper(const double* src, i64 lds, double* dst, i64 ldd,
 }
 
 // ------------------------------------------------------------------ init
-__global__ void __launch_bounds__(BT) bat_init_kernel(BatArgs a, Slot sl, int slot_id) {
+__device__ void body_init(const BatArgs& a, const int mat, const int sub) {
     __shared__ double red[BT];
     __shared__ int s_bad;
-    for (;;) {
-        const Item it = next_item(a, sl, slot_id);
-        if (it.mat < 0) break;
-        const BatMat M = a.mats[it.mat];
+        {
+        const BatMat M = a.mats[mat];
         const double* A = a.A + M.offA;
         const i64 tot = M.m * M.n;
         double acc = 0.0;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(BT) bat_init_kernel(BatArgs a, Slot sl, int sl
             tau[j] = 0.0;
         }
         if (threadIdx.x == 0) {
-            BatState& S = a.st[it.mat];
+            BatState& S = a.st[mat];
             S.anorm = sqrt(red[0]);
             S.r00 = 0.0;
             S.k = 0;
@@ -222,6 +221,14 @@ __global__ void __launch_bounds__(BT) bat_init_kernel(BatArgs a, Slot sl, int sl
             S.info = s_bad ? BQRRP_ENUMERIC : 0;
             S.done = (s_bad || M.n == 0) ? 1 : 0;
         }
+    }
+}
+
+__global__ void __launch_bounds__(BT) bat_init_kernel(BatArgs a, Slot sl, int slot_id) {
+    for (;;) {
+        const Item it = next_item(a, sl, slot_id);
+        if (it.mat < 0) break;
+        body_init(a, it.mat, it.sub);
     }
 }
 
@@ -276,15 +283,13 @@ __device__ void sketch_pass(const double* A, i64 m, i64 j0, int nc, i64 d, int p
     }
 }
 
-__global__ void __launch_bounds__(BT) bat_sketch_kernel(BatArgs a, Slot sl, int slot_id) {
+__device__ void body_sketch(const BatArgs& a, const int mat, const int sub) {
     __shared__ double As[SK_RK][CT];
     __shared__ uint32_t Sw[SK_RK][4];
-    for (;;) {
-        const Item it = next_item(a, sl, slot_id);
-        if (it.mat < 0) break;
-        if (a.st[it.mat].done) continue;
-        const BatMat M = a.mats[it.mat];
-        const i64 j0 = (i64)it.sub * CT;
+        {
+        if (a.st[mat].done) return;
+        const BatMat M = a.mats[mat];
+        const i64 j0 = (i64)sub * CT;
         const int nc = (int)min((i64)CT, M.n - j0);
         const double* A = a.A + M.offA;
         double* Sk = a.wsd + M.offSk;
@@ -297,6 +302,14 @@ __global__ void __launch_bounds__(BT) bat_sketch_kernel(BatArgs a, Slot sl, int 
             else if (nrows <= 96) sketch_pass<24>(A, M.m, j0, nc, M.d, p, k0s, k1s, As, Sw, Sk);
             else sketch_pass<32>(A, M.m, j0, nc, M.d, p, k0s, k1s, As, Sw, Sk);
         }
+    }
+}
+
+__global__ void __launch_bounds__(BT) bat_sketch_kernel(BatArgs a, Slot sl, int slot_id) {
+    for (;;) {
+        const Item it = next_item(a, sl, slot_id);
+        if (it.mat < 0) break;
+        body_sketch(a, it.mat, it.sub);
     }
 }
 
@@ -383,22 +396,22 @@ __device__ void cta_house_qr(double* W, i64 d, i64 nc, double* vbuf, double* s_t
     }
 }
 
-__global__ void __launch_bounds__(BT) bat_qrcp_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
+__device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int iter) {
     __shared__ double pc[kMaxD];
-    __shared__ double Lw[NW][kMaxD];
     __shared__ double wv[NW];
     __shared__ int wi[NW];
     __shared__ int ipiv[kMaxD];
-    __shared__ int Js[kMaxN];
+    // dynamic shared memory: one L row per warp, then the pivot vector
+    extern __shared__ double qdsm[];
+    double (*Lw)[kMaxD] = reinterpret_cast<double (*)[kMaxD]>(qdsm);
+    int* Js = reinterpret_cast<int*>(qdsm + NW * kMaxD);
     __shared__ int s_flag, s_cnt, s_next;
     __shared__ double s_tau;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (;;) {
-        const Item it = next_item(a, sl, slot_id);
-        if (it.mat < 0) break;
-        BatState* S = a.st + it.mat;
-        if (S->done) continue;
-        const BatMat M = a.mats[it.mat];
+        {
+        BatState* S = a.st + mat;
+        if (S->done) return;
+        const BatMat M = a.mats[mat];
         const i64 d = M.d, n = M.n, b = M.b;
         const i64 s = (i64)iter * b;
         const i64 c = min(n, s + b), w = c - s, N = n - s;
@@ -558,22 +571,28 @@ __global__ void __launch_bounds__(BT) bat_qrcp_kernel(BatArgs a, Slot sl, int sl
     }
 }
 
-// ------------------------------------------------------------------ permutation (Alg. 5 on moved columns)
-// Item = (matrix, 32-row chunk).  The moved columns are staged in shared
-// memory, then written to their new places; chunk 0 also permutes J.
-__global__ void __launch_bounds__(BT) bat_perm_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
-    extern __shared__ double stg[];      // [moved][RCH]
-    __shared__ int64_t jst[2 * kMaxD];
+__global__ void __launch_bounds__(BT) bat_qrcp_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
     for (;;) {
         const Item it = next_item(a, sl, slot_id);
         if (it.mat < 0) break;
-        const BatState* S = a.st + it.mat;
-        if (S->done) continue;
+        body_qrcp(a, it.mat, it.sub, iter);
+    }
+}
+
+// ------------------------------------------------------------------ permutation (Alg. 5 on moved columns)
+// Item = (matrix, 32-row chunk).  The moved columns are staged in shared
+// memory, then written to their new places; chunk 0 also permutes J.
+__device__ void body_perm(const BatArgs& a, const int mat, const int sub, int iter) {
+    extern __shared__ double stg[];      // [moved][RCH]
+    __shared__ int64_t jst[2 * kMaxD];
+        {
+        const BatState* S = a.st + mat;
+        if (S->done) return;
         const int nm = (int)S->nmoved;
-        if (nm == 0) continue;
-        const BatMat M = a.mats[it.mat];
+        if (nm == 0) return;
+        const BatMat M = a.mats[mat];
         const i64 m = M.m, s = (i64)iter * M.b;
-        const i64 r0 = (i64)it.sub * RCH;
+        const i64 r0 = (i64)sub * RCH;
         const int nr = (int)min((i64)RCH, m - r0);
         const int* Jg = a.wsi + M.offI;
         const int* mv = Jg + M.n;
@@ -587,7 +606,7 @@ __global__ void __launch_bounds__(BT) bat_perm_kernel(BatArgs a, Slot sl, int sl
             const int q = e / RCH, rr = e % RCH;
             if (rr < nr) A[(r0 + rr) + (s + mv[q]) * m] = stg[e];
         }
-        if (it.sub == 0) {
+        if (sub == 0) {
             int64_t* J = a.jpvt + M.offJ;
             for (int q = threadIdx.x; q < nm; q += BT) jst[q] = J[s + Jg[mv[q]]];
             __syncthreads();
@@ -596,20 +615,26 @@ __global__ void __launch_bounds__(BT) bat_perm_kernel(BatArgs a, Slot sl, int sl
     }
 }
 
+__global__ void __launch_bounds__(BT) bat_perm_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
+    for (;;) {
+        const Item it = next_item(a, sl, slot_id);
+        if (it.mat < 0) break;
+        body_perm(a, it.mat, it.sub, iter);
+    }
+}
+
 // ------------------------------------------------------------------ Alg. 3 panel, one matrix per CTA
 // Shared memory: Gs (kb x kb, ld kb) and a Gram chunk (RG x kb, [row][col]).
-__global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, int slot_id, int iter, int kb) {
+__device__ void body_panel(const BatArgs& a, const int mat, const int sub, int iter, int kb) {
     extern __shared__ double sm[];
     double* Gs = sm;
     double* Yc = sm + (size_t)kb * kb;
     __shared__ double Dsg[kMaxB];
     __shared__ int s_flag, s_kc;
-    for (;;) {
-        const Item it = next_item(a, sl, slot_id);
-        if (it.mat < 0) break;
-        BatState* S = a.st + it.mat;
-        if (S->done) continue;
-        const BatMat M = a.mats[it.mat];
+        {
+        BatState* S = a.st + mat;
+        if (S->done) return;
+        const BatMat M = a.mats[mat];
         const i64 m = M.m, n = M.n, b = M.b, d = M.d;
         const i64 s = (i64)iter * b;
         const i64 c = min(n, s + b), w = c - s, rows = m - s;
@@ -633,7 +658,7 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
                 S->ell = s;
                 S->done = 1;
             }
-            continue;
+            return;
         }
 
         // ---- Pre = A_p(:, 0:k) Rsk11^{-1}  (Rsk11 staged in Gs)
@@ -752,7 +777,7 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
                     S->ell = s;
                     S->done = 1;
                 }
-                continue;
+                return;
             }
         }
 
@@ -871,6 +896,14 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
     }
 }
 
+__global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, int slot_id, int iter, int kb) {
+    for (;;) {
+        const Item it = next_item(a, sl, slot_id);
+        if (it.mat < 0) break;
+        body_panel(a, it.mat, it.sub, iter, kb);
+    }
+}
+
 // ------------------------------------------------------------------ trailing update
 // Item = (matrix, 64-column tile of A(:, c:)).  W = Y^T C (k x 64), then
 // C(0:keep, :) -= V(0:keep, :) W with V = Y T^T from the panel; keep = rows
@@ -885,25 +918,23 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
 //    of an RT2-row chunk and columns 4 jb .. 4 jb + 3.
 constexpr int RT2 = 64;
 
-__global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, int slot_id, int iter, int kb) {
+__device__ void body_trailing(const BatArgs& a, const int mat, const int sub, int iter, int kb) {
     extern __shared__ double sm[];
     double* Yc = sm;
     double* Cc = Yc + (size_t)RT2 * kb;
     double* Ws = Cc + (size_t)RT * CT;
-    for (;;) {
-        const Item it = next_item(a, sl, slot_id);
-        if (it.mat < 0) break;
-        const BatState* S = a.st + it.mat;
-        if (S->upd_iter != iter) continue;
-        const BatMat M = a.mats[it.mat];
+        {
+        const BatState* S = a.st + mat;
+        if (S->upd_iter != iter) return;
+        const BatMat M = a.mats[mat];
         const i64 m = M.m, n = M.n, b = M.b;
         const i64 s = (i64)iter * b;
         const i64 c = min(n, s + b), w = c - s, rows = m - s;
         const int k = (int)S->k;
         const i64 keep = (k == w) ? rows : k;
-        const i64 j0 = c + (i64)it.sub * CT;
+        const i64 j0 = c + (i64)sub * CT;
         const int nc = (int)min((i64)CT, n - j0);
-        if (nc <= 0) continue;
+        if (nc <= 0) return;
         const double* Y = a.wsd + M.offY;
         const double* V = a.wsd + M.offV;
         double* C = a.A + M.offA + s + j0 * m;
@@ -1013,21 +1044,27 @@ __global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, in
     }
 }
 
-// ------------------------------------------------------------------ sketch update (Duersch-Gu)
-// Item = (matrix, 64-column tile of Msk(:, c:)).
-__global__ void __launch_bounds__(BT) bat_skupdate_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
+__global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, int slot_id, int iter, int kb) {
     for (;;) {
         const Item it = next_item(a, sl, slot_id);
         if (it.mat < 0) break;
-        const BatState* S = a.st + it.mat;
-        if (S->cont_iter != iter) continue;
-        const BatMat M = a.mats[it.mat];
+        body_trailing(a, it.mat, it.sub, iter, kb);
+    }
+}
+
+// ------------------------------------------------------------------ sketch update (Duersch-Gu)
+// Item = (matrix, 64-column tile of Msk(:, c:)).
+__device__ void body_skupdate(const BatArgs& a, const int mat, const int sub, int iter) {
+        {
+        const BatState* S = a.st + mat;
+        if (S->cont_iter != iter) return;
+        const BatMat M = a.mats[mat];
         const i64 m = M.m, n = M.n, b = M.b, d = M.d;
         const i64 s = (i64)iter * b;
         const i64 c = min(n, s + b), w = c - s;
-        const i64 j0 = c + (i64)it.sub * CT;
+        const i64 j0 = c + (i64)sub * CT;
         const int nc = (int)min((i64)CT, n - j0);
-        if (nc <= 0) continue;
+        if (nc <= 0) return;
         const double* Wk = a.wsd + M.offW;
         const double* Zb = a.wsd + M.offSm + 2 * b * b;
         const double* A = a.A + M.offA;
@@ -1045,13 +1082,19 @@ __global__ void __launch_bounds__(BT) bat_skupdate_kernel(BatArgs a, Slot sl, in
     }
 }
 
-// ------------------------------------------------------------------ finish
-__global__ void __launch_bounds__(BT) bat_finish_kernel(BatArgs a, Slot sl, int slot_id) {
+__global__ void __launch_bounds__(BT) bat_skupdate_kernel(BatArgs a, Slot sl, int slot_id, int iter) {
     for (;;) {
         const Item it = next_item(a, sl, slot_id);
         if (it.mat < 0) break;
-        const BatMat M = a.mats[it.mat];
-        const BatState* S = a.st + it.mat;
+        body_skupdate(a, it.mat, it.sub, iter);
+    }
+}
+
+// ------------------------------------------------------------------ finish
+__device__ void body_finish(const BatArgs& a, const int mat, const int sub) {
+        {
+        const BatMat M = a.mats[mat];
+        const BatState* S = a.st + mat;
         const i64 m = M.m, n = M.n;
         int64_t* J = a.jpvt + M.offJ;
         for (i64 j = threadIdx.x; j < n; j += BT) J[j] += 1;
@@ -1075,11 +1118,200 @@ __global__ void __launch_bounds__(BT) bat_finish_kernel(BatArgs a, Slot sl, int 
                 if (tail <= thr2) best = i;
                 else break;
             }
-            a.rank_out[it.mat] = ell;
-            if (a.trunc_out) a.trunc_out[it.mat] = best;
-            if (a.info_out) a.info_out[it.mat] = S->info;
+            a.rank_out[mat] = ell;
+            if (a.trunc_out) a.trunc_out[mat] = best;
+            if (a.info_out) a.info_out[mat] = S->info;
         }
     }
+}
+
+__global__ void __launch_bounds__(BT) bat_finish_kernel(BatArgs a, Slot sl, int slot_id) {
+    for (;;) {
+        const Item it = next_item(a, sl, slot_id);
+        if (it.mat < 0) break;
+        body_finish(a, it.mat, it.sub);
+    }
+}
+
+// ------------------------------------------------------------------ dependency-driven form
+// One persistent kernel runs every phase of every matrix.  Its CTAs take
+// tasks from a device queue; a matrix moves to its next phase as soon as the
+// last task of its current phase finishes, independently of the others, so no
+// SM waits for the slowest matrix of a lock-step iteration.  Per matrix:
+//   INIT -> SKETCH (one task per 64-column tile) -> per block iteration
+//   QRCP (Alg. 2 plus the column permutation) -> PANEL (Alg. 3) ->
+//   TRAIL (one task per 64-column tile, plus that tile's sketch update)
+//   -> QRCP of the next block, or FINISH.
+// The last finisher of a phase (an atomic count per matrix) pushes the next
+// phase's tasks.  The queue is a slot array written once per run: a slot holds
+// task + 1 once published (release store), 0 before.  A worker takes the next
+// slot index and polls it (acquire) until it is published or every matrix is
+// done; polls are bounded, and a worker that gives up records a timeout.
+enum : int { T_INIT = 0, T_SKETCH = 1, T_QRCP = 2, T_PANEL = 3, T_TRAIL = 4, T_FINISH = 5 };
+
+struct MegaArgs {
+    unsigned long long* slots;   // cap entries
+    unsigned int* ctl;           // [0] head, [1] tail, [2] matrices done, [3] error
+    int* pending;                // per matrix: unfinished tasks of its current phase
+    int* finished;               // per matrix: 1 once FINISH has run
+    const int* order;            // initial INIT order (largest first)
+    unsigned int cap;
+    int batch;
+    int kb;
+    int nperm;                   // unused placeholder for alignment
+};
+
+__device__ __forceinline__ i64 dcdiv(i64 x, i64 y) { return (x + y - 1) / y; }
+
+__device__ __forceinline__ unsigned long long task_enc(int mat, int type, int iter, int sub) {
+    return ((unsigned long long)mat << 44) | ((unsigned long long)type << 40) | ((unsigned long long)iter << 20) |
+           (unsigned long long)sub;
+}
+
+__device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_acq_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ void task_push(const MegaArgs& q, unsigned long long t) {
+    const unsigned int idx = atomicAdd(&q.ctl[1], 1u);
+    if (idx >= q.cap) {
+        atomicExch(&q.ctl[3], 1u);
+        return;
+    }
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(q.slots + idx), "l"(t + 1ull) : "memory");
+}
+
+// Thread 0, after every thread of the CTA has finished task (mat, type, iter):
+// if it was the last task of the matrix's phase, start the next phase.
+__device__ void task_done(const BatArgs& a, const MegaArgs& q, int mat, int type, int iter) {
+    __threadfence();
+    if (atomicSub(&q.pending[mat], 1) != 1) return;
+    __threadfence();
+    const BatMat M = a.mats[mat];
+    const BatState* S = a.st + mat;
+    int ntype = T_FINISH, niter = iter, count = 1;
+    switch (type) {
+        case T_INIT:
+            if (!S->done) { ntype = T_SKETCH; count = (int)dcdiv(M.n, CT); }
+            break;
+        case T_SKETCH: ntype = T_QRCP; niter = 0; break;
+        case T_QRCP: ntype = T_PANEL; break;
+        case T_PANEL:
+            if (S->upd_iter == iter) {
+                const i64 c = min(M.n, (i64)iter * M.b + M.b);
+                const int nt = (int)dcdiv(M.n - c, CT);
+                if (nt > 0) { ntype = T_TRAIL; count = nt; }
+            }
+            break;
+        case T_TRAIL:
+            if (S->cont_iter == iter) { ntype = T_QRCP; niter = iter + 1; }
+            break;
+        default:
+            q.finished[mat] = 1;
+            __threadfence();
+            atomicAdd(&q.ctl[2], 1u);
+            return;
+    }
+    q.pending[mat] = count;
+    __threadfence();
+    for (int sub = 0; sub < count; ++sub) task_push(q, task_enc(mat, ntype, niter, sub));
+}
+
+constexpr unsigned long long kPollLimit = 1ull << 27;
+
+__global__ void __launch_bounds__(BT, 2) bat_mega_kernel(BatArgs a, MegaArgs q) {
+    __shared__ unsigned long long s_task;
+    __shared__ int s_stop;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_stop = 0;
+            const unsigned int idx = atomicAdd(&q.ctl[0], 1u);
+            if (idx >= q.cap) {
+                s_stop = 1;
+            } else {
+                unsigned long long spins = 0;
+                for (;;) {
+                    const unsigned long long v = ld_acq_u64(q.slots + idx);
+                    if (v) {
+                        s_task = v - 1ull;
+                        break;
+                    }
+                    if (ld_acq_u32(&q.ctl[2]) >= (unsigned)q.batch || ld_acq_u32(&q.ctl[3])) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if (++spins > kPollLimit) {
+                        atomicExch(&q.ctl[3], 1u);
+                        s_stop = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const unsigned long long t = s_task;
+        const int mat = (int)(t >> 44), type = (int)((t >> 40) & 15ull), iter = (int)((t >> 20) & 0xFFFFFull),
+                  sub = (int)(t & 0xFFFFFull);
+        switch (type) {
+            case T_INIT: body_init(a, mat, 0); break;
+            case T_SKETCH: body_sketch(a, mat, sub); break;
+            case T_QRCP: {
+                body_qrcp(a, mat, 0, iter);
+                const i64 nch = dcdiv(a.mats[mat].m, RCH);
+                for (i64 ch = 0; ch < nch; ++ch) {
+                    __syncthreads();
+                    body_perm(a, mat, (int)ch, iter);
+                }
+                break;
+            }
+            case T_PANEL: body_panel(a, mat, 0, iter, q.kb); break;
+            case T_TRAIL:
+                body_trailing(a, mat, sub, iter, q.kb);
+                __syncthreads();
+                body_skupdate(a, mat, sub, iter);
+                break;
+            default: body_finish(a, mat, 0); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) task_done(a, q, mat, type, iter);
+    }
+}
+
+// Reset the queue for a run: slot i < batch holds INIT of order[i], the rest
+// are empty; every matrix has one pending task.
+__global__ void mega_reset_kernel(MegaArgs q) {
+    const unsigned int stride = gridDim.x * blockDim.x;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.cap; i += stride)
+        q.slots[i] = (i < (unsigned)q.batch) ? task_enc(q.order[i], T_INIT, 0, 0) + 1ull : 0ull;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned)q.batch; i += stride) {
+        q.pending[i] = 1;
+        q.finished[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q.ctl[0] = 0;
+        q.ctl[1] = (unsigned)q.batch;
+        q.ctl[2] = 0;
+        q.ctl[3] = 0;
+    }
+}
+
+// After a run: a matrix the queue did not finish (a worker gave up) reports
+// BQRRP_ETIMEOUT and rank 0.
+__global__ void mega_check_kernel(BatArgs a, MegaArgs q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q.batch || q.finished[i]) return;
+    a.rank_out[i] = 0;
+    if (a.trunc_out) a.trunc_out[i] = 0;
+    if (a.info_out) a.info_out[i] = BQRRP_ETIMEOUT;
 }
 
 }  // namespace
@@ -1104,12 +1336,19 @@ struct BatchPlan {
     };
     std::vector<Launch> launches;
     std::vector<int> smat, spre;
+    // dependency-driven form: queue capacity, initial order, launch shape
+    bool mega = true;
+    unsigned int qcap = 0;
+    std::vector<int> order;
+    size_t dsm_mega = 0;
+    int grid_mega = 0;
     // device image offsets (bytes) in the workspace
     size_t o_mats = 0, o_state = 0, o_smat = 0, o_spre = 0, o_ctr = 0, o_wsd = 0, o_wsi = 0, total = 0;
+    size_t o_order = 0, o_slots = 0, o_qctl = 0, o_pend = 0, o_fin = 0;
     size_t n_wsd = 0, n_wsi = 0;
     // grid sizes
     int grid[8] = {0};
-    size_t dsm_perm = 0, dsm_panel = 0, dsm_trail = 0;
+    size_t dsm_perm = 0, dsm_panel = 0, dsm_trail = 0, dsm_qrcp = 0;
     // device image written where
     void* uploaded_ws = nullptr;
     int device = -1;
@@ -1255,6 +1494,32 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     P->n_wsd = wd;
     P->n_wsi = wi;
 
+    // dependency-driven form: every task a run can push, and the initial order
+    {
+        unsigned long long cap = 0;
+        std::vector<std::pair<double, int>> ord;
+        for (i64 i = 0; i < batch; ++i) {
+            const BatMat& M = P->mats[i];
+            cap += 2;                                           // INIT, FINISH
+            if (M.n > 0) {
+                cap += (unsigned long long)cdiv(M.n, CT);       // SKETCH tiles
+                for (i64 it = 0; it * M.b < M.n; ++it) {
+                    const i64 c = std::min(M.n, it * M.b + M.b);
+                    cap += 2 + (unsigned long long)cdiv(M.n - c, CT);   // QRCP, PANEL, TRAIL tiles
+                }
+            }
+            ord.push_back({2.0 * M.m * (double)M.n * M.n, (int)i});
+        }
+        if (cap >= (1ull << 31)) { set_error("batched: too many tasks"); delete P; return BQRRP_EUNSUPPORTED; }
+        std::stable_sort(ord.begin(), ord.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+            return x.first > y.first;
+        });
+        P->qcap = (unsigned int)std::max<unsigned long long>(cap, 1);
+        for (auto& o : ord) P->order.push_back(o.second);
+        const char* env = getenv("BQRRP_BATCH_LOCKSTEP");
+        P->mega = !(env && env[0] && env[0] != '0');
+    }
+
     // launch list and work queues
     std::vector<std::pair<double, int>> order;
     std::vector<int> ns(batch);
@@ -1302,6 +1567,11 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     P->o_smat = off;  off = align256(off + sizeof(int) * std::max<size_t>(P->smat.size(), 1));
     P->o_spre = off;  off = align256(off + sizeof(int) * std::max<size_t>(P->spre.size(), 1));
     P->o_ctr = off;   off = align256(off + sizeof(unsigned int) * std::max<size_t>(nl, 1));
+    P->o_order = off; off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
+    P->o_slots = off; off = align256(off + sizeof(unsigned long long) * (size_t)P->qcap);
+    P->o_qctl = off;  off = align256(off + sizeof(unsigned int) * 4);
+    P->o_pend = off;  off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
+    P->o_fin = off;   off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
     P->o_wsd = off;   off = align256(off + sizeof(double) * std::max<size_t>(P->n_wsd, 1));
     P->o_wsi = off;   off = align256(off + sizeof(int) * std::max<size_t>(P->n_wsi, 1));
     P->total = off;
@@ -1311,10 +1581,11 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     P->dsm_perm = sizeof(double) * (size_t)maxmoved * RCH;
     P->dsm_panel = sizeof(double) * ((size_t)kb * kb + (size_t)RG * kb);
     P->dsm_trail = sizeof(double) * ((size_t)RT2 * kb + (size_t)RT * CT + (size_t)kb * CT);
+    P->dsm_qrcp = sizeof(double) * NW * kMaxD + sizeof(int) * kMaxN;
     struct KInfo { const void* fn; size_t dsm; };
     const KInfo ki[8] = {
         {(const void*)bat_init_kernel, 0},        {(const void*)bat_sketch_kernel, 0},
-        {(const void*)bat_qrcp_kernel, 0},        {(const void*)bat_perm_kernel, P->dsm_perm},
+        {(const void*)bat_qrcp_kernel, P->dsm_qrcp}, {(const void*)bat_perm_kernel, P->dsm_perm},
         {(const void*)bat_panel_kernel, P->dsm_panel}, {(const void*)bat_trailing_kernel, P->dsm_trail},
         {(const void*)bat_skupdate_kernel, 0},    {(const void*)bat_finish_kernel, 0}};
     for (int q = 0; q < 8; ++q) {
@@ -1337,6 +1608,20 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
         }
         P->grid[q] = occ * dev.sms;
     }
+    P->dsm_mega = std::max(std::max(P->dsm_perm, P->dsm_qrcp), std::max(P->dsm_panel, P->dsm_trail));
+    {
+        cudaError_t e = cudaFuncSetAttribute((const void*)bat_mega_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)P->dsm_mega);
+        int occ = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)bat_mega_kernel, BT, P->dsm_mega);
+        if (e != cudaSuccess || occ < 1) {
+            set_error("dependency-driven kernel cannot be resident (%s)", cudaGetErrorString(e));
+            delete P;
+            return BQRRP_ECUDA;
+        }
+        P->grid_mega = occ * dev.sms;
+    }
     *out = P;
     return 0;
 }
@@ -1349,13 +1634,14 @@ int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, co
 size_t batch_plan_bytes(const BatchPlan* P) { return P ? P->total : 0; }
 
 static int batch_upload(BatchPlan* P, char* ws) {
-    // spre: the prefix list of slot q starts at (slot.first + q); rebuild the
-    // flat array in that order (it already is, by construction in add_slot)
+    // records and launch queues up to the counters, then the initial task order
     std::vector<char> img(P->o_ctr);
     if (P->batch > 0) std::memcpy(img.data() + P->o_mats, P->mats.data(), sizeof(BatMat) * P->batch);
     if (!P->smat.empty()) std::memcpy(img.data() + P->o_smat, P->smat.data(), sizeof(int) * P->smat.size());
     if (!P->spre.empty()) std::memcpy(img.data() + P->o_spre, P->spre.data(), sizeof(int) * P->spre.size());
     BQ_CUDA(cudaMemcpy(ws, img.data(), img.size(), cudaMemcpyHostToDevice));
+    if (!P->order.empty())
+        BQ_CUDA(cudaMemcpy(ws + P->o_order, P->order.data(), sizeof(int) * P->order.size(), cudaMemcpyHostToDevice));
     P->uploaded_ws = ws;
     return 0;
 }
@@ -1364,7 +1650,36 @@ static int batch_upload(BatchPlan* P, char* ws) {
 // LU, piv_transform, gather, Householder QR and tri_rank run in one kernel).
 constexpr int kPhaseOf[8] = {7, 0, 1, 3, 4, 5, 6, 7};
 
+static MegaArgs mega_args(const BatchPlan* P, char* ws) {
+    MegaArgs q;
+    q.slots = (unsigned long long*)(ws + P->o_slots);
+    q.ctl = (unsigned int*)(ws + P->o_qctl);
+    q.pending = (int*)(ws + P->o_pend);
+    q.finished = (int*)(ws + P->o_fin);
+    q.order = (const int*)(ws + P->o_order);
+    q.cap = P->qcap;
+    q.batch = (int)P->batch;
+    q.kb = P->kb;
+    q.nperm = 0;
+    return q;
+}
+
+// The dependency-driven form: reset the queue, one persistent kernel, then
+// mark the matrices a worker gave up on.
+static int batch_launch_mega(BatchPlan* P, BatArgs a, cudaStream_t st, char* ws) {
+    const MegaArgs q = mega_args(P, ws);
+    const unsigned rb = (unsigned)std::min<i64>(1024, std::max<i64>(1, cdiv((i64)P->qcap, 256)));
+    mega_reset_kernel<<<rb, 256, 0, st>>>(q);
+    BQ_LAUNCH_CHECK();
+    bat_mega_kernel<<<P->grid_mega, BT, P->dsm_mega, st>>>(a, q);
+    BQ_LAUNCH_CHECK();
+    mega_check_kernel<<<(unsigned)cdiv(P->batch, 256), 256, 0, st>>>(a, q);
+    BQ_LAUNCH_CHECK();
+    return 0;
+}
+
 static int batch_launch_all(BatchPlan* P, BatArgs a, cudaStream_t st, char* ws, std::vector<cudaEvent_t>* ev) {
+    if (P->mega && !ev) return batch_launch_mega(P, a, st, ws);
     BQ_CUDA(cudaMemsetAsync(ws + P->o_ctr, 0, sizeof(unsigned int) * std::max<size_t>(P->launches.size(), 1), st));
     for (size_t q = 0; q < P->launches.size(); ++q) {
         const BatchPlan::Launch& L = P->launches[q];
@@ -1375,7 +1690,7 @@ static int batch_launch_all(BatchPlan* P, BatArgs a, cudaStream_t st, char* ws, 
         switch (L.kind) {
             case BatchPlan::K_INIT: bat_init_kernel<<<g, BT, 0, st>>>(a, L.slot, sid); break;
             case BatchPlan::K_SKETCH: bat_sketch_kernel<<<g, BT, 0, st>>>(a, L.slot, sid); break;
-            case BatchPlan::K_QRCP: bat_qrcp_kernel<<<g, BT, 0, st>>>(a, L.slot, sid, L.iter); break;
+            case BatchPlan::K_QRCP: bat_qrcp_kernel<<<g, BT, P->dsm_qrcp, st>>>(a, L.slot, sid, L.iter); break;
             case BatchPlan::K_PERM: bat_perm_kernel<<<g, BT, P->dsm_perm, st>>>(a, L.slot, sid, L.iter); break;
             case BatchPlan::K_PANEL:
                 bat_panel_kernel<<<g, BT, P->dsm_panel, st>>>(a, L.slot, sid, L.iter, P->kb);
@@ -1498,6 +1813,7 @@ double batch_plan_flops(const BatchPlan* P, int phase) {
 
 int batch_plan_launches(const BatchPlan* P) {
     if (!P) return 0;
+    if (P->mega) return 3;
     int c = 0;
     for (auto& L : P->launches) c += L.slot.total > 0;
     return c;

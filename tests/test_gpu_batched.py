@@ -199,3 +199,23 @@ def test_batched_autotune_choices_are_valid_and_meet_the_bar():
     pick = [0, 17, 42, 59]
     sub = [mats[i] for i in pick]
     check_against_oracle(sub, b[pick], d[pick], seeds[pick], run_batch(sub, b[pick], d[pick], seeds[pick]))
+
+
+def test_dependency_driven_and_lockstep_forms_agree_bitwise(monkeypatch):
+    """The default form runs every phase from one device task queue; the
+    lock-step form (BQRRP_BATCH_LOCKSTEP=1) launches one kernel per phase and
+    iteration.  Both run the same per-phase arithmetic."""
+    m, n = W.batched_shapes(30, 17, m_hi=500)
+    mats = [W.batched_matrix(int(a), int(c), 800 + i) for i, (a, c) in enumerate(zip(m, n))]
+    b = np.array([[16, 32, 64][i % 3] for i in range(30)], dtype=np.int64)
+    d = np.ceil(1.25 * b).astype(np.int64)
+    seeds = np.arange(30, dtype=np.uint64) + 77
+    mega = run_batch(mats, b, d, seeds, use_graph=True)
+    monkeypatch.setenv("BQRRP_BATCH_LOCKSTEP", "1")
+    lock = run_batch(mats, b, d, seeds, use_graph=True)
+    for x, y in zip(mega, lock):
+        assert np.array_equal(x, y)
+    check_against_oracle(mats[:6], b[:6], d[:6], seeds[:6],
+                         (mega[0][:6], mega[1][:6], mega[2][:W.batch_offsets(mega[0][:6], mega[1][:6])[2]],
+                          mega[3][:W.batch_offsets(mega[0][:6], mega[1][:6])[3]],
+                          mega[4][:W.batch_offsets(mega[0][:6], mega[1][:6])[3]], mega[5][:6], mega[6][:6], mega[7][:6]))
