@@ -1143,22 +1143,29 @@ __global__ void __launch_bounds__(BT) bat_finish_kernel(BatArgs a, Slot sl, int 
 //   TRAIL (one task per 64-column tile, plus that tile's sketch update)
 //   -> QRCP of the next block, or FINISH.
 // The last finisher of a phase (an atomic count per matrix) pushes the next
-// phase's tasks.  The queue is a slot array written once per run: a slot holds
-// task + 1 once published (release store), 0 before.  A worker takes the next
-// slot index and polls it (acquire) until it is published or every matrix is
-// done; polls are bounded, and a worker that gives up records a timeout.
+// phase's tasks.  There are two queues, each a slot array written once per
+// run (a slot holds task + 1 once published by a release store, 0 before):
+//  - the hot queue takes every task of the largest matrices, whose chains of
+//    phases are the critical path;
+//  - the normal queue takes the rest.
+// A worker reserves the next normal slot; while that slot is unpublished it
+// claims published hot tasks (compare-and-swap on the hot head) and runs
+// them, keeping its reservation.  Polls are bounded; a worker that gives up
+// records a timeout.
 enum : int { T_INIT = 0, T_SKETCH = 1, T_QRCP = 2, T_PANEL = 3, T_TRAIL = 4, T_FINISH = 5 };
 
 struct MegaArgs {
-    unsigned long long* slots;   // cap entries
-    unsigned int* ctl;           // [0] head, [1] tail, [2] matrices done, [3] error
+    unsigned long long* slots;   // normal queue, cap entries
+    unsigned long long* hslots;  // hot queue, hcap entries
+    unsigned int* ctl;           // [0] head, [1] tail, [2] matrices done, [3] error, [4] hot head, [5] hot tail
     int* pending;                // per matrix: unfinished tasks of its current phase
     int* finished;               // per matrix: 1 once FINISH has run
-    const int* order;            // initial INIT order (largest first)
-    unsigned int cap;
+    const int* order;            // initial INIT order (largest first); the first nhot are hot
+    const int* hot;              // per matrix: 1 if its tasks go to the hot queue
+    unsigned int cap, hcap;
     int batch;
+    int nhot;
     int kb;
-    int nperm;                   // unused placeholder for alignment
 };
 
 __device__ __forceinline__ i64 dcdiv(i64 x, i64 y) { return (x + y - 1) / y; }
@@ -1179,13 +1186,14 @@ __device__ __forceinline__ unsigned int ld_acq_u32(const unsigned int* p) {
     return v;
 }
 
-__device__ void task_push(const MegaArgs& q, unsigned long long t) {
-    const unsigned int idx = atomicAdd(&q.ctl[1], 1u);
-    if (idx >= q.cap) {
+__device__ void task_push(const MegaArgs& q, unsigned long long t, bool hot) {
+    const unsigned int idx = atomicAdd(&q.ctl[hot ? 5 : 1], 1u);
+    if (idx >= (hot ? q.hcap : q.cap)) {
         atomicExch(&q.ctl[3], 1u);
         return;
     }
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(q.slots + idx), "l"(t + 1ull) : "memory");
+    unsigned long long* slot = (hot ? q.hslots : q.slots) + idx;
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(t + 1ull) : "memory");
 }
 
 // Thread 0, after every thread of the CTA has finished task (mat, type, iter):
@@ -1221,7 +1229,8 @@ __device__ void task_done(const BatArgs& a, const MegaArgs& q, int mat, int type
     }
     q.pending[mat] = count;
     __threadfence();
-    for (int sub = 0; sub < count; ++sub) task_push(q, task_enc(mat, ntype, niter, sub));
+    const bool hot = q.hot[mat] != 0;
+    for (int sub = 0; sub < count; ++sub) task_push(q, task_enc(mat, ntype, niter, sub), hot);
 }
 
 constexpr unsigned long long kPollLimit = 1ull << 27;
@@ -1229,30 +1238,49 @@ constexpr unsigned long long kPollLimit = 1ull << 27;
 __global__ void __launch_bounds__(BT, 2) bat_mega_kernel(BatArgs a, MegaArgs q) {
     __shared__ unsigned long long s_task;
     __shared__ int s_stop;
+    __shared__ unsigned int s_low;    // reserved normal slot (valid while s_have)
+    __shared__ int s_have;
+    if (threadIdx.x == 0) s_have = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             s_stop = 0;
-            const unsigned int idx = atomicAdd(&q.ctl[0], 1u);
-            if (idx >= q.cap) {
-                s_stop = 1;
-            } else {
-                unsigned long long spins = 0;
-                for (;;) {
-                    const unsigned long long v = ld_acq_u64(q.slots + idx);
+            if (!s_have) {
+                s_low = atomicAdd(&q.ctl[0], 1u);
+                s_have = 1;
+            }
+            const bool low_ok = s_low < q.cap;
+            unsigned long long spins = 0;
+            for (;;) {
+                // a published hot task, if any
+                const unsigned int h = *((volatile unsigned int*)&q.ctl[4]);
+                if (h < q.hcap) {
+                    const unsigned long long v = ld_acq_u64(q.hslots + h);
+                    if (v) {
+                        if (atomicCAS(&q.ctl[4], h, h + 1) == h) {
+                            s_task = v - 1ull;
+                            break;
+                        }
+                        continue;
+                    }
+                }
+                // the reserved normal slot
+                if (low_ok) {
+                    const unsigned long long v = ld_acq_u64(q.slots + s_low);
                     if (v) {
                         s_task = v - 1ull;
+                        s_have = 0;
                         break;
                     }
-                    if (ld_acq_u32(&q.ctl[2]) >= (unsigned)q.batch || ld_acq_u32(&q.ctl[3])) {
-                        s_stop = 1;
-                        break;
-                    }
-                    if (++spins > kPollLimit) {
-                        atomicExch(&q.ctl[3], 1u);
-                        s_stop = 1;
-                        break;
-                    }
+                }
+                if (ld_acq_u32(&q.ctl[2]) >= (unsigned)q.batch || ld_acq_u32(&q.ctl[3])) {
+                    s_stop = 1;
+                    break;
+                }
+                if (++spins > kPollLimit) {
+                    atomicExch(&q.ctl[3], 1u);
+                    s_stop = 1;
+                    break;
                 }
             }
         }
@@ -1290,17 +1318,22 @@ __global__ void __launch_bounds__(BT, 2) bat_mega_kernel(BatArgs a, MegaArgs q) 
 // are empty; every matrix has one pending task.
 __global__ void mega_reset_kernel(MegaArgs q) {
     const unsigned int stride = gridDim.x * blockDim.x;
+    const unsigned int nlow = (unsigned)(q.batch - q.nhot);
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.cap; i += stride)
-        q.slots[i] = (i < (unsigned)q.batch) ? task_enc(q.order[i], T_INIT, 0, 0) + 1ull : 0ull;
+        q.slots[i] = (i < nlow) ? task_enc(q.order[q.nhot + i], T_INIT, 0, 0) + 1ull : 0ull;
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.hcap; i += stride)
+        q.hslots[i] = (i < (unsigned)q.nhot) ? task_enc(q.order[i], T_INIT, 0, 0) + 1ull : 0ull;
     for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned)q.batch; i += stride) {
         q.pending[i] = 1;
         q.finished[i] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         q.ctl[0] = 0;
-        q.ctl[1] = (unsigned)q.batch;
+        q.ctl[1] = nlow;
         q.ctl[2] = 0;
         q.ctl[3] = 0;
+        q.ctl[4] = 0;
+        q.ctl[5] = (unsigned)q.nhot;
     }
 }
 
@@ -1338,13 +1371,14 @@ struct BatchPlan {
     std::vector<int> smat, spre;
     // dependency-driven form: queue capacity, initial order, launch shape
     bool mega = true;
-    unsigned int qcap = 0;
-    std::vector<int> order;
+    unsigned int qcap = 0, hcap = 0;
+    int nhot = 0;
+    std::vector<int> order, hot;
     size_t dsm_mega = 0;
     int grid_mega = 0;
     // device image offsets (bytes) in the workspace
     size_t o_mats = 0, o_state = 0, o_smat = 0, o_spre = 0, o_ctr = 0, o_wsd = 0, o_wsi = 0, total = 0;
-    size_t o_order = 0, o_slots = 0, o_qctl = 0, o_pend = 0, o_fin = 0;
+    size_t o_order = 0, o_slots = 0, o_qctl = 0, o_pend = 0, o_fin = 0, o_hot = 0, o_hslots = 0;
     size_t n_wsd = 0, n_wsi = 0;
     // grid sizes
     int grid[8] = {0};
@@ -1494,28 +1528,45 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     P->n_wsd = wd;
     P->n_wsi = wi;
 
-    // dependency-driven form: every task a run can push, and the initial order
+    // dependency-driven form: the initial order (largest first), the hot
+    // matrices (the largest tenth, 1 to 512 of them) and every task a run can
+    // push into each queue
     {
-        unsigned long long cap = 0;
         std::vector<std::pair<double, int>> ord;
+        std::vector<unsigned long long> tasks(batch);
         for (i64 i = 0; i < batch; ++i) {
             const BatMat& M = P->mats[i];
-            cap += 2;                                           // INIT, FINISH
+            unsigned long long t = 2;                           // INIT, FINISH
             if (M.n > 0) {
-                cap += (unsigned long long)cdiv(M.n, CT);       // SKETCH tiles
+                t += (unsigned long long)cdiv(M.n, CT);         // SKETCH tiles
                 for (i64 it = 0; it * M.b < M.n; ++it) {
                     const i64 c = std::min(M.n, it * M.b + M.b);
-                    cap += 2 + (unsigned long long)cdiv(M.n - c, CT);   // QRCP, PANEL, TRAIL tiles
+                    t += 2 + (unsigned long long)cdiv(M.n - c, CT);     // QRCP, PANEL, TRAIL tiles
                 }
             }
+            tasks[i] = t;
             ord.push_back({2.0 * M.m * (double)M.n * M.n, (int)i});
         }
-        if (cap >= (1ull << 31)) { set_error("batched: too many tasks"); delete P; return BQRRP_EUNSUPPORTED; }
         std::stable_sort(ord.begin(), ord.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
             return x.first > y.first;
         });
+        P->nhot = (int)std::min<i64>(batch, std::min<i64>(512, std::max<i64>(1, batch / 10)));
+        if (batch == 0) P->nhot = 0;
+        P->hot.assign(batch, 0);
+        unsigned long long cap = 0, hcap = 0;
+        for (i64 r = 0; r < batch; ++r) {
+            const int i = ord[r].second;
+            P->order.push_back(i);
+            if (r < P->nhot) {
+                P->hot[i] = 1;
+                hcap += tasks[i];
+            } else {
+                cap += tasks[i];
+            }
+        }
+        if (cap + hcap >= (1ull << 31)) { set_error("batched: too many tasks"); delete P; return BQRRP_EUNSUPPORTED; }
         P->qcap = (unsigned int)std::max<unsigned long long>(cap, 1);
-        for (auto& o : ord) P->order.push_back(o.second);
+        P->hcap = (unsigned int)std::max<unsigned long long>(hcap, 1);
         const char* env = getenv("BQRRP_BATCH_LOCKSTEP");
         P->mega = !(env && env[0] && env[0] != '0');
     }
@@ -1569,7 +1620,9 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
     P->o_ctr = off;   off = align256(off + sizeof(unsigned int) * std::max<size_t>(nl, 1));
     P->o_order = off; off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
     P->o_slots = off; off = align256(off + sizeof(unsigned long long) * (size_t)P->qcap);
-    P->o_qctl = off;  off = align256(off + sizeof(unsigned int) * 4);
+    P->o_hslots = off; off = align256(off + sizeof(unsigned long long) * (size_t)P->hcap);
+    P->o_hot = off;   off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
+    P->o_qctl = off;  off = align256(off + sizeof(unsigned int) * 8);
     P->o_pend = off;  off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
     P->o_fin = off;   off = align256(off + sizeof(int) * std::max<i64>(batch, 1));
     P->o_wsd = off;   off = align256(off + sizeof(double) * std::max<size_t>(P->n_wsd, 1));
@@ -1640,8 +1693,10 @@ static int batch_upload(BatchPlan* P, char* ws) {
     if (!P->smat.empty()) std::memcpy(img.data() + P->o_smat, P->smat.data(), sizeof(int) * P->smat.size());
     if (!P->spre.empty()) std::memcpy(img.data() + P->o_spre, P->spre.data(), sizeof(int) * P->spre.size());
     BQ_CUDA(cudaMemcpy(ws, img.data(), img.size(), cudaMemcpyHostToDevice));
-    if (!P->order.empty())
+    if (!P->order.empty()) {
         BQ_CUDA(cudaMemcpy(ws + P->o_order, P->order.data(), sizeof(int) * P->order.size(), cudaMemcpyHostToDevice));
+        BQ_CUDA(cudaMemcpy(ws + P->o_hot, P->hot.data(), sizeof(int) * P->hot.size(), cudaMemcpyHostToDevice));
+    }
     P->uploaded_ws = ws;
     return 0;
 }
@@ -1653,14 +1708,17 @@ constexpr int kPhaseOf[8] = {7, 0, 1, 3, 4, 5, 6, 7};
 static MegaArgs mega_args(const BatchPlan* P, char* ws) {
     MegaArgs q;
     q.slots = (unsigned long long*)(ws + P->o_slots);
+    q.hslots = (unsigned long long*)(ws + P->o_hslots);
     q.ctl = (unsigned int*)(ws + P->o_qctl);
     q.pending = (int*)(ws + P->o_pend);
     q.finished = (int*)(ws + P->o_fin);
     q.order = (const int*)(ws + P->o_order);
+    q.hot = (const int*)(ws + P->o_hot);
     q.cap = P->qcap;
+    q.hcap = P->hcap;
     q.batch = (int)P->batch;
+    q.nhot = P->nhot;
     q.kb = P->kb;
-    q.nperm = 0;
     return q;
 }
 
@@ -1668,7 +1726,7 @@ static MegaArgs mega_args(const BatchPlan* P, char* ws) {
 // mark the matrices a worker gave up on.
 static int batch_launch_mega(BatchPlan* P, BatArgs a, cudaStream_t st, char* ws) {
     const MegaArgs q = mega_args(P, ws);
-    const unsigned rb = (unsigned)std::min<i64>(1024, std::max<i64>(1, cdiv((i64)P->qcap, 256)));
+    const unsigned rb = (unsigned)std::min<i64>(1024, std::max<i64>(1, cdiv((i64)std::max(P->qcap, P->hcap), 256)));
     mega_reset_kernel<<<rb, 256, 0, st>>>(q);
     BQ_LAUNCH_CHECK();
     bat_mega_kernel<<<P->grid_mega, BT, P->dsm_mega, st>>>(a, q);
