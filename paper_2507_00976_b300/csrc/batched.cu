@@ -1376,6 +1376,7 @@ struct BatchPlan {
     std::vector<int> order, hot;
     size_t dsm_mega = 0;
     int grid_mega = 0;
+    int grid_cap = 0;                // > 0: at most this many persistent CTAs (leaves SMs to other work)
     // device image offsets (bytes) in the workspace
     size_t o_mats = 0, o_state = 0, o_smat = 0, o_spre = 0, o_ctr = 0, o_wsd = 0, o_wsi = 0, total = 0;
     size_t o_order = 0, o_slots = 0, o_qctl = 0, o_pend = 0, o_fin = 0, o_hot = 0, o_hslots = 0;
@@ -1729,7 +1730,8 @@ static int batch_launch_mega(BatchPlan* P, BatArgs a, cudaStream_t st, char* ws)
     const unsigned rb = (unsigned)std::min<i64>(1024, std::max<i64>(1, cdiv((i64)std::max(P->qcap, P->hcap), 256)));
     mega_reset_kernel<<<rb, 256, 0, st>>>(q);
     BQ_LAUNCH_CHECK();
-    bat_mega_kernel<<<P->grid_mega, BT, P->dsm_mega, st>>>(a, q);
+    const int grid = (P->grid_cap > 0) ? std::min(P->grid_cap, P->grid_mega) : P->grid_mega;
+    bat_mega_kernel<<<grid, BT, P->dsm_mega, st>>>(a, q);
     BQ_LAUNCH_CHECK();
     mega_check_kernel<<<(unsigned)cdiv(P->batch, 256), 256, 0, st>>>(a, q);
     BQ_LAUNCH_CHECK();
@@ -1860,6 +1862,14 @@ int batch_factor(BatchPlan* P, double* A, int64_t* jpvt, double* tau, int64_t* r
 }
 
 void batch_plan_destroy(BatchPlan* P) { delete P; }
+
+void batch_plan_set_grid_cap(BatchPlan* P, int ctas) {
+    if (P) P->grid_cap = ctas;
+}
+
+void batch_plan_set_lockstep(BatchPlan* P, bool on) {
+    if (P) P->mega = !on;
+}
 
 double batch_plan_flops(const BatchPlan* P, int phase) {
     double f = 0.0;

@@ -189,6 +189,12 @@ size_t batch_plan_bytes(const BatchPlan* P);
 int batch_factor(BatchPlan* P, double* A, int64_t* jpvt, double* tau, int64_t* rank, int64_t* trunc,
                  int32_t* info, void* ws, size_t ws_bytes, cudaStream_t stream, int use_graph);
 void batch_plan_destroy(BatchPlan* P);
+// Cap the dependency-driven kernel's grid (persistent CTAs), leaving SMs to
+// concurrent work; 0 removes the cap.
+void batch_plan_set_grid_cap(BatchPlan* P, int ctas);
+// Run the plan as one kernel per phase and block iteration (short launches
+// that interleave with concurrent work) instead of the persistent form.
+void batch_plan_set_lockstep(BatchPlan* P, bool on);
 
 // ------------------------------------------------------------------ launchers (internal API)
 struct Ctx {

@@ -14,9 +14,10 @@
 // Two lanes run concurrently, each with its own worker thread, CUDA stream and
 // half of the workspace arena:
 //  - small lane (m*n <= small_max_elems): every admitted small request is
-//    factored in one batched call (the lock-step batched kernels, addressing
-//    each request's state in place through per-matrix offsets).  Requests
-//    that arrive meanwhile join the next batch (continuous batching);
+//    factored in one batched call (the lock-step batched kernels, whose short
+//    launches interleave with the large lane, addressing each request's state
+//    in place through per-matrix offsets).  Requests that arrive meanwhile join
+//    the next batch (continuous batching);
 //  - large lane: one admitted large request at a time, through the
 //    single-matrix path.
 // The batched kernels never wait on other work, so the single-matrix path's
@@ -257,6 +258,9 @@ int Server::do_small(std::vector<Req*>& batch) {
     int rc = batch_plan_create_ex(&P, nb, m.data(), n.data(), b.data(), d.data(), sd.data(), tol, oA.data(),
                                   oJ.data(), oT.data());
     if (rc != 0) return rc;
+    // short per-phase launches: they interleave with the large lane's
+    // grid-wide kernels, where the persistent form would hold the SMs
+    batch_plan_set_lockstep(P, true);
     // workspace arena: rank, truncation rank, info, then the plan's workspace
     char* w = wsbase[0];
     int64_t* rk = (int64_t*)w;   w += up(sizeof(int64_t) * nb);
