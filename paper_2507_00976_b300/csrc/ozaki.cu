@@ -24,6 +24,8 @@
 
 #include <cstdlib>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bq {
@@ -293,11 +295,10 @@ inline i64 rup(i64 x, i64 m) { return (x + m - 1) / m * m; }
 template <int SA, int SB, int TMAX>
 int launch_mma(const Ctx& c, OzArgs a, i64 Mp, i64 Np) {
     const size_t smem = 2ull * (size_t)(SA * OBM + SB * OBN) * OPAD * sizeof(__nv_bfloat16);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
         cudaFuncSetAttribute(ozaki_mma_kernel<SA, SB, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     if (Np / OBN > 65535) { set_error("ozaki: N too large"); return BQRRP_EUNSUPPORTED; }
     dim3 grid((unsigned)(Mp / OBM), (unsigned)(Np / OBN));
     ozaki_mma_kernel<SA, SB, TMAX><<<grid, ONT, smem, c.stream>>>(a);

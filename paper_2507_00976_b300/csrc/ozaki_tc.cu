@@ -34,6 +34,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bq {
@@ -382,16 +384,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* f = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (EncodeTiledFn)f;
-    }
+    });
     return fn;
 }
 
@@ -418,11 +419,10 @@ int launch_tc(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16
     BQ_TRY(make_plane_map(&tmA, As, ldk, Mp, SA, TC_M, 1));
     BQ_TRY(make_plane_map(&tmB, Bs, ldk, Np, SB, TC_N, SB));
     const size_t smem = 1024 + (size_t)TC_NA * TC_ABYTES + (size_t)TC_NB * SB * TC_BPLANE + 8 * (2 * TC_NA + 2 * TC_NB + 3) + 16;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
         cudaFuncSetAttribute(ozaki_tc_kernel<SA, SB, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     TcArgs a;
     a.M = M;
     a.N = N;

@@ -20,6 +20,9 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bq {
@@ -594,11 +597,10 @@ static int launch_coop(const Ctx& c, const void* kernel, int grid, size_t smem, 
 int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
     const i64 steps = imin(N, d);
     if (steps <= 0) return 0;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_set_once;
+    std::call_once(attr_set_once, [&] {
         cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemLu);
-        attr_set = true;
-    }
+    });
     const i64 nbmax = 64;
     const int Gmax_all = (int)imin(c.dev.sms, 148);
     size_t need = 0;
@@ -663,12 +665,11 @@ constexpr i64 kClusterRowsMax = 16 * 280;   // 16 CTAs x 280 rows x 64 columns f
 // cooperative grid kernel), or an error code.
 static int hh_panel_cluster(const Ctx& c, i64 prow, int pw, double* Ap, i64 lda, double* tau, double* V, i64 ldv,
                             double* T, i64 ldt) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_set_once;
+    std::call_once(attr_set_once, [&] {
         cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
-        attr_set = true;
-    }
+    });
     int C = (int)imin(16, imax(1, cdiv(prow, 32)));
     i64 R = cdiv(prow, C);
     C = (int)cdiv(prow, R);
@@ -693,12 +694,10 @@ static int hh_panel_cluster(const Ctx& c, i64 prow, int pw, double* Ap, i64 lda,
     const cudaError_t e = cudaLaunchKernelEx(&cfg, hh_panel_cluster_kernel, a);
     if (e != cudaSuccess) {
         cudaGetLastError();   // clear the launch error; the grid kernel takes over
-        static bool logged = false;
-        if (!logged && getenv("BQRRP_LOG")) {
+        static std::atomic<bool> logged{false};
+        if (getenv("BQRRP_LOG") && !logged.exchange(true))
             fprintf(stderr, "bqrrp: cluster launch (%d CTAs, %zu B smem) failed: %s; using the grid kernel\n", C,
                     smem, cudaGetErrorString(e));
-            logged = true;
-        }
         return -1;
     }
     return 0;
@@ -713,11 +712,10 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
     if (kstop >= 0) kk = imin(kk, kstop);   // factor only the first kstop columns, update all
     if (kk <= 0) return 0;
     if (nb > 64) nb = 64;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_set_once;
+    std::call_once(attr_set_once, [&] {
         cudaFuncSetAttribute(hh_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
-        attr_set = true;
-    }
+    });
     const int Gmax_all = (int)imin(c.dev.sms, 148);
     size_t need = 0;
     coop_scratch_elems(nb, Gmax_all, &need);

@@ -5,6 +5,8 @@
 // per column, the "fast sparse operator" the paper mentions for its tall
 // predecessor, Sec. 2 remark): applied as a deterministic sparse x dense
 // product, reading A once.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bq {
@@ -253,11 +255,10 @@ int sketch_sparse_apply(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, i64 nn
     BQ_LAUNCH_CHECK();
     sort_rows_kernel<<<(unsigned)cdiv(d, 128), 128, 0, c.stream>>>(d, w.ptr, w.col, w.val);
     BQ_LAUNCH_CHECK();
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
         cudaFuncSetAttribute(sparse_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    });
     sparse_apply_kernel<<<(unsigned)cdiv(n, SJ), 256, smem, c.stream>>>(d, m, n, A, lda, w.ptr, w.col, w.val, Msk,
                                                                          ldsk);
     BQ_LAUNCH_CHECK();
