@@ -541,7 +541,9 @@ def run_batched(a, world, rank, local):
 
 
 # ------------------------------------------------------------------ serving workload
-SERVING_SHAPES = [(256, 256, 64, 80), (1024, 512, 64, 80), (4096, 2048, 256, 320), (8192, 4096, 512, 640)]
+# (m, n, b, d): b is the fastest of a sweep on this part (8192 x 4096: 128 over 256 and 512; 4096 x 2048: 64 over
+# 128 and 256); the two small shapes use b = 32 in the batched lane
+SERVING_SHAPES = [(256, 256, 32, 40), (1024, 512, 32, 40), (4096, 2048, 64, 80), (8192, 4096, 128, 160)]
 SERVING_WEIGHTS = [0.5, 0.3, 0.15, 0.05]
 
 

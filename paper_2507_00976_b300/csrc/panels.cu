@@ -798,6 +798,129 @@ __global__ void zero_rows_kernel(i64 r0, i64 r1, i64 N, double* X, i64 ldx) {
 // row signs cancel in everything BQRRP derives from R^sk (R11, Y, T) and leave
 // the next LU's pivots unchanged.  Writes R^sk (zeros below the diagonal) into
 // Sk (d x N, ld ldsk); X (the LU factors) is consumed.
+namespace {
+// R factor of the Householder QR (dlarfg convention) of a small d x s matrix
+// W (ld d, s <= d) held entirely in the distributed shared memory of one
+// thread-block cluster.  Column c lives in CTA c mod C at local slot c / C.
+// Step j: the owner of column j forms the reflector and publishes it in its
+// shared memory (double-buffered by step parity); after one cluster barrier
+// every CTA copies it through DSMEM and applies it to its own columns.  Only
+// R (upper triangle, zeros below) is written back to W.
+constexpr int kSqrMaxD = 640;
+
+__global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
+    extern __shared__ double loc[];                 // [ncl][d] local columns
+    __shared__ double vbuf[2][kSqrMaxD];
+    __shared__ double vloc[kSqrMaxD];
+    __shared__ double s_tau[2];
+    __shared__ double red[NT / 32];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), g = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncl = (int)((s - g + C - 1) / C);    // columns g, g + C, ... below s
+    for (int lc = 0; lc < ncl; ++lc) {
+        const i64 gc = (i64)lc * C + g;
+        for (i64 r = tid; r < d; r += NT) loc[(i64)lc * d + r] = W[r + gc * d];
+    }
+    __syncthreads();
+    for (i64 j = 0; j < s; ++j) {
+        const int o = (int)(j % C), par = (int)(j & 1);
+        if (g == o) {
+            double* x = loc + (j / C) * d;
+            double xn2 = 0.0;
+            for (i64 r = j + 1 + tid; r < d; r += NT) xn2 += x[r] * x[r];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
+            if (lane == 0) red[warp] = xn2;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int q = 0; q < NT / 32; ++q) t += red[q];
+                red[0] = t;
+            }
+            __syncthreads();
+            xn2 = red[0];
+            const double alpha = x[j];
+            double tau = 0.0, beta = alpha, scal = 1.0;
+            if (xn2 != 0.0) {
+                const double nrm = sqrt(alpha * alpha + xn2);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            for (i64 r = j + 1 + tid; r < d; r += NT) {
+                const double v = (xn2 != 0.0) ? x[r] * scal : x[r];
+                vbuf[par][r] = v;
+                x[r] = 0.0;                                   // below the diagonal of R
+            }
+            if (tid == 0) {
+                vbuf[par][j] = 1.0;
+                x[j] = beta;
+                s_tau[par] = tau;
+            }
+        }
+        cl.sync();
+        // the reflector of column j, from its owner
+        const double* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
+        const double* tsrc = cl.map_shared_rank(&s_tau[par], o);
+        for (i64 r = j + tid; r < d; r += NT) vloc[r] = vsrc[r];
+        const double tau = *tsrc;
+        __syncthreads();
+        if (tau != 0.0) {
+            for (int lc = warp; lc < ncl; lc += NT / 32) {
+                const i64 gc = (i64)lc * C + g;
+                if (gc <= j) continue;
+                double* col = loc + (i64)lc * d;
+                double dot = 0.0;
+                for (i64 r = j + lane; r < d; r += 32) dot += vloc[r] * col[r];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+                const double w = tau * dot;
+                for (i64 r = j + lane; r < d; r += 32) col[r] -= w * vloc[r];
+            }
+        }
+        __syncthreads();
+    }
+    for (int lc = 0; lc < ncl; ++lc) {
+        const i64 gc = (i64)lc * C + g;
+        for (i64 r = tid; r < d; r += NT) W[r + gc * d] = (r <= gc) ? loc[(i64)lc * d + r] : 0.0;
+    }
+    cl.sync();    // no CTA leaves while another may still read its shared memory
+}
+
+// Launch on a cluster of up to 16 CTAs; -1 when the shape or the cluster does
+// not fit (the caller then uses the blocked QR).
+int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
+    if (d > kSqrMaxD || s < 1 || s > d) return -1;
+    int C = 16;
+    size_t smem = (size_t)((s + C - 1) / C) * (size_t)d * sizeof(double);
+    if (smem > 208 * 1024) return -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(small_qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(small_qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 208 * 1024);
+    });
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launch();
+    if (cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel, d, s, W) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return 0;
+}
+}  // namespace
+
 int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 ldsk, double* Ub, double* tau,
                 double* V, double* T, double* W, double* W2) {
     const i64 s = imin(N, d);
@@ -805,8 +928,12 @@ int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 
     const unsigned blocks = (unsigned)imax(1, imin(cdiv(d * N, 256), 8LL * c.dev.sms));
     lu_split_kernel<<<blocks, 256, 0, c.stream>>>(d, s, N, X, ldx, Ub, d);
     BQ_LAUNCH_CHECK();
-    BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
-    BQ_TRY(set_zero_below(c, s, s, Ub, d));
+    // R1 of U^T: on one cluster when the d x s factor fits its shared memory,
+    // else by the blocked Householder QR
+    if (small_qr_cluster(c, d, s, Ub) != 0) {
+        BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
+        BQ_TRY(set_zero_below(c, s, s, Ub, d));
+    }
     BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk));
     if (s < d) {
         zero_rows_kernel<<<blocks, 256, 0, c.stream>>>(s, d, N, Sk, ldsk);
