@@ -2,8 +2,8 @@
 //
 // Every O(b^3) step of the panel (Alg. 3) is cast as a right-looking blocked
 // algorithm: a 64-wide diagonal block handled by one CTA in shared memory (or,
-// for triangular solves, one thread per matrix row with the block in shared
-// memory) plus GEMM updates that spread over all SMs.  With B300's slow FP64
+// for triangular solves, one warp per matrix row with the block in shared
+// memory, rows spread over all SMs) plus GEMM updates.  With B300's slow FP64
 // pipe a single SM runs at ~8 GFLOP/s, so nothing of size b^3 may stay on one
 // SM.
 #include <climits>
@@ -17,69 +17,53 @@ namespace {
 constexpr int NBD = 64;   // diagonal block size
 
 // X <- X * R^{-1} for the nb (<= 64) columns of X; R upper (unit diagonal if
-// unit != 0; then only the strictly upper part of R is read).  One thread per
-// row of X, the triangle of R in shared memory.
-template <int NB>
-__global__ void __launch_bounds__(64) trsm_small_kernel(i64 rows, int nb, View R, View X, int unit) {
-    __shared__ double Rs[NB][NB + 1];
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int t = e % NB, j = e / NB;
-        double v = 0.0;
-        if (t < nb && j < nb && t <= j) v = (t == j && unit) ? 1.0 : *R.at(t, j);
-        Rs[t][j] = v;
-    }
+// unit != 0; then only the strictly upper part of R is read).
+//
+// The kernel factors R = D R' (D = diag(R), R' unit upper with R'(t, j) =
+// R(t, j) / R(t, t)), solves y R' = x by forward substitution and returns
+// x = y D^{-1}: the dependency chain then holds only FMAs, and the nb
+// divisions happen once per CTA instead of once per row and column.  On
+// B300 every FP64 instruction is slow (2 DFMA/clk/SM), so rows are spread
+// over all SMs.
+__device__ inline void load_unit_triangle(int nb, View R, int unit, double (*Rs)[NBD + 1], double* dinv) {
+    for (int e = threadIdx.x; e < NBD; e += blockDim.x) dinv[e] = (e < nb && !unit) ? 1.0 / *R.at(e, e) : 1.0;
     __syncthreads();
-    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    double x[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) x[j] = (j < nb) ? *X.at(i, j) : 0.0;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (j < nb) {
-            double s = x[j];
-#pragma unroll
-            for (int t = 0; t < j; ++t) s = fma(-x[t], Rs[t][j], s);
-            x[j] = unit ? s : s / Rs[j][j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if (j < nb) *X.at(i, j) = x[j];
-}
-
-// Same solve with one warp per row for short, wide problems: lane l holds
-// x[j] for j = l and l + 32; column j's inner product is split across lanes
-// and combined with a fixed shuffle tree, so a row costs ~nb shuffle rounds
-// instead of an nb^2/2-long dependent DFMA chain on one thread.
-__global__ void __launch_bounds__(256) trsm_warp_kernel(i64 rows, int nb, View R, View X, int unit) {
-    __shared__ double Rs[NBD][NBD + 1];
     for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
         const int t = e % NBD, j = e / NBD;
-        double v = 0.0;
-        if (t < nb && j < nb && t <= j) v = (t == j && unit) ? 1.0 : *R.at(t, j);
-        Rs[t][j] = v;
+        Rs[t][j] = (t < j && j < nb) ? *R.at(t, j) * dinv[t] : 0.0;
     }
     __syncthreads();
+}
+
+// One warp per row: lane l holds columns l and l + 32; step j broadcasts y_j
+// from its lane and the lanes of the later columns apply it (right-looking),
+// so a row costs nb shuffle+FMA steps.  Rows are strided over a grid of at
+// most a few CTAs per SM.  (Measured against one thread per row with the row
+// in registers: faster at every height, as the warp form keeps many more
+// warps in flight per SM.)
+constexpr int kTrsmWarps = 4;
+__global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp_kernel(i64 rows, int nb, View R, View X, int unit) {
+    __shared__ double Rs[NBD][NBD + 1];
+    __shared__ double dinv[NBD];
+    load_unit_triangle(nb, R, unit, Rs, dinv);
     const int lane = threadIdx.x & 31;
-    const i64 i = (i64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (i >= rows) return;
-    double x0 = (lane < nb) ? *X.at(i, lane) : 0.0;
-    double x1 = (lane + 32 < nb) ? *X.at(i, lane + 32) : 0.0;
-    for (int j = 0; j < nb; ++j) {
-        double p = 0.0;
-        if (lane < j) p = x0 * Rs[lane][j];
-        if (lane + 32 < j) p = fma(x1, Rs[lane + 32][j], p);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-        if (j < 32) {
-            if (lane == j) x0 = unit ? (x0 - p) : (x0 - p) / Rs[j][j];
-        } else {
-            if (lane == j - 32) x1 = unit ? (x1 - p) : (x1 - p) / Rs[j][j];
+    const i64 stride = (i64)gridDim.x * kTrsmWarps;
+    for (i64 i = (i64)blockIdx.x * kTrsmWarps + (threadIdx.x >> 5); i < rows; i += stride) {
+        double x0 = (lane < nb) ? *X.at(i, lane) : 0.0;
+        double x1 = (lane + 32 < nb) ? *X.at(i, lane + 32) : 0.0;
+        const int n0 = nb < 32 ? nb : 32;
+        for (int j = 0; j < n0; ++j) {
+            const double y = __shfl_sync(0xffffffffu, x0, j);
+            if (lane > j) x0 = fma(-y, Rs[j][lane], x0);
+            x1 = fma(-y, Rs[j][lane + 32], x1);
         }
+        for (int j = 32; j < nb; ++j) {
+            const double y = __shfl_sync(0xffffffffu, x1, j - 32);
+            if (lane + 32 > j) x1 = fma(-y, Rs[j][lane + 32], x1);
+        }
+        if (lane < nb) *X.at(i, lane) = x0 * dinv[lane];
+        if (lane + 32 < nb) *X.at(i, lane + 32) = x1 * dinv[lane + 32];
     }
-    if (lane < nb) *X.at(i, lane) = x0;
-    if (lane + 32 < nb) *X.at(i, lane + 32) = x1;
 }
 
 // Upper Cholesky of one nb x nb diagonal block in place (G = R^T R), reading
@@ -200,13 +184,9 @@ int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit) {
     if (rows <= 0 || k <= 0) return 0;
     for (i64 jb = 0; jb < k; jb += NBD) {
         const int nb = (int)imin(NBD, k - jb);
-        if (rows <= 4096) {
-            trsm_warp_kernel<<<(unsigned)cdiv(rows, 8), 256, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb),
+        const i64 grid = imin(cdiv(rows, kTrsmWarps), 6LL * c.dev.sms);
+        trsm_warp_kernel<<<(unsigned)grid, 32 * kTrsmWarps, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb),
                                                                          unit ? 1 : 0);
-        } else {
-            trsm_small_kernel<NBD><<<(unsigned)cdiv(rows, 64), 64, 0, c.stream>>>(rows, nb, R.sub(jb, jb),
-                                                                                X.sub(0, jb), unit ? 1 : 0);
-        }
         BQ_LAUNCH_CHECK();
         if (jb + nb < k) {
             // X(:, jb+nb:k) -= X(:, jb:jb+nb) * R(jb:jb+nb, jb+nb:k)

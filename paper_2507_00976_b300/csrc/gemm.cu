@@ -31,6 +31,7 @@ struct GemmArgs {
     i64 kchunk;        // K range per split
     double* partial;   // non-null when gridDim.z > 1
     uint64_t seed;     // sketch generator
+    int a_upper;       // op(A) upper triangular: row tile m0 reads K >= m0 only
 };
 
 // AMODE: 0 = load A, 1 = load A^T, 2 = generate the dense +-1 sketch S (M x K).
@@ -43,8 +44,9 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(GemmArgs p) {
     const int tx = tid & 15, ty = tid >> 4;
     const i64 m0 = (i64)blockIdx.x * BM;
     const i64 n0 = (i64)blockIdx.y * BN;
-    const i64 kbeg = (i64)blockIdx.z * p.kchunk;
-    const i64 kend = (kbeg + p.kchunk < p.K) ? kbeg + p.kchunk : p.K;
+    const i64 kz = (i64)blockIdx.z * p.kchunk;
+    const i64 kend = (kz + p.kchunk < p.K) ? kz + p.kchunk : p.K;
+    const i64 kbeg = (p.a_upper && m0 > kz) ? m0 : kz;   // m0 is a multiple of BK
 
     double ra[4], rb[4];
     double acc[4][4];
@@ -203,11 +205,12 @@ int launch(const Ctx& c, GemmArgs a) {
 }  // namespace
 
 int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
-          const double* B, i64 ldb, double beta, double* C, i64 ldc) {
+          const double* B, i64 ldb, double beta, double* C, i64 ldc, bool a_upper) {
     if (M <= 0 || N <= 0) return 0;
     GemmArgs a{};
     a.M = M; a.N = N; a.K = K < 0 ? 0 : K; a.alpha = alpha; a.beta = beta;
     a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+    a.a_upper = a_upper ? 1 : 0;
     if (a.K == 0) {
         // C = beta*C: run the kernel with an empty K range (writes alpha*0 + beta*C)
         a.kchunk = BK;

@@ -38,16 +38,63 @@ struct Best {
     i64 t;
 };
 
+// ---------------------------------------------------------------------------
+// LU panel.  X(t, c) = Sk[c + t*ldsk]; panel = X rows [jb, N), columns
+// [jb, jb+pw); steps pivot steps.  CTA g owns rows [jb + g*R, jb + (g+1)*R).
+//
+// Pivot exchange without a grid barrier: for every step each CTA publishes
+// one slot {|candidate| bits, candidate row}, both words all-ones until
+// published, and the candidate row itself; every CTA polls the G slots of the
+// step, picks the winner (largest value, then smallest row) and fetches the
+// winner's row.  Slots and rows are triple-buffered by step: once a CTA has
+// seen every slot of step j, all CTAs have finished reading step j-1's
+// buffer, so the CTA resets its own slot there for step j+2 (the reset is
+// ordered before its next publication, which readers of step j+2 have seen).
+//
+// Lookahead: after the interchange of step j a CTA computes the multipliers,
+// updates only column j+1 (the next pivot column), publishes its step-(j+1)
+// candidate and the current row j+1 (their other columns updated on the fly),
+// and only then runs the bulk update of columns j+2.. while the other CTAs'
+// slots arrive.  The arithmetic per element is the unblocked GETRF step
+// (divide by the pivot, one FMA per entry), in the same order.
+struct LuArgs {
+    i64 N, jb, ldsk;
+    int pw, steps, R, Rp;
+    double* Sk;
+    i64* ipiv;
+    DevStatus* st;
+    unsigned long long* slot;   // [3][G][2], all-ones before the launch
+    double* cand_row;           // [3][G][pw]
+    double* cur_row;            // [3][pw]
+};
+
+constexpr unsigned long long kSlotEmpty = ~0ull;
+constexpr long long kNoRow = LLONG_MAX;
+constexpr unsigned long long kPollLimit = 1ull << 22;   // slot polls of ~1 us: a few seconds
+
+__device__ inline unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// First-maximum rule: the larger value wins, equal values go to the smaller
+// row; t == kNoRow marks "no candidate".  A NaN never beats a held candidate
+// (the sketch's non-finite check reports such input).
 __device__ inline Best better(Best a, Best b) {
-    if (b.v > a.v) return b;
-    if (b.v == a.v && b.t < a.t && b.t >= 0) return b;
-    if (a.t < 0) return b;
+    if (b.t == kNoRow) return a;
+    if (a.t == kNoRow) return b;
+    if (b.v > a.v || (b.v == a.v && b.t < a.t)) return b;
     return a;
 }
 
-__device__ Best block_best(Best x) {
-    __shared__ double sv[NT / 32];
-    __shared__ long long st[NT / 32];
+// Block-wide first maximum; every thread returns the same result.  wv/wt hold
+// one entry per warp and are rewritten only after a later __syncthreads.
+__device__ inline Best block_best_all(Best x, double* wv, long long* wt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -56,128 +103,183 @@ __device__ Best block_best(Best x) {
         y.t = __shfl_down_sync(0xffffffffu, x.t, o);
         x = better(x, y);
     }
-    if (lane == 0) { sv[w] = x.v; st[w] = x.t; }
+    if (lane == 0) { wv[w] = x.v; wt[w] = x.t; }
     __syncthreads();
-    if (w == 0) {
-        x.v = lane < NT / 32 ? sv[lane] : -1.0;
-        x.t = lane < NT / 32 ? st[lane] : -1;
+    Best r{wv[0], wt[0]};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Best y;
-            y.v = __shfl_down_sync(0xffffffffu, x.v, o);
-            y.t = __shfl_down_sync(0xffffffffu, x.t, o);
-            x = better(x, y);
-        }
-        if (lane == 0) { sv[0] = x.v; st[0] = x.t; }
-    }
-    __syncthreads();
-    Best r{sv[0], st[0]};
-    __syncthreads();
+    for (int q = 1; q < NT / 32; ++q) r = better(r, Best{wv[q], wt[q]});
     return r;
 }
 
-// ---------------------------------------------------------------------------
-// LU panel.  X(t, c) = Sk[c + t*ldsk]; panel = X rows [jb, N), columns
-// [jb, jb+pw); steps pivot steps.  CTA g owns rows [jb + g*R, jb + (g+1)*R).
-struct LuArgs {
-    i64 N, jb, ldsk;
-    int pw, steps, R, Rp;
-    double* Sk;
-    i64* ipiv;
-    DevStatus* st;
-    double* cand_v;    // [2][G]
-    double* cand_t;    // [2][G]
-    double* cand_row;  // [2][G][pw]
-    double* cur_row;   // [2][pw]
-};
-
 __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
     extern __shared__ double slab[];          // [pw][Rp]
-    __shared__ double prow[64], crow[64];
+    __shared__ double prow[64];
+    __shared__ double wv[NT / 32];
+    __shared__ long long wt[NT / 32];
     __shared__ long long s_p;
+    __shared__ int s_gw, s_ok;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const i64 t0 = a.jb + (i64)g * a.R;
     const i64 t1 = (t0 + a.R < a.N) ? t0 + a.R : a.N;
     const int nloc = t1 > t0 ? (int)(t1 - t0) : 0;
-    const int pw = a.pw;
+    const int pw = a.pw, Rp = a.Rp;
 
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
-        slab[c * a.Rp + rl] = a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
+        slab[c * Rp + rl] = a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
     }
     __syncthreads();
 
+    // Publish the candidate for pivot step k = j + 1 (j = -1: the first step).
+    // Row r's entry in column c: columns <= j+1 are current in the slab; the
+    // later ones still lack step j's update, applied here when elim is set.
+    auto publish = [&](int j, bool elim, Best b) {
+        const int k = j + 1, buf = k % 3;
+        const i64 cur = a.jb + k;
+        if (b.t != kNoRow && tid < pw) {
+            const int r = (int)(b.t - t0), c = tid;
+            const double x = slab[c * Rp + r];
+            a.cand_row[((size_t)buf * G + g) * pw + c] =
+                (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
+        }
+        if (cur >= t0 && cur < t1 && tid >= 64 && tid < 64 + pw) {
+            const int r = (int)(cur - t0), c = tid - 64;
+            const double x = slab[c * Rp + r];
+            a.cur_row[(size_t)buf * pw + c] = (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (j >= 0) {
+                unsigned long long* old = a.slot + ((size_t)((j + 2) % 3) * G + g) * 2;
+                st_relaxed_u64(old, kSlotEmpty);
+                st_relaxed_u64(old + 1, kSlotEmpty);
+            }
+            __threadfence();
+            unsigned long long* s = a.slot + ((size_t)buf * G + g) * 2;
+            st_relaxed_u64(s, (unsigned long long)__double_as_longlong(b.v));
+            st_relaxed_u64(s + 1, (unsigned long long)b.t);
+        }
+    };
+
+    {   // step 0 candidate: first maximum of |X(t, jb)| over the owned rows
+        Best b{-1.0, kNoRow};
+        for (int rl = tid; rl < nloc; rl += NT) {
+            const double v = fabs(slab[rl]);
+            if (b.t == kNoRow || v > b.v) { b.v = v; b.t = t0 + rl; }
+        }
+        b = block_best_all(b, wv, wt);
+        publish(-1, false, b);
+    }
+
     for (int j = 0; j < a.steps; ++j) {
         const i64 jg = a.jb + j;
-        const int par = j & 1;
-        // (1) local first-maximum of |X(t, jg)| over owned rows t >= jg
-        Best b{-1.0, -1};
-        const int rl0 = (jg > t0) ? (int)(jg - t0) : 0;
-        for (int rl = rl0 + tid; rl < nloc; rl += NT) {
-            const double v = fabs(slab[j * a.Rp + rl]);
-            if (v > b.v) { b.v = v; b.t = t0 + rl; }
-        }
-        b = block_best(b);
-        // (2) publish candidate, its row, and (owner) the current row jg
-        if (tid == 0) {
-            a.cand_v[par * G + g] = b.v;
-            a.cand_t[par * G + g] = (double)b.t;
-        }
-        if (b.t >= 0)
-            for (int c = tid; c < pw; c += NT) a.cand_row[((size_t)par * G + g) * pw + c] = slab[c * a.Rp + (b.t - t0)];
-        if (jg >= t0 && jg < t1)
-            for (int c = tid; c < pw; c += NT) a.cur_row[par * pw + c] = slab[c * a.Rp + (jg - t0)];
-        // (3)
-        if (!grid_barrier(a.st, G)) return;
-        // (4) winner over all CTAs (fixed rule: largest value, then smallest index)
+        const bool has_next = j + 1 < a.steps;
+        // (1) wait for the G slots of step j; winner = largest value, then smallest row
         if (tid < 32) {
-            Best w{-1.0, -1};
-#pragma unroll 5
-            for (int q = tid; q < G; q += 32) {
-                Best y{__ldcg(&a.cand_v[par * G + q]), (i64)__ldcg(&a.cand_t[par * G + q])};
-                if (y.t >= 0) w = better(w, y);
+            const unsigned long long* sl = a.slot + (size_t)(j % 3) * G * 2;
+            Best w{-1.0, kNoRow};
+            int wq = -1, ok = 1;
+            unsigned long long polls = 0;
+            for (;;) {
+                bool all = true;
+                w = Best{-1.0, kNoRow};
+                wq = -1;
+                for (int q = tid; q < G; q += 32) {
+                    const unsigned long long vb = ld_relaxed_u64(sl + 2 * q), tb = ld_relaxed_u64(sl + 2 * q + 1);
+                    if (vb == kSlotEmpty || tb == kSlotEmpty) { all = false; continue; }
+                    const Best y{__longlong_as_double((long long)vb), (i64)tb};
+                    const Best z = better(w, y);
+                    if (z.t != w.t) { w = z; wq = q; }
+                }
+                if (__all_sync(0xffffffffu, all)) break;
+                // warp-uniform exit: the poll count is the same in every lane and the
+                // error flag is voted on
+                ++polls;
+                if (polls > kPollLimit ||
+                    ((polls & 1023) == 0 &&
+                     __any_sync(0xffffffffu, *((volatile int*)&a.st->err_timeout) != 0))) {
+                    ok = 0;
+                    break;
+                }
             }
+            // acquire side of the slots' publication: each lane fences after its own polls
+            __threadfence();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                Best y;
-                y.v = __shfl_down_sync(0xffffffffu, w.v, o);
-                y.t = __shfl_down_sync(0xffffffffu, w.t, o);
-                w = better(w, y);
+                const Best y{__shfl_down_sync(0xffffffffu, w.v, o), (i64)__shfl_down_sync(0xffffffffu, (long long)w.t, o)};
+                const int yq = __shfl_down_sync(0xffffffffu, wq, o);
+                const Best z = better(w, y);
+                if (z.t != w.t) { w = z; wq = yq; }
             }
-            if (tid == 0) s_p = w.t;
+            if (tid == 0) {
+                if (!ok || wq < 0) atomicExch(&a.st->err_timeout, 1);
+                s_ok = ok && wq >= 0;
+                s_p = w.t;
+                s_gw = wq;
+                if (g == 0 && s_ok) a.ipiv[jg] = w.t;
+            }
         }
         __syncthreads();
+        if (!s_ok) return;
         const i64 p = s_p;
-        // locate the winning CTA from the row index
-        const int gw = (int)((p - a.jb) / a.R);
-        // (5)
-        for (int c = tid; c < pw; c += NT) {
-            prow[c] = __ldcg(&a.cand_row[((size_t)par * G + gw) * pw + c]);
-            crow[c] = __ldcg(&a.cur_row[par * pw + c]);
+        const int gw = s_gw, buf = j % 3;
+        // (2) pivot row into prow and the slab; current row jg to the winner's place
+        if (tid < pw) {
+            const double pr = __ldcg(&a.cand_row[((size_t)buf * G + gw) * pw + tid]);
+            prow[tid] = pr;
+            if (jg >= t0 && jg < t1) slab[tid * Rp + (jg - t0)] = pr;
+            if (p != jg && p >= t0 && p < t1) slab[tid * Rp + (p - t0)] = __ldcg(&a.cur_row[(size_t)buf * pw + tid]);
         }
         __syncthreads();
-        // (6) row interchange jg <-> p
-        if (jg >= t0 && jg < t1)
-            for (int c = tid; c < pw; c += NT) slab[c * a.Rp + (jg - t0)] = prow[c];
-        if (p != jg && p >= t0 && p < t1)
-            for (int c = tid; c < pw; c += NT) slab[c * a.Rp + (p - t0)] = crow[c];
-        __syncthreads();
-        // (7) elimination below the pivot (skipped on an exact zero pivot, as GETRF)
+        // (3) multipliers and column j+1 of the owned rows below jg; next candidate
         const double piv = prow[j];
-        if (piv != 0.0) {
-            const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
-            for (int rl = r0 + tid; rl < nloc; rl += NT) {
-                const double l = slab[j * a.Rp + rl] / piv;
-                slab[j * a.Rp + rl] = l;
-                for (int c = j + 1; c < pw; ++c) slab[c * a.Rp + rl] = fma(-l, prow[c], slab[c * a.Rp + rl]);
+        const bool elim = piv != 0.0;   // exact zero pivot: no elimination, as GETRF
+        const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
+        Best b{-1.0, kNoRow};
+        for (int rl = r0 + tid; rl < nloc; rl += NT) {
+            double l = 0.0;
+            if (elim) {
+                l = slab[j * Rp + rl] / piv;
+                slab[j * Rp + rl] = l;
+            }
+            if (has_next) {
+                double x = slab[(j + 1) * Rp + rl];
+                if (elim) {
+                    x = fma(-l, prow[j + 1], x);
+                    slab[(j + 1) * Rp + rl] = x;
+                }
+                const double v = fabs(x);
+                if (b.t == kNoRow || v > b.v) { b.v = v; b.t = t0 + rl; }
             }
         }
-        if (g == 0 && tid == 0) a.ipiv[jg] = p;
+        if (has_next) {
+            b = block_best_all(b, wv, wt);
+            publish(j, elim, b);
+        } else {
+            __syncthreads();
+        }
+        // (4) bulk update of columns cs.. of the owned rows below jg
+        const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
+        if (elim && nr > 0 && cs < pw) {
+            if (nr >= NT) {
+                for (int rl = r0 + tid; rl < nloc; rl += NT) {
+                    const double l = slab[j * Rp + rl];
+                    for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
+                }
+            } else {
+                const int ng = NT / nr, grp = tid / nr;
+                if (grp < ng) {
+                    const int rl = r0 + tid - grp * nr;
+                    const double l = slab[j * Rp + rl];
+                    for (int c = cs + grp; c < pw; c += ng) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
+                }
+            }
+        }
         __syncthreads();
     }
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
-        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * a.Rp + rl];
+        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * Rp + rl];
     }
 }
 
@@ -567,9 +669,9 @@ int coop_grid(const void* kernel, size_t smem, const Ctx& c, int want) {
 }  // namespace
 
 int coop_scratch_elems(i64 nb, int grid, size_t* elems) {
-    // LU: 2G (vals) + 2G (idx) + 2*G*nb + 2*nb ; HH: G + 1 + G*nb + G*nb*nb + nb*nb
+    // LU: 6G (slots) + 3*G*nb (candidate rows) + 3*nb (current rows); HH: G + 1 + G*nb + G*nb*nb + nb*nb
     const size_t G = (size_t)grid;
-    const size_t lu = 4 * G + 2 * G * nb + 2 * nb;
+    const size_t lu = 6 * G + 3 * G * nb + 3 * nb;
     const size_t hh = G + 8 + G * nb + G * nb * nb + nb * nb;
     *elems = (lu > hh ? lu : hh) + 64;
     return 0;
@@ -634,10 +736,11 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
         LuArgs a{};
         a.N = N; a.jb = jb; a.ldsk = ldsk; a.pw = pw; a.steps = st; a.R = (int)R; a.Rp = (int)(R | 1);
         a.Sk = Sk; a.ipiv = ipiv; a.st = c.st;
-        a.cand_v = c.coop;
-        a.cand_t = c.coop + 2 * G;
-        a.cand_row = c.coop + 4 * G;
-        a.cur_row = c.coop + 4 * G + 2 * (size_t)G * pw;
+        a.slot = reinterpret_cast<unsigned long long*>(c.coop);
+        a.cand_row = c.coop + 6 * (size_t)G;
+        a.cur_row = c.coop + 6 * (size_t)G + 3 * (size_t)G * pw;
+        // every slot starts unpublished (all-ones) in each launch
+        BQ_CUDA(cudaMemsetAsync(a.slot, 0xff, 6 * (size_t)G * sizeof(unsigned long long), c.stream));
         BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));
         const i64 below = d - (jb + pw);
         if (d - pw > 0) {
@@ -934,7 +1037,7 @@ int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 
         BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
         BQ_TRY(set_zero_below(c, s, s, Ub, d));
     }
-    BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk));
+    BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk, /*a_upper=*/true));
     if (s < d) {
         zero_rows_kernel<<<blocks, 256, 0, c.stream>>>(s, d, N, Sk, ldsk);
         BQ_LAUNCH_CHECK();
