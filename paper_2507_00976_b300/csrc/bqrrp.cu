@@ -356,7 +356,7 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
     View Yv = colmajor(Y, ldy);
     BQ_TRY(copy_mat(c, rows, k, Mp, ldm, Y, ldy));
     BQ_TRY(trsm_ru(c, rows, k, colmajor(Rsk, ldr), Yv, false));                       // Pre = M Rsk11^-1
-    BQ_TRY(dgemm(c, true, false, k, k, rows, 1.0, Y, ldy, Y, ldy, 0.0, G, ldb));       // G = Pre^T Pre
+    BQ_TRY(dgemm(c, true, false, k, k, rows, 1.0, Y, ldy, Y, ldy, 0.0, G, ldb, kGemmCUpper));   // G = Pre^T Pre
     BQ_CUDA(cudaMemsetAsync(&c.st->potrf_info, 0x7f, sizeof(int), c.stream));         // "no failure"
     BQ_TRY(potrf_u(c, k, G, ldb));                                                     // Rchol
     DevStatus hs{};

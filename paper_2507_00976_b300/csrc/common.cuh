@@ -213,15 +213,18 @@ struct Ctx {
 };
 
 // gemm.cu
-// a_upper: op(A) is upper triangular (M == K), so output rows [m0, m0+64)
-// only take K >= m0 and the K range below the diagonal is skipped.
+// Structure flags of dgemm/pgemm.  kGemmAUpper: op(A) is upper triangular
+// (M == K), so output rows [m0, m0+64) only take K >= m0.  kGemmCUpper: only
+// the upper triangle of C is wanted (M == N); output tiles strictly below the
+// diagonal are written as beta*C (zero when beta == 0) without a K loop.
+constexpr int kGemmAUpper = 1, kGemmCUpper = 2;
 int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
-          const double* B, i64 ldb, double beta, double* C, i64 ldc, bool a_upper = false);
+          const double* B, i64 ldb, double beta, double* C, i64 ldc, int flags = 0);
 int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, double beta, View C);
 // FP64-accurate product: the tensor-core slice GEMM when c.mixed and the
 // problem is large enough (and its workspace fits), else the FP64 SIMT GEMM.
 int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
-          const double* B, i64 ldb, double beta, double* C, i64 ldc, bool a_upper = false);
+          const double* B, i64 ldb, double beta, double* C, i64 ldc, int flags = 0);
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,
                       i64 ldsk);
 

@@ -31,7 +31,7 @@ struct GemmArgs {
     i64 kchunk;        // K range per split
     double* partial;   // non-null when gridDim.z > 1
     uint64_t seed;     // sketch generator
-    int a_upper;       // op(A) upper triangular: row tile m0 reads K >= m0 only
+    int flags;         // kGemmAUpper / kGemmCUpper
 };
 
 // AMODE: 0 = load A, 1 = load A^T, 2 = generate the dense +-1 sketch S (M x K).
@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(GemmArgs p) {
     const i64 m0 = (i64)blockIdx.x * BM;
     const i64 n0 = (i64)blockIdx.y * BN;
     const i64 kz = (i64)blockIdx.z * p.kchunk;
-    const i64 kend = (kz + p.kchunk < p.K) ? kz + p.kchunk : p.K;
-    const i64 kbeg = (p.a_upper && m0 > kz) ? m0 : kz;   // m0 is a multiple of BK
+    const i64 kend = ((p.flags & kGemmCUpper) && m0 >= n0 + BN) ? kz            // tile below the diagonal
+                     : (kz + p.kchunk < p.K) ? kz + p.kchunk : p.K;
+    const i64 kbeg = ((p.flags & kGemmAUpper) && m0 > kz) ? m0 : kz;   // m0 is a multiple of BK
 
     double ra[4], rb[4];
     double acc[4][4];
@@ -174,13 +175,15 @@ int launch(const Ctx& c, GemmArgs a) {
         set_error("dgemm: grid too large (%lld x %lld tiles)", (long long)tm, (long long)tn);
         return BQRRP_EUNSUPPORTED;
     }
-    // split-K when the output tiles cannot fill the GPU and K is long
+    // split-K when the output tiles cannot fill the GPU: one 64x64 tile with
+    // K = 64 is ~65 us of FP64 work on a single SM, so even short K ranges
+    // are split, down to one 16-deep slab per CTA
     int splits = 1;
     const i64 tiles = tm * tn;
     const i64 target = 4LL * c.dev.sms;
-    if (tiles < target && a.K >= 128 && c.splitk != nullptr) {
+    if (tiles < target && a.K >= 2 * BK && c.splitk != nullptr) {
         i64 s = cdiv(target, tiles);
-        s = imin(s, a.K / 64);
+        s = imin(s, a.K / BK);
         s = imin(s, 64);
         const i64 fit = (i64)(c.splitk_elems / (size_t)(a.M * a.N));
         s = imin(s, fit);
@@ -205,12 +208,12 @@ int launch(const Ctx& c, GemmArgs a) {
 }  // namespace
 
 int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
-          const double* B, i64 ldb, double beta, double* C, i64 ldc, bool a_upper) {
+          const double* B, i64 ldb, double beta, double* C, i64 ldc, int flags) {
     if (M <= 0 || N <= 0) return 0;
     GemmArgs a{};
     a.M = M; a.N = N; a.K = K < 0 ? 0 : K; a.alpha = alpha; a.beta = beta;
     a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
-    a.a_upper = a_upper ? 1 : 0;
+    a.flags = flags;
     if (a.K == 0) {
         // C = beta*C: run the kernel with an empty K range (writes alpha*0 + beta*C)
         a.kchunk = BK;

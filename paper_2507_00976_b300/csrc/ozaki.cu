@@ -381,11 +381,11 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
 }
 
 int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
-          const double* B, i64 ldb, double beta, double* C, i64 ldc, bool a_upper) {
+          const double* B, i64 ldb, double beta, double* C, i64 ldc, int flags) {
     if (c.mixed && c.oz_ws && M > 0 && N > 0 && K >= 32 && (double)M * N * K >= 16.0 * 1024 * 1024 &&
         ozaki_ws_bytes(M, N, K, kSlices) <= c.oz_bytes)
         return ozaki_gemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.oz_ws, c.oz_bytes);
-    return dgemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, a_upper);
+    return dgemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
 }
 
 // Msk = S A with the dense +-1 operator S (d x m) as one exact slice:

@@ -33,19 +33,15 @@ constexpr int NT = 256;
 constexpr int kMaxSmemLu = 210 * 1024;   // dynamic part; static use is ~2 KB
 constexpr int kMaxSmemHh = 185 * 1024;   // dynamic part; static use is ~35 KB
 
-struct Best {
-    double v;
-    i64 t;
-};
 
 // ---------------------------------------------------------------------------
 // LU panel.  X(t, c) = Sk[c + t*ldsk]; panel = X rows [jb, N), columns
 // [jb, jb+pw); steps pivot steps.  CTA g owns rows [jb + g*R, jb + (g+1)*R).
 //
 // Pivot exchange without a grid barrier: for every step each CTA publishes
-// one slot {|candidate| bits, candidate row}, both words all-ones until
+// one slot {candidate value bits, candidate row}, both words all-ones until
 // published, and the candidate row itself; every CTA polls the G slots of the
-// step, picks the winner (largest value, then smallest row) and fetches the
+// step, picks the winner (largest |value|, then smallest row) and fetches the
 // winner's row.  Slots and rows are triple-buffered by step: once a CTA has
 // seen every slot of step j, all CTAs have finished reading step j-1's
 // buffer, so the CTA resets its own slot there for step j+2 (the reset is
@@ -55,8 +51,14 @@ struct Best {
 // updates only column j+1 (the next pivot column), publishes its step-(j+1)
 // candidate and the current row j+1 (their other columns updated on the fly),
 // and only then runs the bulk update of columns j+2.. while the other CTAs'
-// slots arrive.  The arithmetic per element is the unblocked GETRF step
-// (divide by the pivot, one FMA per entry), in the same order.
+// slots arrive.
+//
+// Cost model on B300: every FP64 instruction holds its SM sub-partition's
+// FP64 unit for ~64 cycles whatever the number of active lanes, and a
+// division ~640.  The search therefore compares |x| as integers (the bit
+// patterns of non-negative doubles order like their values), and the
+// multipliers use one reciprocal of the pivot, formed by a single warp while
+// the pivot row is in flight: l = x * (1/piv) (within an ulp of GETRF's x/piv).
 struct LuArgs {
     i64 N, jb, ldsk;
     int pw, steps, R, Rp;
@@ -69,6 +71,7 @@ struct LuArgs {
 };
 
 constexpr unsigned long long kSlotEmpty = ~0ull;
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr long long kNoRow = LLONG_MAX;
 constexpr unsigned long long kPollLimit = 1ull << 22;   // slot polls of ~1 us: a few seconds
 
@@ -82,41 +85,47 @@ __device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long 
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// First-maximum rule: the larger value wins, equal values go to the smaller
-// row; t == kNoRow marks "no candidate".  A NaN never beats a held candidate
-// (the sketch's non-finite check reports such input).
-__device__ inline Best better(Best a, Best b) {
-    if (b.t == kNoRow) return a;
-    if (a.t == kNoRow) return b;
-    if (b.v > a.v || (b.v == a.v && b.t < a.t)) return b;
-    return a;
+// A pivot candidate: key = bits of |x|, row t.  "No candidate" is {0, kNoRow},
+// which loses to every row.  (A NaN's key exceeds every finite one; the
+// sketch's non-finite check reports such input.)
+struct Cand {
+    unsigned long long key;
+    long long t;
+};
+
+__device__ inline unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & kAbsMask;
 }
 
-// Block-wide first maximum; every thread returns the same result.  wv/wt hold
+// First-maximum rule: the larger |x| wins, equal values go to the smaller row.
+__device__ inline Cand better(Cand a, Cand b) { return (b.key > a.key || (b.key == a.key && b.t < a.t)) ? b : a; }
+
+__device__ inline Cand shfl_down_cand(Cand x, int o) {
+    return Cand{__shfl_down_sync(0xffffffffu, x.key, o), __shfl_down_sync(0xffffffffu, x.t, o)};
+}
+
+// Block-wide first maximum; every thread returns the same result.  wk/wt hold
 // one entry per warp and are rewritten only after a later __syncthreads.
-__device__ inline Best block_best_all(Best x, double* wv, long long* wt) {
+__device__ inline Cand block_best_all(Cand x, unsigned long long* wk, long long* wt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Best y;
-        y.v = __shfl_down_sync(0xffffffffu, x.v, o);
-        y.t = __shfl_down_sync(0xffffffffu, x.t, o);
-        x = better(x, y);
-    }
-    if (lane == 0) { wv[w] = x.v; wt[w] = x.t; }
+    for (int o = 16; o > 0; o >>= 1) x = better(x, shfl_down_cand(x, o));
+    if (lane == 0) { wk[w] = x.key; wt[w] = x.t; }
     __syncthreads();
-    Best r{wv[0], wt[0]};
+    Cand r{wk[0], wt[0]};
 #pragma unroll
-    for (int q = 1; q < NT / 32; ++q) r = better(r, Best{wv[q], wt[q]});
+    for (int q = 1; q < NT / 32; ++q) r = better(r, Cand{wk[q], wt[q]});
     return r;
 }
 
 __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
     extern __shared__ double slab[];          // [pw][Rp]
     __shared__ double prow[64];
-    __shared__ double wv[NT / 32];
+    __shared__ unsigned long long wk[NT / 32];
     __shared__ long long wt[NT / 32];
     __shared__ long long s_p;
+    __shared__ unsigned long long s_pivbits;
+    __shared__ double s_rpiv;
     __shared__ int s_gw, s_ok;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const i64 t0 = a.jb + (i64)g * a.R;
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
     // Publish the candidate for pivot step k = j + 1 (j = -1: the first step).
     // Row r's entry in column c: columns <= j+1 are current in the slab; the
     // later ones still lack step j's update, applied here when elim is set.
-    auto publish = [&](int j, bool elim, Best b) {
+    auto publish = [&](int j, bool elim, Cand b) {
         const int k = j + 1, buf = k % 3;
         const i64 cur = a.jb + k;
         if (b.t != kNoRow && tid < pw) {
@@ -154,42 +163,42 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                 st_relaxed_u64(old, kSlotEmpty);
                 st_relaxed_u64(old + 1, kSlotEmpty);
             }
+            unsigned long long vb = 0;   // signed candidate value (+0 for "no candidate")
+            if (b.t != kNoRow) vb = (unsigned long long)__double_as_longlong(slab[k * Rp + (int)(b.t - t0)]);
+            if (vb == kSlotEmpty) vb = 0xfff8000000000000ull;   // that NaN pattern marks an empty slot
             __threadfence();
             unsigned long long* s = a.slot + ((size_t)buf * G + g) * 2;
-            st_relaxed_u64(s, (unsigned long long)__double_as_longlong(b.v));
+            st_relaxed_u64(s, vb);
             st_relaxed_u64(s + 1, (unsigned long long)b.t);
         }
     };
 
     {   // step 0 candidate: first maximum of |X(t, jb)| over the owned rows
-        Best b{-1.0, kNoRow};
-        for (int rl = tid; rl < nloc; rl += NT) {
-            const double v = fabs(slab[rl]);
-            if (b.t == kNoRow || v > b.v) { b.v = v; b.t = t0 + rl; }
-        }
-        b = block_best_all(b, wv, wt);
+        Cand b{0, kNoRow};
+        for (int rl = tid; rl < nloc; rl += NT) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
+        b = block_best_all(b, wk, wt);
         publish(-1, false, b);
     }
 
     for (int j = 0; j < a.steps; ++j) {
         const i64 jg = a.jb + j;
         const bool has_next = j + 1 < a.steps;
-        // (1) wait for the G slots of step j; winner = largest value, then smallest row
+        // (1) wait for the G slots of step j; winner = largest |value|, then smallest row
         if (tid < 32) {
             const unsigned long long* sl = a.slot + (size_t)(j % 3) * G * 2;
-            Best w{-1.0, kNoRow};
+            Cand w{0, kNoRow};
+            unsigned long long wvb = 0;
             int wq = -1, ok = 1;
             unsigned long long polls = 0;
             for (;;) {
                 bool all = true;
-                w = Best{-1.0, kNoRow};
+                w = Cand{0, kNoRow};
                 wq = -1;
                 for (int q = tid; q < G; q += 32) {
                     const unsigned long long vb = ld_relaxed_u64(sl + 2 * q), tb = ld_relaxed_u64(sl + 2 * q + 1);
                     if (vb == kSlotEmpty || tb == kSlotEmpty) { all = false; continue; }
-                    const Best y{__longlong_as_double((long long)vb), (i64)tb};
-                    const Best z = better(w, y);
-                    if (z.t != w.t) { w = z; wq = q; }
+                    const Cand z = better(w, Cand{vb & kAbsMask, (long long)tb});
+                    if (z.t != w.t) { w = z; wq = q; wvb = vb; }
                 }
                 if (__all_sync(0xffffffffu, all)) break;
                 // warp-uniform exit: the poll count is the same in every lane and the
@@ -206,16 +215,18 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
             __threadfence();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const Best y{__shfl_down_sync(0xffffffffu, w.v, o), (i64)__shfl_down_sync(0xffffffffu, (long long)w.t, o)};
+                const Cand y = shfl_down_cand(w, o);
                 const int yq = __shfl_down_sync(0xffffffffu, wq, o);
-                const Best z = better(w, y);
-                if (z.t != w.t) { w = z; wq = yq; }
+                const unsigned long long yvb = __shfl_down_sync(0xffffffffu, wvb, o);
+                const Cand z = better(w, y);
+                if (z.t != w.t) { w = z; wq = yq; wvb = yvb; }
             }
             if (tid == 0) {
                 if (!ok || wq < 0) atomicExch(&a.st->err_timeout, 1);
                 s_ok = ok && wq >= 0;
                 s_p = w.t;
                 s_gw = wq;
+                s_pivbits = wvb;
                 if (g == 0 && s_ok) a.ipiv[jg] = w.t;
             }
         }
@@ -223,23 +234,25 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         if (!s_ok) return;
         const i64 p = s_p;
         const int gw = s_gw, buf = j % 3;
-        // (2) pivot row into prow and the slab; current row jg to the winner's place
+        const bool elim = (s_pivbits & kAbsMask) != 0;   // exact zero pivot: no elimination, as GETRF
+        // (2) pivot row into prow and the slab; current row jg to the winner's
+        // place; one warp forms 1/piv meanwhile
         if (tid < pw) {
             const double pr = __ldcg(&a.cand_row[((size_t)buf * G + gw) * pw + tid]);
             prow[tid] = pr;
             if (jg >= t0 && jg < t1) slab[tid * Rp + (jg - t0)] = pr;
             if (p != jg && p >= t0 && p < t1) slab[tid * Rp + (p - t0)] = __ldcg(&a.cur_row[(size_t)buf * pw + tid]);
         }
+        if (tid == 64 && elim) s_rpiv = 1.0 / __longlong_as_double((long long)s_pivbits);
         __syncthreads();
         // (3) multipliers and column j+1 of the owned rows below jg; next candidate
-        const double piv = prow[j];
-        const bool elim = piv != 0.0;   // exact zero pivot: no elimination, as GETRF
+        const double rpiv = s_rpiv;
         const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
-        Best b{-1.0, kNoRow};
+        Cand b{0, kNoRow};
         for (int rl = r0 + tid; rl < nloc; rl += NT) {
             double l = 0.0;
             if (elim) {
-                l = slab[j * Rp + rl] / piv;
+                l = slab[j * Rp + rl] * rpiv;
                 slab[j * Rp + rl] = l;
             }
             if (has_next) {
@@ -248,12 +261,11 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                     x = fma(-l, prow[j + 1], x);
                     slab[(j + 1) * Rp + rl] = x;
                 }
-                const double v = fabs(x);
-                if (b.t == kNoRow || v > b.v) { b.v = v; b.t = t0 + rl; }
+                b = better(b, Cand{abs_key(x), t0 + rl});
             }
         }
         if (has_next) {
-            b = block_best_all(b, wv, wt);
+            b = block_best_all(b, wk, wt);
             publish(j, elim, b);
         } else {
             __syncthreads();
@@ -905,10 +917,14 @@ namespace {
 // R factor of the Householder QR (dlarfg convention) of a small d x s matrix
 // W (ld d, s <= d) held entirely in the distributed shared memory of one
 // thread-block cluster.  Column c lives in CTA c mod C at local slot c / C.
-// Step j: the owner of column j forms the reflector and publishes it in its
-// shared memory (double-buffered by step parity); after one cluster barrier
-// every CTA copies it through DSMEM and applies it to its own columns.  Only
-// R (upper triangle, zeros below) is written back to W.
+// Reflector j is published by the owner of column j in its shared memory
+// (double-buffered by step parity).  Step j: every CTA copies reflector j
+// through DSMEM and applies it to its own columns; with lookahead, warp 0 of
+// the owner of column j+1 first updates that column and forms reflector j+1
+// while the other warps update the rest, so one cluster barrier per step
+// separates the reflectors and the owner's scalar work (a square root and a
+// division, ~650 cycles each on B300's FP64 unit) leaves the critical path.
+// Only R (upper triangle, zeros below) is written back to W.
 constexpr int kSqrMaxD = 640;
 
 __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
@@ -916,7 +932,6 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     __shared__ double vbuf[2][kSqrMaxD];
     __shared__ double vloc[kSqrMaxD];
     __shared__ double s_tau[2];
-    __shared__ double red[NT / 32];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), g = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -926,63 +941,79 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
         for (i64 r = tid; r < d; r += NT) loc[(i64)lc * d + r] = W[r + gc * d];
     }
     __syncthreads();
+
+    // Reflector of column j (owned here) into vbuf[par], by one warp: v(j) = 1,
+    // v(j+1:) = x(j+1:) / (alpha - beta), tau = (beta - alpha) / beta, both
+    // from the single quotient q = 1 / (beta (alpha - beta)).  The column
+    // becomes (beta, 0, ..., 0).
+    auto reflect = [&](i64 j, int par) {
+        double* x = loc + (j / C) * d;
+        double xn2 = 0.0;
+        for (i64 r = j + 1 + lane; r < d; r += 32) xn2 = fma(x[r], x[r], xn2);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
+        const double alpha = x[j];
+        const bool nz = ((unsigned long long)__double_as_longlong(xn2) & 0x7fffffffffffffffull) != 0;
+        double tau = 0.0, beta = alpha, scal = 1.0;
+        if (nz) {
+            const long long ab = __double_as_longlong(alpha);
+            const bool apos = ab >= 0 || ab == (long long)0x8000000000000000ull;   // alpha >= 0.0
+            const double nrm = sqrt(alpha * alpha + xn2);
+            beta = apos ? -nrm : nrm;
+            const double am = alpha - beta;
+            const double q = 1.0 / (beta * am);
+            scal = beta * q;
+            tau = -(am * am) * q;
+        }
+        for (i64 r = j + 1 + lane; r < d; r += 32) {
+            const double v = nz ? x[r] * scal : x[r];
+            vbuf[par][r] = v;
+            x[r] = 0.0;                                   // below the diagonal of R
+        }
+        if (lane == 0) {
+            vbuf[par][j] = 1.0;
+            x[j] = beta;
+            s_tau[par] = tau;
+        }
+    };
+    // col -= tau v (v^T col) over rows [j, d), by one warp
+    auto apply = [&](double* col, i64 j, double tau) {
+        double dot = 0.0;
+        for (i64 r = j + lane; r < d; r += 32) dot = fma(vloc[r], col[r], dot);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+        const double w = tau * dot;
+        for (i64 r = j + lane; r < d; r += 32) col[r] = fma(-w, vloc[r], col[r]);
+    };
+
+    if (g == 0 && warp == 0) reflect(0, 0);
+    cl.sync();
     for (i64 j = 0; j < s; ++j) {
         const int o = (int)(j % C), par = (int)(j & 1);
-        if (g == o) {
-            double* x = loc + (j / C) * d;
-            double xn2 = 0.0;
-            for (i64 r = j + 1 + tid; r < d; r += NT) xn2 += x[r] * x[r];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
-            if (lane == 0) red[warp] = xn2;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int q = 0; q < NT / 32; ++q) t += red[q];
-                red[0] = t;
-            }
-            __syncthreads();
-            xn2 = red[0];
-            const double alpha = x[j];
-            double tau = 0.0, beta = alpha, scal = 1.0;
-            if (xn2 != 0.0) {
-                const double nrm = sqrt(alpha * alpha + xn2);
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
-            }
-            for (i64 r = j + 1 + tid; r < d; r += NT) {
-                const double v = (xn2 != 0.0) ? x[r] * scal : x[r];
-                vbuf[par][r] = v;
-                x[r] = 0.0;                                   // below the diagonal of R
-            }
-            if (tid == 0) {
-                vbuf[par][j] = 1.0;
-                x[j] = beta;
-                s_tau[par] = tau;
-            }
-        }
-        cl.sync();
-        // the reflector of column j, from its owner
+        // reflector j from its owner
         const double* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
-        const double* tsrc = cl.map_shared_rank(&s_tau[par], o);
         for (i64 r = j + tid; r < d; r += NT) vloc[r] = vsrc[r];
-        const double tau = *tsrc;
+        const double tau = *cl.map_shared_rank(&s_tau[par], o);
         __syncthreads();
-        if (tau != 0.0) {
-            for (int lc = warp; lc < ncl; lc += NT / 32) {
-                const i64 gc = (i64)lc * C + g;
-                if (gc <= j) continue;
-                double* col = loc + (i64)lc * d;
-                double dot = 0.0;
-                for (i64 r = j + lane; r < d; r += 32) dot += vloc[r] * col[r];
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-                const double w = tau * dot;
-                for (i64 r = j + lane; r < d; r += 32) col[r] -= w * vloc[r];
+        const bool live = ((unsigned long long)__double_as_longlong(tau) & 0x7fffffffffffffffull) != 0;
+        const bool next_here = j + 1 < s && (int)((j + 1) % C) == g;
+        if (next_here && warp == 0) {
+            // lookahead: column j+1 first, then its reflector
+            if (live) apply(loc + ((j + 1) / C) * d, j, tau);
+            __syncwarp();
+            reflect(j + 1, par ^ 1);
+        }
+        if (live) {
+            const int w0 = next_here ? 1 : 0, nw = NT / 32 - w0;
+            if (warp >= w0) {
+                for (int lc = warp - w0; lc < ncl; lc += nw) {
+                    const i64 gc = (i64)lc * C + g;
+                    if (gc <= j || (next_here && gc == j + 1)) continue;
+                    apply(loc + (i64)lc * d, j, tau);
+                }
             }
         }
-        __syncthreads();
+        cl.sync();   // reflector j+1 published; reflector j no longer read
     }
     for (int lc = 0; lc < ncl; ++lc) {
         const i64 gc = (i64)lc * C + g;
@@ -1037,7 +1068,7 @@ int rsk_from_lu(const Ctx& c, i64 d, i64 N, double* X, i64 ldx, double* Sk, i64 
         BQ_TRY(geqrf_blocked(c, d, s, Ub, d, tau, V, T, W, W2, 64));
         BQ_TRY(set_zero_below(c, s, s, Ub, d));
     }
-    BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk, /*a_upper=*/true));
+    BQ_TRY(pgemm(c, false, false, s, N, s, 1.0, Ub, d, X, ldx, 0.0, Sk, ldsk, kGemmAUpper));
     if (s < d) {
         zero_rows_kernel<<<blocks, 256, 0, c.stream>>>(s, d, N, Sk, ldsk);
         BQ_LAUNCH_CHECK();
