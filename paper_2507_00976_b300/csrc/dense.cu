@@ -66,12 +66,33 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp_kernel(i64 rows, in
     }
 }
 
+// Element e of the upper triangle (c1 <= c2) of a w x w block, folded so
+// that rows i and w-1-i share one row of length w+1: consecutive e cover
+// consecutive c2, and no lane is masked off in the middle of the range.
+__device__ inline bool upper_pair(int e, int w, int* c1, int* c2) {
+    const int i = e / (w + 1), k = e - i * (w + 1);
+    if (k < w - i) { *c1 = i; *c2 = i + k; return true; }
+    const int i2 = w - 1 - i;
+    if (i2 == i) return false;   // middle row of an odd w: already covered
+    *c1 = i2;
+    *c2 = i2 + (k - (w - i));
+    return true;
+}
+
 // Upper Cholesky of one nb x nb diagonal block in place (G = R^T R), reading
 // and writing only the upper triangle; zeroes the strict lower triangle.  A
 // non-positive or non-finite pivot at local column j records jg0 + j in
 // st->potrf_info (atomicMin) and stops.
+//
+// B300 cost model: an FP64 instruction holds an SM sub-partition's FP64 unit
+// for ~64 cycles whatever the active lanes, a square root or a division
+// ~650.  So the pivot test is an integer test on the bits, r_jj = d_jj *
+// rsqrt(d_jj) and the row is scaled by that reciprocal (one special function
+// per step instead of a square root plus a division), and the symmetric
+// update touches only the upper triangle through the folded enumeration.
 __global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* G, i64 ldg, int jg0, DevStatus* st) {
     __shared__ double A[NBD][NBD + 1];
+    __shared__ double s_rinv;
     __shared__ int fail;
     for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
         const int i = e % NBD, j = e / NBD;
@@ -80,30 +101,35 @@ __global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* G, i64
     if (threadIdx.x == 0) fail = (st->potrf_info < jg0) ? 1 : 0;   // an earlier block failed
     __syncthreads();
     if (fail) return;
-    int done = nb;
     for (int j = 0; j < nb; ++j) {
         if (threadIdx.x == 0) {
             const double dj = A[j][j];
-            if (!(dj > 0.0) || !isfinite(dj)) {
+            const long long bits = __double_as_longlong(dj);
+            if (!(bits > 0 && bits < 0x7ff0000000000000ll)) {   // not (finite and > 0)
                 fail = 1;
                 atomicMin(&st->potrf_info, jg0 + j);
             } else {
-                A[j][j] = sqrt(dj);
+                const double ri = rsqrt(dj);
+                A[j][j] = dj * ri;
+                s_rinv = ri;
             }
         }
         __syncthreads();
-        if (fail) { done = j; break; }
-        const double rjj = A[j][j];
-        for (int c = j + 1 + threadIdx.x; c < nb; c += blockDim.x) A[j][c] /= rjj;
+        if (fail) break;
+        const double ri = s_rinv;
+        for (int c = j + 1 + threadIdx.x; c < nb; c += blockDim.x) A[j][c] *= ri;
         __syncthreads();
-        const int w = nb - j - 1;
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            const int c1 = j + 1 + e % w, c2 = j + 1 + e / w;
-            if (c1 <= c2) A[c1][c2] = fma(-A[j][c1], A[j][c2], A[c1][c2]);
+        const int w = nb - j - 1, np = (w + 1) / 2 * (w + 1);
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            int c1, c2;
+            if (upper_pair(e, w, &c1, &c2)) {
+                c1 += j + 1;
+                c2 += j + 1;
+                A[c1][c2] = fma(-A[j][c1], A[j][c2], A[c1][c2]);
+            }
         }
         __syncthreads();
     }
-    (void)done;
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         G[i + (i64)j * ldg] = (i <= j) ? A[i][j] : 0.0;
@@ -113,30 +139,46 @@ __global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* G, i64
 // Modified LU (Householder reconstruction, BD2015 Alg. 5 as cited in Sec. 2.3)
 // of one nb x nb diagonal block in place: for each column j the sign
 // s_j = -sign(a_jj) (sign(0) = +1) is recorded in D[j], a_jj -= s_j, then the
-// column below is divided by the new a_jj and the block's trailing part gets
-// the rank-1 update.  No pivoting.
+// column below is scaled by 1/a_jj and the block's trailing part gets the
+// rank-1 update.  No pivoting.  Lookahead: thread 0 forms the next pivot
+// (its one entry of the update, the sign and the reciprocal, ~700 cycles of
+// FP64 latency) while the other threads update the rest of the block.
 __global__ void __launch_bounds__(256) modlu_small_kernel(int nb, double* Y, i64 ldy, double* D) {
     __shared__ double A[NBD][NBD + 1];
+    __shared__ double s_rp;
     for (int e = threadIdx.x; e < NBD * NBD; e += blockDim.x) {
         const int i = e % NBD, j = e / NBD;
         A[i][j] = (i < nb && j < nb) ? Y[i + (i64)j * ldy] : 0.0;
     }
     __syncthreads();
+    // pivot of column jj from its (fully updated) diagonal entry: sign, shift, reciprocal
+    auto pivot = [&](int jj) {
+        const double a = A[jj][jj];
+        const long long bits = __double_as_longlong(a);
+        const double s = (bits >= 0 || bits == (long long)0x8000000000000000ull) ? -1.0 : 1.0;   // a >= 0
+        D[jj] = s;
+        const double piv = a - s;
+        A[jj][jj] = piv;
+        s_rp = 1.0 / piv;
+    };
+    if (threadIdx.x == 0 && nb > 0) pivot(0);
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
-            const double a = A[j][j];
-            const double s = (a >= 0.0) ? -1.0 : 1.0;
-            D[j] = s;
-            A[j][j] = a - s;
-        }
-        __syncthreads();
-        const double piv = A[j][j];
-        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] /= piv;
+        const double rp = s_rp;
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] *= rp;
         __syncthreads();
         const int w = nb - j - 1;
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            const int i = j + 1 + e % w, c = j + 1 + e / w;
-            A[i][c] = fma(-A[i][j], A[j][c], A[i][c]);
+        if (threadIdx.x == 0) {
+            if (w > 0) {
+                A[j + 1][j + 1] = fma(-A[j + 1][j], A[j][j + 1], A[j + 1][j + 1]);
+                pivot(j + 1);
+            }
+        } else {
+            for (int e = threadIdx.x - 1; e < w * w; e += blockDim.x - 1) {
+                if (e == 0) continue;   // (j+1, j+1): thread 0's
+                const int i = j + 1 + e % w, c = j + 1 + e / w;
+                A[i][c] = fma(-A[i][j], A[j][c], A[i][c]);
+            }
         }
         __syncthreads();
     }
@@ -229,7 +271,7 @@ int modlu(const Ctx& c, i64 rows, i64 k, double* Y, i64 ldy, double* D) {
             // U12 = L11^{-1} A12  <=>  U12^T = A12^T L11^{-T}, L11^T unit upper
             BQ_TRY(trsm_ru(c, right, nb, Yv.sub(jb, jb).t(), Yv.sub(jb, jb + nb).t(), true));
             if (below > 0)   // A22 -= L21 U12
-                BQ_TRY(dgemm(c, false, false, below, right, nb, -1.0, Y + (jb + nb) + jb * ldy, ldy,
+                BQ_TRY(pgemm(c, false, false, below, right, nb, -1.0, Y + (jb + nb) + jb * ldy, ldy,
                              Y + jb + (jb + nb) * ldy, ldy, 1.0, Y + (jb + nb) + (jb + nb) * ldy, ldy));
         }
     }

@@ -177,17 +177,26 @@ int launch(const Ctx& c, GemmArgs a) {
     }
     // split-K when the output tiles cannot fill the GPU: one 64x64 tile with
     // K = 64 is ~65 us of FP64 work on a single SM, so even short K ranges
-    // are split, down to one 16-deep slab per CTA
+    // are split, down to one 16-deep slab per CTA.  FP64 throughput is per SM,
+    // so the time of a split GEMM goes with the CTAs on the busiest SM over
+    // the split count, ceil(work_tiles * s / SMs) / s; s minimizes that (the
+    // smallest s within 1 % of the best, to keep the reduction short).
+    // Tiles below the diagonal of an upper-triangle-only C do no work.
     int splits = 1;
     const i64 tiles = tm * tn;
-    const i64 target = 4LL * c.dev.sms;
-    if (tiles < target && a.K >= 2 * BK && c.splitk != nullptr) {
-        i64 s = cdiv(target, tiles);
-        s = imin(s, a.K / BK);
-        s = imin(s, 64);
+    const i64 work_tiles = (a.flags & kGemmCUpper) ? imin(tm, tn) * (imin(tm, tn) + 1) / 2 + imax(0, tn - tm) * tm
+                                                   : tiles;
+    const i64 sms = c.dev.sms;
+    if (work_tiles < 4 * sms && a.K >= 2 * BK && c.splitk != nullptr) {
         const i64 fit = (i64)(c.splitk_elems / (size_t)(a.M * a.N));
-        s = imin(s, fit);
-        if (s > 1) splits = (int)s;
+        const i64 smax = imin(imin(a.K / BK, 64), fit);
+        double best = 1e30;
+        i64 bs = 1;
+        for (i64 sc = 1; sc <= smax; ++sc) {
+            const double cost = (double)cdiv(work_tiles * sc, sms) / (double)sc;
+            if (cost < best * 0.99) { best = cost; bs = sc; }
+        }
+        splits = (int)bs;
     }
     a.kchunk = cdiv(cdiv(a.K, splits), BK) * BK;
     splits = (int)cdiv(a.K, a.kchunk);
@@ -229,7 +238,8 @@ int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, con
 }
 
 // C (M x N) = alpha * A (M x K) * B (K x N) + beta * C on strided views; each
-// view must be column-major (rs == 1) or row-major (cs == 1).
+// view must be column-major (rs == 1) or row-major (cs == 1).  Runs through
+// pgemm: the tensor-core slice GEMM in the mixed-precision form when large.
 int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, double beta, View C) {
     if (M <= 0 || N <= 0) return 0;
     auto as_op = [](View v, i64 rows, i64 cols, bool* trans, i64* ld) -> bool {
@@ -247,7 +257,7 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
             set_error("gemm_view: bad operand view");
             return BQRRP_EUNSUPPORTED;
         }
-        return dgemm(c, tA, tB, M, N, K, alpha, A.p, la, B.p, lb, beta, C.p, lc);
+        return pgemm(c, tA, tB, M, N, K, alpha, A.p, la, B.p, lb, beta, C.p, lc);
     }
     // C^T = B^T A^T with C^T column-major
     View At = A.t(), Bt = B.t();
@@ -255,7 +265,7 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
         set_error("gemm_view: bad operand view");
         return BQRRP_EUNSUPPORTED;
     }
-    return dgemm(c, tB, tA, N, M, K, alpha, Bt.p, lb, At.p, la, beta, C.p, lc);
+    return pgemm(c, tB, tA, N, M, K, alpha, Bt.p, lb, At.p, la, beta, C.p, lc);
 }
 
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,

@@ -270,25 +270,29 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         } else {
             __syncthreads();
         }
-        // (4) bulk update of columns cs.. of the owned rows below jg
+        // (4) bulk update of columns cs.. of the owned rows below jg, by warps
+        // 1.. only: warp 0 goes straight on to poll the next step's slots, and
+        // the barrier after that poll orders the bulk before the next interchange
         const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
-        if (elim && nr > 0 && cs < pw) {
-            if (nr >= NT) {
-                for (int rl = r0 + tid; rl < nloc; rl += NT) {
+        constexpr int BT = NT - 32;
+        if (elim && nr > 0 && cs < pw && tid >= 32) {
+            const int bt = tid - 32;
+            if (nr >= BT) {
+                for (int rl = r0 + bt; rl < nloc; rl += BT) {
                     const double l = slab[j * Rp + rl];
                     for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             } else {
-                const int ng = NT / nr, grp = tid / nr;
+                const int ng = BT / nr, grp = bt / nr;
                 if (grp < ng) {
-                    const int rl = r0 + tid - grp * nr;
+                    const int rl = r0 + bt - grp * nr;
                     const double l = slab[j * Rp + rl];
                     for (int c = cs + grp; c < pw; c += ng) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
         a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * Rp + rl];
@@ -297,22 +301,46 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
 
 // Apply the panel's interchanges to every sketch row outside the panel rows
 // [jb, jb+pw): swap columns jb+j and ipiv[jb+j] in order (LAPACK applies them to
-// the L part on the left and the trailing part on the right alike).  One
-// thread per row.
-__global__ void lu_swap_rows_kernel(i64 pw, i64 d, i64 jb, int steps, const i64* __restrict__ ipiv, double* Sk,
-                                    i64 ldsk) {
-    const i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= d - pw) return;
-    const i64 r = (q < jb) ? q : q + pw;
-    for (int j = 0; j < steps; ++j) {
-        const i64 a = jb + j, p = ipiv[jb + j];
-        if (p != a) {
-            double* x = Sk + r + a * ldsk;
-            double* y = Sk + r + p * ldsk;
-            const double t = *x;
-            *x = *y;
-            *y = t;
+// the L part on the left and the trailing part on the right alike).  The
+// swaps name at most 2*steps positions; each CTA tracks every named position y
+// forward through the sequence to its final place f(y), then gathers its rows
+// in one pass (all loads, a barrier, all stores), so a row costs one memory
+// round trip instead of a chain of dependent swaps.  Duplicate names carry the
+// same (y, f(y)) pair and store the same value.
+constexpr int kSwapRows = 32;
+__global__ void __launch_bounds__(256) lu_swap_rows_kernel(i64 pw, i64 d, i64 jb, int steps,
+                                                           const i64* __restrict__ ipiv, double* Sk, i64 ldsk) {
+    __shared__ i64 ip[64];
+    __shared__ i64 ys[128], fs[128];
+    const int tid = threadIdx.x, ne = 2 * steps;
+    if (tid < steps) ip[tid] = ipiv[jb + tid];
+    __syncthreads();
+    if (tid < ne) {
+        const i64 y = tid < steps ? jb + tid : ip[tid - steps];
+        i64 cur = y;
+        for (int j = 0; j < steps; ++j) {
+            const i64 a = jb + j, p = ip[j];
+            if (cur == a) cur = p;
+            else if (cur == p) cur = a;
         }
+        ys[tid] = y;
+        fs[tid] = cur;
+    }
+    __syncthreads();
+    const i64 q = (i64)blockIdx.x * kSwapRows + (tid & 31);
+    const bool valid = q < d - pw;
+    const i64 r = (q < jb) ? q : q + pw;
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = (tid >> 5) + 8 * k;
+        if (valid && i < ne) v[k] = Sk[r + ys[i] * ldsk];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = (tid >> 5) + 8 * k;
+        if (valid && i < ne) Sk[r + fs[i] * ldsk] = v[k];
     }
 }
 
@@ -756,7 +784,8 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
         BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));
         const i64 below = d - (jb + pw);
         if (d - pw > 0) {
-            lu_swap_rows_kernel<<<(unsigned)cdiv(d - pw, 128), 128, 0, c.stream>>>(pw, d, jb, st, ipiv, Sk, ldsk);
+            lu_swap_rows_kernel<<<(unsigned)cdiv(d - pw, kSwapRows), 256, 0, c.stream>>>(pw, d, jb, st, ipiv, Sk,
+                                                                                       ldsk);
             BQ_LAUNCH_CHECK();
         }
         if (below > 0) {
