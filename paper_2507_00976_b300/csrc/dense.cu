@@ -42,6 +42,7 @@ __device__ inline void load_unit_triangle(int nb, View R, int unit, double (*Rs)
 // in registers: faster at every height, as the warp form keeps many more
 // warps in flight per SM.)
 constexpr int kTrsmWarps = 4;
+constexpr i64 kTrsmTall = 4096;   // rows from which four rows per warp pay (enough warps for every SMSP)
 __global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp_kernel(i64 rows, int nb, View R, View X, int unit) {
     __shared__ double Rs[NBD][NBD + 1];
     __shared__ double dinv[NBD];
@@ -63,6 +64,39 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp_kernel(i64 rows, in
         }
         if (lane < nb) *X.at(i, lane) = x0 * dinv[lane];
         if (lane + 32 < nb) *X.at(i, lane + 32) = x1 * dinv[lane + 32];
+    }
+}
+
+// Four rows per warp for tall X, where throughput rather than latency
+// bounds the solve: lane l serves row l / 8 and columns l % 8 + 8q (q < 8).
+// Step j issues one FMA per column group still ahead of j, 8 - j/8 of them,
+// 72 FP64 instructions per row against 96 for one row per warp.
+__global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp4_kernel(i64 rows, int nb, View R, View X, int unit) {
+    __shared__ double Rs[NBD][NBD + 1];
+    __shared__ double dinv[NBD];
+    load_unit_triangle(nb, R, unit, Rs, dinv);
+    const int lane = threadIdx.x & 31, l8 = lane & 7, sub = lane >> 3;
+    const i64 stride = (i64)gridDim.x * kTrsmWarps * 4;
+    for (i64 i0 = ((i64)blockIdx.x * kTrsmWarps + (threadIdx.x >> 5)) * 4; i0 < rows; i0 += stride) {
+        const i64 i = i0 + sub;
+        const bool live = i < rows;
+        double x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = (live && l8 + 8 * q < nb) ? *X.at(i, l8 + 8 * q) : 0.0;
+#pragma unroll
+        for (int j = 0; j < NBD; ++j) {
+            if (j < nb) {
+                const double y = __shfl_sync(0xffffffffu, x[j / 8], (lane & ~7) | (j & 7));
+                if (l8 > (j & 7)) x[j / 8] = fma(-y, Rs[j][l8 + 8 * (j / 8)], x[j / 8]);
+#pragma unroll
+                for (int q = j / 8 + 1; q < 8; ++q) x[q] = fma(-y, Rs[j][l8 + 8 * q], x[q]);
+            }
+        }
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (l8 + 8 * q < nb) *X.at(i, l8 + 8 * q) = x[q] * dinv[l8 + 8 * q];
+        }
     }
 }
 
@@ -142,7 +176,7 @@ __global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* G, i64
 // column below is scaled by 1/a_jj and the block's trailing part gets the
 // rank-1 update.  No pivoting.  Lookahead: thread 0 forms the next pivot
 // (its one entry of the update, the sign and the reciprocal, ~700 cycles of
-// FP64 latency) while the other threads update the rest of the block.
+// FP64 latency) while warps 1.. update the rest of the block.
 __global__ void __launch_bounds__(256) modlu_small_kernel(int nb, double* Y, i64 ldy, double* D) {
     __shared__ double A[NBD][NBD + 1];
     __shared__ double s_rp;
@@ -168,14 +202,16 @@ __global__ void __launch_bounds__(256) modlu_small_kernel(int nb, double* Y, i64
         for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] *= rp;
         __syncthreads();
         const int w = nb - j - 1;
-        if (threadIdx.x == 0) {
-            if (w > 0) {
+        if (threadIdx.x < 32) {
+            // warp 0 does only the pivot (its other lanes idle): a lane of a warp
+            // that also ran update FMAs would serialize with them
+            if (threadIdx.x == 0 && w > 0) {
                 A[j + 1][j + 1] = fma(-A[j + 1][j], A[j][j + 1], A[j + 1][j + 1]);
                 pivot(j + 1);
             }
         } else {
-            for (int e = threadIdx.x - 1; e < w * w; e += blockDim.x - 1) {
-                if (e == 0) continue;   // (j+1, j+1): thread 0's
+            for (int e = threadIdx.x - 32; e < w * w; e += blockDim.x - 32) {
+                if (e == 0) continue;   // (j+1, j+1): the pivot warp's
                 const int i = j + 1 + e % w, c = j + 1 + e / w;
                 A[i][c] = fma(-A[i][j], A[j][c], A[i][c]);
             }
@@ -226,9 +262,15 @@ int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit) {
     if (rows <= 0 || k <= 0) return 0;
     for (i64 jb = 0; jb < k; jb += NBD) {
         const int nb = (int)imin(NBD, k - jb);
-        const i64 grid = imin(cdiv(rows, kTrsmWarps), 6LL * c.dev.sms);
-        trsm_warp_kernel<<<(unsigned)grid, 32 * kTrsmWarps, 0, c.stream>>>(rows, nb, R.sub(jb, jb), X.sub(0, jb),
-                                                                         unit ? 1 : 0);
+        if (rows >= kTrsmTall) {
+            const i64 grid = imin(cdiv(rows, 4 * kTrsmWarps), 6LL * c.dev.sms);
+            trsm_warp4_kernel<<<(unsigned)grid, 32 * kTrsmWarps, 0, c.stream>>>(rows, nb, R.sub(jb, jb),
+                                                                              X.sub(0, jb), unit ? 1 : 0);
+        } else {
+            const i64 grid = imin(cdiv(rows, kTrsmWarps), 6LL * c.dev.sms);
+            trsm_warp_kernel<<<(unsigned)grid, 32 * kTrsmWarps, 0, c.stream>>>(rows, nb, R.sub(jb, jb),
+                                                                             X.sub(0, jb), unit ? 1 : 0);
+        }
         BQ_LAUNCH_CHECK();
         if (jb + nb < k) {
             // X(:, jb+nb:k) -= X(:, jb:jb+nb) * R(jb:jb+nb, jb+nb:k)

@@ -270,29 +270,25 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         } else {
             __syncthreads();
         }
-        // (4) bulk update of columns cs.. of the owned rows below jg, by warps
-        // 1.. only: warp 0 goes straight on to poll the next step's slots, and
-        // the barrier after that poll orders the bulk before the next interchange
+        // (4) bulk update of columns cs.. of the owned rows below jg
         const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
-        constexpr int BT = NT - 32;
-        if (elim && nr > 0 && cs < pw && tid >= 32) {
-            const int bt = tid - 32;
-            if (nr >= BT) {
-                for (int rl = r0 + bt; rl < nloc; rl += BT) {
+        if (elim && nr > 0 && cs < pw) {
+            if (nr >= NT) {
+                for (int rl = r0 + tid; rl < nloc; rl += NT) {
                     const double l = slab[j * Rp + rl];
                     for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             } else {
-                const int ng = BT / nr, grp = bt / nr;
+                const int ng = NT / nr, grp = tid / nr;
                 if (grp < ng) {
-                    const int rl = r0 + bt - grp * nr;
+                    const int rl = r0 + tid - grp * nr;
                     const double l = slab[j * Rp + rl];
                     for (int c = cs + grp; c < pw; c += ng) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
         a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * Rp + rl];
@@ -956,11 +952,14 @@ namespace {
 // Only R (upper triangle, zeros below) is written back to W.
 constexpr int kSqrMaxD = 640;
 
+__device__ inline void bar_sync_64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }   // warps 0-1
+
 __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
     extern __shared__ double loc[];                 // [ncl][d] local columns
     __shared__ double vbuf[2][kSqrMaxD];
     __shared__ double vloc[kSqrMaxD];
-    __shared__ double s_tau[2];
+    __shared__ double s_tau[2], s_scal[2];
+    __shared__ double red2[2];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), g = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -971,16 +970,15 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     }
     __syncthreads();
 
-    // Reflector of column j (owned here) into vbuf[par], by one warp: v(j) = 1,
+    // Reflector of column j (owned here), by one warp: v(j) = 1,
     // v(j+1:) = x(j+1:) / (alpha - beta), tau = (beta - alpha) / beta, both
-    // from the single quotient q = 1 / (beta (alpha - beta)).  The column
-    // becomes (beta, 0, ..., 0).
-    auto reflect = [&](i64 j, int par) {
-        double* x = loc + (j / C) * d;
-        double xn2 = 0.0;
-        for (i64 r = j + 1 + lane; r < d; r += 32) xn2 = fma(x[r], x[r], xn2);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
+    // from the single quotient q = 1 / (beta (alpha - beta)).  vbuf[par] gets
+    // x(j+1:) unscaled and s_scal[par] the scale, which every reader applies
+    // as it copies (off the owner's critical path).  The column becomes
+    // (beta, 0, ..., 0).
+    // Scalars of the reflector of column j (x), given xn2 = ||x(j+1:)||^2;
+    // one thread.  Writes beta into x(j) and tau, scale to s_tau/s_scal[par].
+    auto reflector_scalars = [&](double* x, i64 j, double xn2, int par) {
         const double alpha = x[j];
         const bool nz = ((unsigned long long)__double_as_longlong(xn2) & 0x7fffffffffffffffull) != 0;
         double tau = 0.0, beta = alpha, scal = 1.0;
@@ -994,15 +992,22 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
             scal = beta * q;
             tau = -(am * am) * q;
         }
+        x[j] = beta;
+        s_tau[par] = tau;
+        s_scal[par] = scal;
+    };
+    // The first reflector, by one warp.
+    auto reflect = [&](i64 j, int par) {
+        double* x = loc + (j / C) * d;
+        double xn2 = 0.0;
+        for (i64 r = j + 1 + lane; r < d; r += 32) xn2 = fma(x[r], x[r], xn2);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
+        __syncwarp();
+        if (lane == 0) reflector_scalars(x, j, xn2, par);
         for (i64 r = j + 1 + lane; r < d; r += 32) {
-            const double v = nz ? x[r] * scal : x[r];
-            vbuf[par][r] = v;
+            vbuf[par][r] = x[r];
             x[r] = 0.0;                                   // below the diagonal of R
-        }
-        if (lane == 0) {
-            vbuf[par][j] = 1.0;
-            x[j] = beta;
-            s_tau[par] = tau;
         }
     };
     // col -= tau v (v^T col) over rows [j, d), by one warp
@@ -1019,21 +1024,47 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     cl.sync();
     for (i64 j = 0; j < s; ++j) {
         const int o = (int)(j % C), par = (int)(j & 1);
-        // reflector j from its owner
+        // reflector j from its owner (the two scalars and the vector in one round of
+        // remote loads)
         const double* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
-        for (i64 r = j + tid; r < d; r += NT) vloc[r] = vsrc[r];
+        const double scal = *cl.map_shared_rank(&s_scal[par], o);
         const double tau = *cl.map_shared_rank(&s_tau[par], o);
+        for (i64 r = j + tid; r < d; r += NT) vloc[r] = (r == j) ? 1.0 : vsrc[r] * scal;
         __syncthreads();
         const bool live = ((unsigned long long)__double_as_longlong(tau) & 0x7fffffffffffffffull) != 0;
         const bool next_here = j + 1 < s && (int)((j + 1) % C) == g;
-        if (next_here && warp == 0) {
-            // lookahead: column j+1 first, then its reflector
-            if (live) apply(loc + ((j + 1) / C) * d, j, tau);
-            __syncwarp();
-            reflect(j + 1, par ^ 1);
+        if (next_here && warp < 2) {
+            // lookahead: warps 0-1 update column j+1 first, then form its reflector
+            // (rows split over 64 threads, partial sums combined through shared
+            // memory behind named barrier 1)
+            const int t = tid;
+            double* x = loc + ((j + 1) / C) * d;
+            if (live) {
+                double dot = 0.0;
+                for (i64 r = j + t; r < d; r += 64) dot = fma(vloc[r], x[r], dot);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+                if (lane == 0) red2[warp] = dot;
+                bar_sync_64();
+                const double w = tau * (red2[0] + red2[1]);
+                for (i64 r = j + t; r < d; r += 64) x[r] = fma(-w, vloc[r], x[r]);
+                bar_sync_64();
+            }
+            const i64 jj = j + 1;
+            double xn2 = 0.0;
+            for (i64 r = jj + 1 + t; r < d; r += 64) xn2 = fma(x[r], x[r], xn2);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
+            if (lane == 0) red2[warp] = xn2;
+            bar_sync_64();
+            if (t == 0) reflector_scalars(x, jj, red2[0] + red2[1], par ^ 1);
+            for (i64 r = jj + 1 + t; r < d; r += 64) {   // same rows as this thread's norm terms
+                vbuf[par ^ 1][r] = x[r];
+                x[r] = 0.0;                               // below the diagonal of R
+            }
         }
         if (live) {
-            const int w0 = next_here ? 1 : 0, nw = NT / 32 - w0;
+            const int w0 = next_here ? 2 : 0, nw = NT / 32 - w0;
             if (warp >= w0) {
                 for (int lc = warp - w0; lc < ncl; lc += nw) {
                     const i64 gc = (i64)lc * C + g;
