@@ -150,12 +150,29 @@ __device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i
     }
 }
 
+// |x| as an ordering key: for non-negative doubles the bit patterns order like
+// the values, so pivot searches compare integers (an FP64 compare holds a
+// sub-partition's FP64 unit for ~64 cycles on B300, like a DFMA).
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// First maximum over (key, index): larger key, then smaller index.
+__device__ __forceinline__ void argmax_merge_key(unsigned long long& k, int& i, unsigned long long k2, int i2) {
+    if (k2 > k || (k2 == k && i2 < i)) {
+        k = k2;
+        i = i2;
+    }
+}
+
 // X(i, 0:k) <- X(i, 0:k) R^{-1} for one row i, R upper triangular in shared
-// memory (ld ldr >= k rounded up to 16).  Left-looking in blocks of 16
-// columns held in registers; the subtractions of each element run in column
-// order, then the division, as in row-wise forward substitution.
+// memory (ld ldr >= k rounded up to 16), rinv[j] = 1 / R(j, j) formed once
+// per CTA (an FP64 division holds a sub-partition's FP64 unit for ~640
+// cycles on B300).  Left-looking in blocks of 16 columns held in registers;
+// the subtractions of each element run in column order, then the scaling by
+// the reciprocal, as in row-wise forward substitution.
 __device__ void row_trsm_upper(const double* src, i64 lds, double* dst, i64 ldd, i64 i, int k,
-                               const double* R, int ldr) {
+                               const double* R, int ldr, const double* rinv) {
     for (int jb = 0; jb < k; jb += 16) {
         const int nb = min(16, k - jb);
         double x[16];
@@ -169,7 +186,7 @@ __device__ void row_trsm_upper(const double* src, i64 lds, double* dst, i64 ldd,
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             if (q < nb) {
-                x[q] /= R[(jb + q) + (jb + q) * ldr];
+                x[q] *= rinv[jb + q];
 #pragma unroll
                 for (int u = q + 1; u < 16; ++u) x[u] -= x[q] * R[(jb + q) + (jb + u) * ldr];
             }
@@ -316,33 +333,27 @@ __global__ void __launch_bounds__(BT) bat_sketch_kernel(BatArgs a, Slot sl, int 
 // ------------------------------------------------------------------ Alg. 2 on one matrix per CTA
 // First maximum of |W(j, t)| over t in [j, N) (W ld d): the pivot search of
 // LU step j on X = W^T.
-__device__ int cta_first_argmax(const double* W, i64 d, i64 j, i64 N, double* wv, int* wi) {
+__device__ int cta_first_argmax(const double* W, i64 d, i64 j, i64 N, unsigned long long* wk, int* wi) {
     __shared__ int s_p;
-    double bv = -1.0;
+    unsigned long long bk = 0;
     int bi = INT_MAX;
-    for (i64 t = j + threadIdx.x; t < N; t += BT) {
-        const double v = fabs(W[j + t * d]);
-        if (v > bv) {
-            bv = v;
-            bi = (int)t;
-        }
-    }
+    for (i64 t = j + threadIdx.x; t < N; t += BT) argmax_merge_key(bk, bi, abs_key(W[j + t * d]), (int)t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        argmax_merge(bv, bi, v2, i2);
+        argmax_merge_key(bk, bi, k2, i2);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        wv[wid] = bv;
+        wk[wid] = bk;
         wi[wid] = bi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v = wv[0];
+        unsigned long long k = wk[0];
         int i = wi[0];
-        for (int q = 1; q < NW; ++q) argmax_merge(v, i, wv[q], wi[q]);
+        for (int q = 1; q < NW; ++q) argmax_merge_key(k, i, wk[q], wi[q]);
         s_p = (i == INT_MAX) ? (int)j : i;
     }
     __syncthreads();
@@ -398,8 +409,9 @@ __device__ void cta_house_qr(double* W, i64 d, i64 nc, double* vbuf, double* s_t
 
 __device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int iter) {
     __shared__ double pc[kMaxD];
-    __shared__ double wv[NW];
+    __shared__ unsigned long long wv[NW];
     __shared__ int wi[NW];
+    __shared__ double s_rp;
     __shared__ int ipiv[kMaxD];
     // dynamic shared memory: one L row per warp, then the pivot vector
     extern __shared__ double qdsm[];
@@ -439,6 +451,9 @@ __device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int it
         // next step's pivot candidates come out of the Schur update.  At the
         // end Wk(l, t), l < min(t, r), holds L(t, l) and Wk(c, j), c >= j, j < r,
         // holds U(j, c).
+        // The multipliers use one reciprocal of the pivot per step, formed by
+        // thread 0 as soon as the pivot is known (l = x * (1/piv), within an ulp
+        // of GETRF's x / piv); |x| is compared as an integer key.
         if (!nonfinite) {
             bool search = true;
             for (i64 j = 0; j < r; ++j) {
@@ -452,43 +467,47 @@ __device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int it
                 if (threadIdx.x == 0) ipiv[j] = p;
                 __syncthreads();
                 const double piv = Wk[j + j * d];
-                if (piv != 0.0) {
+                if (abs_key(piv) != 0) {   // exact zero pivot: no elimination, as GETRF
+                    // after a search (first step, or after a zero pivot) every thread
+                    // forms the reciprocal itself; otherwise thread 0 formed it last step
+                    const double rp = search ? 1.0 / piv : s_rp;
                     for (i64 e = j + 1 + threadIdx.x; e < d; e += BT) pc[e] = Wk[e + j * d];
                     __syncthreads();
-                    double bv = -1.0;
+                    unsigned long long bk = 0;
                     int bi = INT_MAX;
                     for (i64 t = j + 1 + threadIdx.x; t < N; t += BT) {
                         double* col = Wk + t * d;
-                        const double l = col[j] / piv;
+                        const double l = col[j] * rp;
                         col[j] = l;
                         if (j + 1 < d) {
                             const double v1 = fma(-l, pc[j + 1], col[j + 1]);
                             col[j + 1] = v1;
-                            const double av = fabs(v1);
-                            if (av > bv) {
-                                bv = av;
-                                bi = (int)t;
-                            }
+                            argmax_merge_key(bk, bi, abs_key(v1), (int)t);
                         }
 #pragma unroll 4
                         for (i64 rr = j + 2; rr < d; ++rr) col[rr] = fma(-l, pc[rr], col[rr]);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
                         const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                        argmax_merge(bv, bi, v2, i2);
+                        argmax_merge_key(bk, bi, k2, i2);
                     }
                     if (lane == 0) {
-                        wv[wid] = bv;
+                        wv[wid] = bk;
                         wi[wid] = bi;
                     }
                     __syncthreads();
                     if (threadIdx.x == 0) {
-                        double v = wv[0];
+                        unsigned long long k = wv[0];
                         int i = wi[0];
-                        for (int q = 1; q < NW; ++q) argmax_merge(v, i, wv[q], wi[q]);
-                        s_next = (i == INT_MAX) ? (int)(j + 1) : i;
+                        for (int q = 1; q < NW; ++q) argmax_merge_key(k, i, wv[q], wi[q]);
+                        const int nx = (i == INT_MAX) ? (int)(j + 1) : i;
+                        s_next = nx;
+                        if (j + 1 < r) {   // next pivot X(nx, j+1), already updated
+                            const double pv = Wk[(j + 1) + (i64)nx * d];
+                            s_rp = (abs_key(pv) != 0) ? 1.0 / pv : 0.0;
+                        }
                     }
                     search = false;
                 } else {
@@ -630,6 +649,7 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
     double* Gs = sm;
     double* Yc = sm + (size_t)kb * kb;
     __shared__ double Dsg[kMaxB];
+    __shared__ double Rinv[kMaxB];   // reciprocals of the diagonal of the triangle in Gs
     __shared__ int s_flag, s_kc;
         {
         BatState* S = a.st + mat;
@@ -666,8 +686,9 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
             const int i = e % k, j = e / k;
             Gs[i + j * kb] = (i <= j) ? Wk[i + (i64)j * d] : 0.0;
         }
+        for (int j = threadIdx.x; j < k; j += BT) Rinv[j] = 1.0 / Wk[j + (i64)j * d];
         __syncthreads();
-        for (i64 i = threadIdx.x; i < rows; i += BT) row_trsm_upper(Ap, m, Y, m, i, k, Gs, kb);
+        for (i64 i = threadIdx.x; i < rows; i += BT) row_trsm_upper(Ap, m, Y, m, i, k, Gs, kb, Rinv);
         __syncthreads();
 
         // ---- G = Pre^T Pre, upper triangle, 4x4 tiles; thread groups split
@@ -751,16 +772,23 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
         // ---- R_chol = chol(G), upper, right-looking; breakdown lowers k (R15)
         if (threadIdx.x == 0) s_kc = k;
         __syncthreads();
+        // thread 0 forms r_jj = g_jj * rsqrt(g_jj) and keeps 1 / r_jj for the row
+        // scaling and the solve with R_chol (one special function per step)
         for (int j = 0; j < k; ++j) {
             if (threadIdx.x == 0) {
                 const double sv = Gs[j + j * kb];
-                if (!(sv > 0.0) || !isfinite(sv)) s_kc = j;
-                else Gs[j + j * kb] = sqrt(sv);
+                const long long bits = __double_as_longlong(sv);
+                if (!(bits > 0 && bits < 0x7ff0000000000000ll)) s_kc = j;   // not (finite and > 0)
+                else {
+                    const double ri = rsqrt(sv);
+                    Gs[j + j * kb] = sv * ri;
+                    Rinv[j] = ri;
+                }
             }
             __syncthreads();
             if (s_kc < k) break;
-            const double rjj = Gs[j + j * kb];
-            for (int l = j + 1 + threadIdx.x; l < k; l += BT) Gs[j + l * kb] /= rjj;
+            const double ri = Rinv[j];
+            for (int l = j + 1 + threadIdx.x; l < k; l += BT) Gs[j + l * kb] *= ri;
             __syncthreads();
             const int nt = k - j - 1;
             for (int e = threadIdx.x; e < nt * nt; e += BT) {
@@ -782,7 +810,7 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
         }
 
         // ---- Q_c = Pre R_chol^{-1} (in place in Y); P = R_chol Rsk(0:k, 0:w)
-        for (i64 i = threadIdx.x; i < rows; i += BT) row_trsm_upper(Y, m, Y, m, i, k, Gs, kb);
+        for (i64 i = threadIdx.x; i < rows; i += BT) row_trsm_upper(Y, m, Y, m, i, k, Gs, kb, Rinv);
         for (int e = threadIdx.x; e < k * (int)w; e += BT) {
             const int i = e % k, j = e / k;
             double acc = 0.0;
@@ -801,13 +829,16 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
         for (int j = 0; j < k; ++j) {
             if (threadIdx.x == 0) {
                 const double av = Gs[j + j * kb];
-                const double sg = (av >= 0.0) ? -1.0 : 1.0;     // s_j = -sign(a), sign(0) = +1
-                Dsg[j] = sg;
-                Gs[j + j * kb] = av - sg;
+                const long long ab = __double_as_longlong(av);
+                const double sg = (ab >= 0 || ab == (long long)0x8000000000000000ull) ? -1.0 : 1.0;   // av >= 0
+                Dsg[j] = sg;                                         // s_j = -sign(a), sign(0) = +1
+                const double pv = av - sg;
+                Gs[j + j * kb] = pv;
+                Rinv[j] = 1.0 / pv;
             }
             __syncthreads();
-            const double pv = Gs[j + j * kb];
-            for (int i = j + 1 + threadIdx.x; i < k; i += BT) Gs[i + j * kb] /= pv;
+            const double rp = Rinv[j];
+            for (int i = j + 1 + threadIdx.x; i < k; i += BT) Gs[i + j * kb] *= rp;
             __syncthreads();
             const int nt = k - j - 1;
             for (int e = threadIdx.x; e < nt * nt; e += BT) {
@@ -817,7 +848,7 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
             __syncthreads();
         }
         // rows k .. rows-1: Y(i, :) = Q(i, :) U^{-1}
-        for (i64 i = k + threadIdx.x; i < rows; i += BT) row_trsm_upper(Y, m, Y, m, i, k, Gs, kb);
+        for (i64 i = k + threadIdx.x; i < rows; i += BT) row_trsm_upper(Y, m, Y, m, i, k, Gs, kb, Rinv);
         // explicit unit lower top block of Y
         for (int e = threadIdx.x; e < k * k; e += BT) {
             const int i = e % k, j = e / k;
@@ -875,12 +906,14 @@ __device__ void body_panel(const BatArgs& a, const int mat, const int sub, int i
         // ---- Z = Rsk11 R11^{-1} for the sketch update (k = w and c < n)
         const bool cont = (k == w) && (c < n);
         if (cont) {
+            __syncthreads();   // Rinv (the modified LU's) is read above until here
             for (int e = threadIdx.x; e < k * k; e += BT) {
                 const int i = e % k, j = e / k;
                 Gs[i + j * kb] = (i <= j) ? Dsg[i] * Pb[i + (i64)j * b] : 0.0;
             }
+            for (int j = threadIdx.x; j < k; j += BT) Rinv[j] = 1.0 / (Dsg[j] * Pb[j + (i64)j * b]);
             __syncthreads();
-            for (int i = threadIdx.x; i < k; i += BT) row_trsm_upper(Wk, d, Zb, b, i, k, Gs, kb);
+            for (int i = threadIdx.x; i < k; i += BT) row_trsm_upper(Wk, d, Zb, b, i, k, Gs, kb, Rinv);
         }
         if (threadIdx.x == 0) {
             S->k = k;
