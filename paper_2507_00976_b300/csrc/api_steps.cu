@@ -1,5 +1,6 @@
 // api_steps.cu -- C-ABI entry points for single steps of BQRRP (used by the
 // per-kernel parity tests) and the FP64 peak probe used by the benchmark.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -22,16 +23,20 @@ __global__ void init_status_small(DevStatus* st) {
 
 constexpr size_t kSplitElems = (size_t)1 << 21;
 
+// split-K partials for a blocked QR of n columns: the W = V^T C products have
+// one 64-row tile band, so their split count needs s * 64 * n partials
+inline size_t qr_split_elems(i64 n) { return std::max(kSplitElems, (size_t)8 * 64 * (size_t)imax(n, 1)); }
+
 // status block, split-K partials and cooperative scratch at the head of a workspace
-void carve_common(Arena& ar, Ctx* c) {
+void carve_common(Arena& ar, Ctx* c, size_t split_elems) {
     c->st = ar.take<DevStatus>(1);
-    c->splitk_elems = kSplitElems;
-    c->splitk = ar.take<double>(kSplitElems);
+    c->splitk_elems = split_elems;
+    c->splitk = ar.take<double>(split_elems);
     coop_scratch_elems(64, 148, &c->coop_elems);
     c->coop = ar.take<double>(c->coop_elems);
 }
 
-int begin(void* ws, size_t bytes, void* stream, Arena* ar, Ctx* c, bool dry) {
+int begin(void* ws, size_t bytes, void* stream, Arena* ar, Ctx* c, bool dry, size_t split_elems = kSplitElems) {
     ar->dry = dry;
     if (!dry) {
         ar->base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
@@ -39,7 +44,7 @@ int begin(void* ws, size_t bytes, void* stream, Arena* ar, Ctx* c, bool dry) {
         BQ_TRY(current_device(&c->dev));
     }
     c->stream = (cudaStream_t)stream;
-    carve_common(*ar, c);
+    carve_common(*ar, c, split_elems);
     return 0;
 }
 
@@ -234,7 +239,7 @@ size_t bqrrp_geqrf_workspace(int64_t m, int64_t n, int64_t nb) {
     if (m < 0 || n < 0) return 0;
     Arena ar;
     Ctx c{};
-    begin(nullptr, 0, nullptr, &ar, &c, true);
+    begin(nullptr, 0, nullptr, &ar, &c, true, qr_split_elems(n));
     ar.take<double>((size_t)imax(m, 1) * 64);
     ar.take<double>(64 * 64);
     ar.take<double>((size_t)64 * imax(n, 1));
@@ -256,7 +261,7 @@ int bqrrp_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau, int64
     if (workspace_bytes < bqrrp_geqrf_workspace(m, n, nb)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
     Arena ar;
     Ctx c{};
-    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false));
+    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false, qr_split_elems(n)));
     double* V = ar.take<double>((size_t)m * 64);
     double* T = ar.take<double>(64 * 64);
     double* W = ar.take<double>((size_t)64 * n);
@@ -284,7 +289,7 @@ int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
     if (workspace_bytes < bqrrp_geqrf_mixed_workspace(m, n)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
     Arena ar;
     Ctx c{};
-    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false));
+    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false, qr_split_elems(n)));
     double* V = ar.take<double>((size_t)m * 64);
     double* T = ar.take<double>(64 * 64);
     double* W = ar.take<double>((size_t)64 * n);

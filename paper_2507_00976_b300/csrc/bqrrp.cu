@@ -270,7 +270,10 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
     B->Z = ar.take<double>((size_t)bb * bb);
     B->D = ar.take<double>((size_t)bb);
     B->sktau = ar.take<double>((size_t)imax(d, n));
-    B->splitk_elems = (size_t)imax(16 * bb * bb, (i64)1 << 22);
+    // split-K partials: the trailing product W = Y^T C has only b/64 tile rows,
+    // so balancing it over the SMs takes a few splits of b x n partials (2048 n
+    // doubles: 8 splits at b = 256; larger b has enough tiles to need fewer)
+    B->splitk_elems = (size_t)imax(imax(16 * bb * bb, (i64)1 << 22), 2048 * n);
     B->splitk = ar.take<double>(B->splitk_elems);
     coop_scratch_elems(64, 148, &B->coop_elems);
     B->coop = ar.take<double>(B->coop_elems);

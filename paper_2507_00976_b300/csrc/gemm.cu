@@ -175,19 +175,21 @@ int launch(const Ctx& c, GemmArgs a) {
         set_error("dgemm: grid too large (%lld x %lld tiles)", (long long)tm, (long long)tn);
         return BQRRP_EUNSUPPORTED;
     }
-    // split-K when the output tiles cannot fill the GPU: one 64x64 tile with
-    // K = 64 is ~65 us of FP64 work on a single SM, so even short K ranges
-    // are split, down to one 16-deep slab per CTA.  FP64 throughput is per SM,
-    // so the time of a split GEMM goes with the CTAs on the busiest SM over
-    // the split count, ceil(work_tiles * s / SMs) / s; s minimizes that (the
-    // smallest s within 1 % of the best, to keep the reduction short).
-    // Tiles below the diagonal of an upper-triangle-only C do no work.
+    // split-K balances the FP64 work over the SMs: one 64x64 tile with K = 64
+    // is ~65 us on a single SM, and the tile count of a product is rarely a
+    // multiple of the SM count (W = V^T C of a 256-wide block, 4 x nc/64 tiles,
+    // lost ~10 % to its last partial wave).  FP64 throughput is per SM, so the
+    // time of a split GEMM goes with the CTAs on the busiest SM over the split
+    // count, ceil(work_tiles * s / SMs) / s; s minimizes that, down to one
+    // 16-deep slab per CTA, taking a larger s only for a gain above 1 % (large
+    // products stay unsplit).  Tiles below the diagonal of an
+    // upper-triangle-only C do no work.
     int splits = 1;
     const i64 tiles = tm * tn;
     const i64 work_tiles = (a.flags & kGemmCUpper) ? imin(tm, tn) * (imin(tm, tn) + 1) / 2 + imax(0, tn - tm) * tm
                                                    : tiles;
     const i64 sms = c.dev.sms;
-    if (work_tiles < 4 * sms && a.K >= 2 * BK && c.splitk != nullptr) {
+    if (a.K >= 2 * BK && c.splitk != nullptr) {
         const i64 fit = (i64)(c.splitk_elems / (size_t)(a.M * a.N));
         const i64 smax = imin(imin(a.K / BK, 64), fit);
         double best = 1e30;

@@ -21,9 +21,10 @@ def test_workspace_queries_are_consistent():
     small = B.bqrrp_workspace_query(2000, 1000, 128, 160)
     big = B.bqrrp_workspace_query(32768, 32768, 1024, 1280)
     assert 0 < small < big
-    # dominant terms: 2 d n + 2 b n + m b + max(m, d) min(n, 2d) doubles, plus fixed scratch
+    # dominant terms: 2 d n + 2 b n + m b + max(m, d) min(n, 2d) doubles, the
+    # split-K partials (2048 n doubles), plus fixed scratch
     m, n, b, d = 32768, 32768, 1024, 1280
-    est = 8 * (2 * d * n + m * b + 2 * b * n + max(m, d) * min(n, 2 * d))
+    est = 8 * (2 * d * n + m * b + 2 * b * n + max(m, d) * min(n, 2 * d) + 2048 * n)
     assert est <= big <= est + 256 * 2**20
     assert B.bqrrp_workspace_query(100, 200, 10, 12) == 0          # m < n
     assert B.bqrrp_workspace_query(100, 50, 0, 12) == 0            # b < 1
