@@ -482,11 +482,12 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         } else {
             // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
             pr.begin(P_PANEL);
-            // The Gram matrix, Cholesky, T, tau and R11 stay in FP64 (dgemm); in the
-            // mixed form only the tall rank-64 updates inside the triangular solves and
-            // the modified LU (pgemm) run on the tensor cores.
-            BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
-                                      tau + s));
+            {
+                Ctx cp = c;
+                cp.mixed = false;   // preconditioner, Gram, Cholesky, reconstruction, tau and R stay in FP64
+                BQ_TRY(cholqr_panel_steps(cp, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D,
+                                          B.bb, tau + s));
+            }
             {
                 const double r = (double)rows, kk = (double)k;
                 // TRSM, Gram, TRSM, reconstruction (rows k^2 each) + Cholesky, T, R11 (k^3 terms)

@@ -313,7 +313,7 @@ int modlu(const Ctx& c, i64 rows, i64 k, double* Y, i64 ldy, double* D) {
             // U12 = L11^{-1} A12  <=>  U12^T = A12^T L11^{-T}, L11^T unit upper
             BQ_TRY(trsm_ru(c, right, nb, Yv.sub(jb, jb).t(), Yv.sub(jb, jb + nb).t(), true));
             if (below > 0)   // A22 -= L21 U12
-                BQ_TRY(pgemm(c, false, false, below, right, nb, -1.0, Y + (jb + nb) + jb * ldy, ldy,
+                BQ_TRY(dgemm(c, false, false, below, right, nb, -1.0, Y + (jb + nb) + jb * ldy, ldy,
                              Y + jb + (jb + nb) * ldy, ldy, 1.0, Y + (jb + nb) + (jb + nb) * ldy, ldy));
         }
     }

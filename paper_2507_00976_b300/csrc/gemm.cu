@@ -240,8 +240,7 @@ int dgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, con
 }
 
 // C (M x N) = alpha * A (M x K) * B (K x N) + beta * C on strided views; each
-// view must be column-major (rs == 1) or row-major (cs == 1).  Runs through
-// pgemm: the tensor-core slice GEMM in the mixed-precision form when large.
+// view must be column-major (rs == 1) or row-major (cs == 1).
 int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, double beta, View C) {
     if (M <= 0 || N <= 0) return 0;
     auto as_op = [](View v, i64 rows, i64 cols, bool* trans, i64* ld) -> bool {
@@ -259,7 +258,7 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
             set_error("gemm_view: bad operand view");
             return BQRRP_EUNSUPPORTED;
         }
-        return pgemm(c, tA, tB, M, N, K, alpha, A.p, la, B.p, lb, beta, C.p, lc);
+        return dgemm(c, tA, tB, M, N, K, alpha, A.p, la, B.p, lb, beta, C.p, lc);
     }
     // C^T = B^T A^T with C^T column-major
     View At = A.t(), Bt = B.t();
@@ -267,7 +266,7 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
         set_error("gemm_view: bad operand view");
         return BQRRP_EUNSUPPORTED;
     }
-    return pgemm(c, tB, tA, N, M, K, alpha, Bt.p, lb, At.p, la, beta, C.p, lc);
+    return dgemm(c, tB, tA, N, M, K, alpha, Bt.p, lb, At.p, la, beta, C.p, lc);
 }
 
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,
