@@ -620,10 +620,12 @@ def run_serving(a, world, rank, local):
     flops_per_req = float(np.mean([canonical_flops(*SERVING_SHAPES[k][:2]) for k, _ in base_stream]))
     loads = {}
     for load in a.loads:
+        # the same request sample at every load (only the arrival gaps differ), so
+        # the levels compare the server, not the shape mix of different samples
         lam = load * capacity
         gaps = rng.exponential(1.0 / lam, size=len(base_stream))
         gaps[0] = 0.0
-        done, sub = run(draw(len(base_stream), rng), gaps)
+        done, sub = run(base_stream, gaps)
         lat = np.array([(c["t_done"] - sub[c["id"]][0]) * 1e3 for c in done])
         kinds = np.array([sub[c["id"]][1] for c in done])
         fl = sum(canonical_flops(*SERVING_SHAPES[sub[c["id"]][1]][:2]) for c in done)

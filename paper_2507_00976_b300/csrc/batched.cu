@@ -452,8 +452,8 @@ __device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int it
         // end Wk(l, t), l < min(t, r), holds L(t, l) and Wk(c, j), c >= j, j < r,
         // holds U(j, c).
         // The multipliers use one reciprocal of the pivot per step, formed by
-        // thread 0 as soon as the pivot is known (l = x * (1/piv), within an ulp
-        // of GETRF's x / piv); |x| is compared as an integer key.
+        // thread 0 as soon as the pivot is known, and one FMA correction that
+        // makes l the quotient x / piv of GETRF; |x| is compared as an integer key.
         if (!nonfinite) {
             bool search = true;
             for (i64 j = 0; j < r; ++j) {
@@ -477,7 +477,9 @@ __device__ void body_qrcp(const BatArgs& a, const int mat, const int sub, int it
                     int bi = INT_MAX;
                     for (i64 t = j + 1 + threadIdx.x; t < N; t += BT) {
                         double* col = Wk + t * d;
-                        const double l = col[j] * rp;
+                        const double x = col[j];
+                        double l = x * rp;
+                        l = fma(fma(-piv, l, x), rp, l);   // the quotient x / piv (Markstein correction)
                         col[j] = l;
                         if (j + 1 < d) {
                             const double v1 = fma(-l, pc[j + 1], col[j + 1]);

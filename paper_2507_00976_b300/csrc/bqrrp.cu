@@ -490,8 +490,9 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             }
             {
                 const double r = (double)rows, kk = (double)k;
-                // TRSM, Gram, TRSM, reconstruction (rows k^2 each) + Cholesky, T, R11 (k^3 terms)
-                pr.flops(P_PANEL, 2.0 * r * kk * kk * 4.0 + kk * kk * kk * (1.0 / 3.0 + 1.0 / 3.0) + 2.0 * kk * kk * w);
+                // preconditioner TRSM, Gram (SYRK), TRSM, reconstruction: rows*k^2 FLOPs each
+                // (summed over the loop, 2 b n^2); + Cholesky, T (k^3/3 each) and R11 (2 k^2 w)
+                pr.flops(P_PANEL, 4.0 * r * kk * kk + kk * kk * kk * (1.0 / 3.0 + 1.0 / 3.0) + 2.0 * kk * kk * w);
             }
             if (k <= 0) { ell = s; break; }
             // ---- trailing update with the block reflector (I - Y T Y^T)^T

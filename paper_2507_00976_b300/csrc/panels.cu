@@ -58,7 +58,7 @@ constexpr int kMaxSmemHh = 185 * 1024;   // dynamic part; static use is ~35 KB
 // division ~640.  The search therefore compares |x| as integers (the bit
 // patterns of non-negative doubles order like their values), and the
 // multipliers use one reciprocal of the pivot, formed by a single warp while
-// the pivot row is in flight: l = x * (1/piv) (within an ulp of GETRF's x/piv).
+// the pivot row is in flight, plus one FMA correction (the quotient x/piv).
 struct LuArgs {
     i64 N, jb, ldsk;
     int pw, steps, R, Rp;
@@ -84,6 +84,11 @@ __device__ inline unsigned long long ld_relaxed_u64(const unsigned long long* p)
 __device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
+// Release / acquire fence at GPU scope: with the relaxed slot stores and loads
+// it forms the PTX release and acquire patterns (a sequentially consistent
+// fence is not needed for a publish/observe exchange).
+__device__ inline void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // A pivot candidate: key = bits of |x|, row t.  "No candidate" is {0, kNoRow},
 // which loses to every row.  (A NaN's key exceeds every finite one; the
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
             unsigned long long vb = 0;   // signed candidate value (+0 for "no candidate")
             if (b.t != kNoRow) vb = (unsigned long long)__double_as_longlong(slab[k * Rp + (int)(b.t - t0)]);
             if (vb == kSlotEmpty) vb = 0xfff8000000000000ull;   // that NaN pattern marks an empty slot
-            __threadfence();
+            fence_acq_rel_gpu();
             unsigned long long* s = a.slot + ((size_t)buf * G + g) * 2;
             st_relaxed_u64(s, vb);
             st_relaxed_u64(s + 1, (unsigned long long)b.t);
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                 }
             }
             // acquire side of the slots' publication: each lane fences after its own polls
-            __threadfence();
+            fence_acq_rel_gpu();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const Cand y = shfl_down_cand(w, o);
@@ -245,14 +250,19 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         }
         if (tid == 64 && elim) s_rpiv = 1.0 / __longlong_as_double((long long)s_pivbits);
         __syncthreads();
-        // (3) multipliers and column j+1 of the owned rows below jg; next candidate
-        const double rpiv = s_rpiv;
+        // (3) multipliers and column j+1 of the owned rows below jg; next candidate.
+        // l = x / piv from the reciprocal with one FMA correction (Markstein's
+        // quotient refinement: r = x - piv*l is exact, l + r/piv rounds to x/piv),
+        // so equal rows still cancel exactly as in GETRF.
+        const double rpiv = s_rpiv, pivv = __longlong_as_double((long long)s_pivbits);
         const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
         Cand b{0, kNoRow};
         for (int rl = r0 + tid; rl < nloc; rl += NT) {
             double l = 0.0;
             if (elim) {
-                l = slab[j * Rp + rl] * rpiv;
+                const double x = slab[j * Rp + rl];
+                l = x * rpiv;
+                l = fma(fma(-pivv, l, x), rpiv, l);
                 slab[j * Rp + rl] = l;
             }
             if (has_next) {

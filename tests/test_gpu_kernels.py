@@ -123,6 +123,20 @@ def test_qrcp_wide_pivots_bitexact_and_rsk(d, N):
     assert np.linalg.norm(sg[:, None] * R - Ro) <= 1e-12 * np.sqrt(d * N) * np.linalg.norm(Msk0)
 
 
+@pytest.mark.parametrize("d,N", [(40, 300), (64, 130)])
+def test_qrcp_wide_exact_ties_take_the_first_maximum(d, N):
+    # duplicated and negated sketch columns make rows of X = Msk^T tie exactly
+    # in |value|; within one 64-step panel equal rows cancel exactly, so the
+    # oracle's first-maximum choices are unique and must be reproduced
+    Msk0 = W.gaussian(d, N, 77 + d)
+    Msk0[:, N // 2:N // 2 + 40] = Msk0[:, 0:40]
+    Msk0[:, N - 5] = -Msk0[:, 3]
+    Jsk, ipiv = bq.bqrrp_qrcp_wide(dev(Msk0))
+    _, ipiv_o, _ = oracle.lupp(Msk0.T.copy())
+    assert np.array_equal(np_(ipiv), ipiv_o)
+    assert np.array_equal(np_(Jsk), oracle.piv_transform(N, ipiv_o))
+
+
 def test_qrcp_wide_nonfinite_sketch_gives_identity_pivots():
     Msk0 = W.gaussian(20, 50, 1)
     Msk0[3, 7] = np.inf
