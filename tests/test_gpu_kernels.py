@@ -146,7 +146,7 @@ def test_qrcp_wide_nonfinite_sketch_gives_identity_pivots():
 
 # ------------------------------------------------------------- Alg. 5 (col_perm)
 @pytest.mark.parametrize("m,N,moves", [(1000, 300, "perm"), (4097, 64, "perm"), (3, 500, "swaps"),
-                                       (128, 40, "none"), (1, 7, "perm")])
+                                       (128, 40, "none"), (1, 7, "perm"), (8192 + 1000, 96, "perm")])
 def test_col_perm_bitexact(m, N, moves):
     rng = np.random.default_rng(m + N)
     M = rng.standard_normal((m, N))
