@@ -126,13 +126,16 @@ __global__ void sort_rows_kernel(i64 d, const int* ptr, int* col, double* val) {
     }
 }
 
-constexpr int SJ = 4;        // columns of A per CTA
-constexpr int SI = 2048;     // rows of A per staged chunk
+constexpr int SJ = 8;        // columns of A per CTA (each CSR entry feeds SJ FMAs)
+constexpr int SI = 1024;     // rows of A per staged chunk
 
 // Msk(r, j) = sum over the CSR entries (i, s) of row r, in increasing i, of s*A(i, j).
-__global__ void __launch_bounds__(256) sparse_apply_kernel(i64 d, i64 m, i64 n, const double* __restrict__ A, i64 lda,
-                                                           const int* __restrict__ ptr, const int* __restrict__ col,
-                                                           const double* __restrict__ val, double* Msk, i64 ldsk) {
+// One thread per sketch row r (the block is sized to d, so every row is served
+// in a single pass); the CTA's SJ columns of A are staged in SI-row chunks.
+__global__ void __launch_bounds__(1024) sparse_apply_kernel(i64 d, i64 m, i64 n, const double* __restrict__ A,
+                                                            i64 lda, const int* __restrict__ ptr,
+                                                            const int* __restrict__ col, const double* __restrict__ val,
+                                                            double* Msk, i64 ldsk) {
     extern __shared__ double sm[];
     double* As = sm;                                  // [SJ][SI]
     double* acc = sm + SJ * SI;                       // [d][SJ]
@@ -154,18 +157,19 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(i64 d, i64 m, i64 n, 
         for (i64 r = threadIdx.x; r < d; r += blockDim.x) {
             int e = cur[r];
             const int end = ptr[r + 1];
-            double a0 = acc[r * SJ + 0], a1 = acc[r * SJ + 1], a2 = acc[r * SJ + 2], a3 = acc[r * SJ + 3];
+            double a[SJ];
+#pragma unroll
+            for (int q = 0; q < SJ; ++q) a[q] = acc[r * SJ + q];
             while (e < end && col[e] < i0 + ni) {
                 const int i = (int)(col[e] - i0);
-                const double s = val[e];
-                a0 = fma(s, As[0 * SI + i], a0);
-                a1 = fma(s, As[1 * SI + i], a1);
-                a2 = fma(s, As[2 * SI + i], a2);
-                a3 = fma(s, As[3 * SI + i], a3);
+                const double sv = val[e];
+#pragma unroll
+                for (int q = 0; q < SJ; ++q) a[q] = fma(sv, As[q * SI + i], a[q]);
                 ++e;
             }
             cur[r] = e;
-            acc[r * SJ + 0] = a0; acc[r * SJ + 1] = a1; acc[r * SJ + 2] = a2; acc[r * SJ + 3] = a3;
+#pragma unroll
+            for (int q = 0; q < SJ; ++q) acc[r * SJ + q] = a[q];
         }
     }
     __syncthreads();
@@ -259,8 +263,9 @@ int sketch_sparse_apply(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, i64 nn
     std::call_once(attr_once, [&] {
         cudaFuncSetAttribute(sparse_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     });
-    sparse_apply_kernel<<<(unsigned)cdiv(n, SJ), 256, smem, c.stream>>>(d, m, n, A, lda, w.ptr, w.col, w.val, Msk,
-                                                                         ldsk);
+    const int threads = (int)imin(1024, cdiv(d, 32) * 32);
+    sparse_apply_kernel<<<(unsigned)cdiv(n, SJ), threads, smem, c.stream>>>(d, m, n, A, lda, w.ptr, w.col, w.val,
+                                                                             Msk, ldsk);
     BQ_LAUNCH_CHECK();
     return 0;
 }
