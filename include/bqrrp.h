@@ -178,6 +178,21 @@ int bqrrp_qrcp_wide(int64_t d, int64_t N, double* Msk, int64_t ldsk, int64_t* Js
                     void* workspace, size_t workspace_bytes, void* stream);
 size_t bqrrp_qrcp_wide_workspace(int64_t d, int64_t N);
 
+/* bqrrp_selftest_lu_wait_timeout -- failure-detection self-test of the pivot
+ * exchange of Alg. 2's LU (the cross-CTA waits of bqrrp_qrcp_wide and
+ * bqrrp_factor).  Two runs on a copy of Msk (d x N, column-major, ld ldsk,
+ * device, read only): first, one CTA of the first LU panel withholds its
+ * step-0 candidate, so every bounded wait of that launch runs out (2^12 polls,
+ * a few milliseconds) and the status word must report the timeout; then the
+ * same LU runs normally in the same CUDA context.  ipiv (device, min(N, d)
+ * int64) receives the second run's 0-based swap sequence.  workspace: at
+ * least bqrrp_qrcp_wide_workspace(d, N) device bytes.  Returns 0 when the
+ * forced wait was reported and the second run completed; BQRRP_ECUDA if the
+ * forced wait was not reported; the second run's status otherwise; -i for a
+ * bad argument i.  No kernel faults or hangs: every wait is bounded. */
+int bqrrp_selftest_lu_wait_timeout(int64_t d, int64_t N, const double* Msk, int64_t ldsk, int64_t* ipiv,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+
 /*
  * bqrrp_col_perm -- column permutation of Alg. 5 in place: afterwards column t
  * of M (m x N, ld ldm) is the former column J[t] (0-based J, a permutation of

@@ -87,6 +87,7 @@ _SIGS = {
     "bqrrp_sketch_apply_sparse_noalloc": ([_i64, _i64, _i64, _vp, _i64, _u64, _i64, _vp, _i64, _vp], ctypes.c_int),
     "bqrrp_qrcp_wide": ([_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_qrcp_wide_workspace": ([_i64, _i64], _sz),
+    "bqrrp_selftest_lu_wait_timeout": ([_i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_col_perm": ([_i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_col_perm_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_cholqr_panel": ([_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, ctypes.POINTER(_i64), _vp, _sz,
@@ -304,6 +305,18 @@ def bqrrp_qrcp_wide(Msk, stream=None):
                                _stream(stream))
     _check("bqrrp_qrcp_wide", rc)
     return Jsk[:N], ipiv[: min(N, d)]
+
+
+def bqrrp_selftest_lu_wait_timeout(Msk, stream=None):
+    """Failure-detection self-test of the LU pivot exchange (see include/bqrrp.h).
+    Returns (status, ipiv of the normal second run)."""
+    torch = _torch()
+    d, N = Msk.shape
+    ipiv = torch.empty(max(min(N, d), 1), dtype=torch.int64, device=Msk.device)
+    ws = _workspace(lib().bqrrp_qrcp_wide_workspace(d, N), Msk.device)
+    rc = lib().bqrrp_selftest_lu_wait_timeout(d, N, _ptr(Msk), _ld(Msk), _ptr(ipiv), _ptr(ws), ws.numel(),
+                                              _stream(stream))
+    return rc, ipiv[: min(N, d)]
 
 
 def bqrrp_col_perm(M, J, max_moved=None, stream=None):

@@ -135,6 +135,43 @@ int bqrrp_qrcp_wide(int64_t d, int64_t N, double* Msk, int64_t ldsk, int64_t* Js
     return finish(c);
 }
 
+// Failure-detection self-test of the pivot exchange (see the header).
+int bqrrp_selftest_lu_wait_timeout(int64_t d, int64_t N, const double* Msk, int64_t ldsk, int64_t* ipiv,
+                                   void* workspace, size_t workspace_bytes, void* stream) {
+    set_error("");
+    if (d < 1) return -1;
+    if (N < 1) return -2;
+    if (!Msk) return -3;
+    if (ldsk < d) return -4;
+    if (!ipiv) return -5;
+    if (workspace_bytes < bqrrp_qrcp_wide_workspace(d, N)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    Arena ar;
+    Ctx c{};
+    BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false));
+    QrcpWs q{};
+    carve_qrcp(ar, d, N, &q);
+    if (!ar.ok()) { set_error("workspace too small"); return BQRRP_ENOMEM; }
+    // 1: CTA 0 of the first panel withholds its step-0 candidate; every wait is
+    // bounded by 2^12 polls (a few ms), so the launch ends with the timeout flag set
+    init_status_small<<<1, 1, 0, c.stream>>>(c.st);
+    BQ_LAUNCH_CHECK();
+    BQ_CUDA(cudaMemcpy2DAsync(q.X, sizeof(double) * d, Msk, sizeof(double) * ldsk, sizeof(double) * d, N,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    BQ_TRY(getrf_pivots_ex(c, N, d, q.X, d, ipiv, 1ull << 12, 0));
+    const int forced = finish(c);
+    if (forced != BQRRP_ETIMEOUT) {
+        set_error("the withheld candidate did not make the exchange time out (status %d)", forced);
+        return BQRRP_ECUDA;
+    }
+    // 2: the same LU without the stall, in the same context, must complete
+    init_status_small<<<1, 1, 0, c.stream>>>(c.st);
+    BQ_LAUNCH_CHECK();
+    BQ_CUDA(cudaMemcpy2DAsync(q.X, sizeof(double) * d, Msk, sizeof(double) * ldsk, sizeof(double) * d, N,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    BQ_TRY(getrf_pivots(c, N, d, q.X, d, ipiv));
+    return finish(c);
+}
+
 size_t bqrrp_col_perm_workspace(int64_t m, int64_t N, int64_t max_moved) {
     if (m < 0 || N < 0) return 0;
     const i64 mm = imax(1, imin(N, max_moved));

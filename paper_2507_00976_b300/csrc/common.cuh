@@ -257,6 +257,8 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
 
 // panels.cu
 int getrf_pivots(const Ctx& c, i64 N, i64 d, double* X, i64 ldx, i64* ipiv); // LUPP in Sk layout
+int getrf_pivots_ex(const Ctx& c, i64 N, i64 d, double* X, i64 ldx, i64* ipiv, unsigned long long poll_limit,
+                    int stall_cta);
 int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* tau, double* V,
                   double* T, double* W, double* W2, i64 nb, i64 kstop = -1);
 int coop_scratch_elems(i64 nb, int grid, size_t* elems);

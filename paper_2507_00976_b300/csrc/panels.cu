@@ -68,6 +68,8 @@ struct LuArgs {
     unsigned long long* slot;   // [3][G][2], all-ones before the launch
     double* cand_row;           // [3][G][pw]
     double* cur_row;            // [3][pw]
+    unsigned long long poll_limit;   // polls per slot wait before giving up
+    int stall_cta;                   // diagnostics: this CTA never publishes step 0 (-1: none)
 };
 
 constexpr unsigned long long kSlotEmpty = ~0ull;
@@ -142,6 +144,10 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         const int c = e % pw, rl = e / pw;
         slab[c * Rp + rl] = a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
     }
+    // identity pivots first: a panel that gives up on the exchange (timeout)
+    // leaves in-range, no-op interchanges for the kernels that follow it
+    if (g == 0)
+        for (int t = tid; t < a.steps; t += NT) a.ipiv[a.jb + t] = a.jb + t;
     __syncthreads();
 
     // Publish the candidate for pivot step k = j + 1 (j = -1: the first step).
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         Cand b{0, kNoRow};
         for (int rl = tid; rl < nloc; rl += NT) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
         b = block_best_all(b, wk, wt);
-        publish(-1, false, b);
+        if (g != a.stall_cta) publish(-1, false, b);   // a stalled CTA leaves its slot empty
     }
 
     for (int j = 0; j < a.steps; ++j) {
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                 // warp-uniform exit: the poll count is the same in every lane and the
                 // error flag is voted on
                 ++polls;
-                if (polls > kPollLimit ||
+                if (polls > a.poll_limit ||
                     ((polls & 1023) == 0 &&
                      __any_sync(0xffffffffu, *((volatile int*)&a.st->err_timeout) != 0))) {
                     ok = 0;
@@ -743,6 +749,14 @@ static int launch_coop(const Ctx& c, const void* kernel, int grid, size_t smem, 
 // ldsk, all min(N, d) steps; writes the 0-based swap sequence to ipiv.  Sk is
 // overwritten by the factors (in transposed layout).
 int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
+    return getrf_pivots_ex(c, N, d, Sk, ldsk, ipiv, kPollLimit, -1);
+}
+
+// poll_limit bounds every slot wait of the pivot exchange; stall_cta >= 0 makes
+// that CTA of the first panel withhold its step-0 candidate, so every wait of
+// that launch runs out (the failure-detection self-test).
+int getrf_pivots_ex(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv, unsigned long long poll_limit,
+                    int stall_cta) {
     const i64 steps = imin(N, d);
     if (steps <= 0) return 0;
     static std::once_flag attr_set_once;
@@ -785,6 +799,8 @@ int getrf_pivots(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv) {
         a.slot = reinterpret_cast<unsigned long long*>(c.coop);
         a.cand_row = c.coop + 6 * (size_t)G;
         a.cur_row = c.coop + 6 * (size_t)G + 3 * (size_t)G * pw;
+        a.poll_limit = poll_limit;
+        a.stall_cta = (jb == 0 && stall_cta < G) ? stall_cta : -1;
         // every slot starts unpublished (all-ones) in each launch
         BQ_CUDA(cudaMemsetAsync(a.slot, 0xff, 6 * (size_t)G * sizeof(unsigned long long), c.stream));
         BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));

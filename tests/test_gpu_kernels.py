@@ -14,6 +14,7 @@ import torch
 import oracle
 import paper_2507_00976_b300 as bq
 from gpu_util import np_
+from paper_2507_00976_b300 import binding as B
 from paper_2507_00976_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -135,6 +136,20 @@ def test_qrcp_wide_exact_ties_take_the_first_maximum(d, N):
     _, ipiv_o, _ = oracle.lupp(Msk0.T.copy())
     assert np.array_equal(np_(ipiv), ipiv_o)
     assert np.array_equal(np_(Jsk), oracle.piv_transform(N, ipiv_o))
+
+
+def test_lu_exchange_wait_times_out_and_context_stays_usable():
+    # one CTA withholds its first candidate, so every bounded wait of that LU
+    # launch runs out (a flag nothing sets); the status must say so, and the
+    # same LU must then complete in the same context with the oracle's pivots
+    Msk0 = W.gaussian(64, 4096, 5)
+    rc, ipiv = B.bqrrp_selftest_lu_wait_timeout(dev(Msk0))
+    assert rc == 0, B.last_error()
+    _, ipiv_o, margin = oracle.lupp(Msk0.T.copy())
+    assert margin > 1e-9
+    assert np.array_equal(np_(ipiv), ipiv_o)
+    _, ipiv2 = bq.bqrrp_qrcp_wide(dev(Msk0))
+    assert np.array_equal(np_(ipiv2), ipiv_o)
 
 
 def test_qrcp_wide_nonfinite_sketch_gives_identity_pivots():
