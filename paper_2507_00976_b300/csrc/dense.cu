@@ -2,8 +2,9 @@
 //
 // Every O(b^3) step of the panel (Alg. 3) is cast as a right-looking blocked
 // algorithm: a 64-wide diagonal block handled by one CTA in shared memory (or,
-// for triangular solves, one warp per matrix row with the block in shared
-// memory, rows spread over all SMs) plus GEMM updates.  With B300's slow FP64
+// for triangular solves, one warp per matrix row -- four rows per warp for tall
+// blocks -- with the block in shared memory, rows spread over all SMs) plus
+// GEMM updates.  With B300's slow FP64
 // pipe a single SM runs at ~8 GFLOP/s, so nothing of size b^3 may stay on one
 // SM.
 #include <climits>

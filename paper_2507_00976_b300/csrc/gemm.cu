@@ -5,9 +5,10 @@
 // dense contraction in BQRRP, so this kernel only has to keep that pipe fed:
 // 64x64 output tiles, 16-deep K slabs staged through shared memory with a
 // register double buffer, 4x4 outputs per thread.  Operand traffic per DFMA is
-// tiny, so occupancy and load balance across the 148 SMs are what matter;
-// small-output / long-K products use a deterministic split-K (partials in the
-// workspace, reduced in a fixed order).
+// tiny, so occupancy and load balance across the 148 SMs are what matter:
+// products whose tiles would load the SMs unevenly use a deterministic split-K
+// (partials in the workspace, reduced in a fixed order), with the split count
+// chosen to even out the FP64 work per SM.
 //
 // The same kernel, with the A operand generated from Philox4x32-10 instead of
 // loaded, forms the sketch S*A of Alg. 1 without ever storing S.

@@ -4,16 +4,19 @@
 //  * lu_panel_kernel: one nb-wide panel of the row-pivoted LU that Alg. 2
 //    runs on the transposed sketch.  X = Sk^T is never formed: a row of X is a
 //    column of the sketch buffer Sk (d x N, column-major), so each CTA keeps a
-//    contiguous slab of X rows (= sketch columns) of the panel in shared memory
-//    and one grid barrier per pivot step exchanges the per-CTA argmax
-//    candidates (first maximum, as GETRF/IDAMAX).
+//    contiguous slab of X rows (= sketch columns) of the panel in shared memory;
+//    per pivot step the CTAs exchange their argmax candidates (first maximum,
+//    as GETRF/IDAMAX) through published slots, without a grid barrier.
 //  * hh_panel_kernel: Householder QR (dlarfg convention) of a tall panel,
 //    rows split across CTAs, two grid barriers per column (norm, then the
 //    reflector's dot products), then the compact-WY factor T of the panel
 //    (LAPACK larft recurrence from V^T V).
+//  * small_qr_cluster_kernel: the R factor of the d x d factor of the sketch's
+//    LU on one thread-block cluster (distributed shared memory).
 //
-// Both are launched cooperatively so that all CTAs are co-resident; every
-// barrier wait is bounded (see grid_barrier).
+// The grid-wide kernels are launched cooperatively so that all CTAs are
+// co-resident; every cross-CTA wait is bounded (grid_barrier, the LU's slot
+// polls).
 #include <cooperative_groups.h>
 
 #include <climits>
