@@ -11,17 +11,19 @@
 // Requests are admitted first-come-first-served whenever their state fits in
 // the request arena (a coalescing first-fit free list).
 //
-// Two lanes run concurrently, each with its own worker thread, CUDA stream and
-// half of the workspace arena:
-//  - small lane (m*n <= small_max_elems): every admitted small request is
-//    factored in one batched call (the lock-step batched kernels, whose short
-//    launches interleave with the large lane, addressing each request's state
-//    in place through per-matrix offsets).  Requests that arrive meanwhile join
-//    the next batch (continuous batching);
-//  - large lane: one admitted large request at a time, through the
-//    single-matrix path.
-// The batched kernels never wait on other work, so the single-matrix path's
-// grid-wide barriers always complete while both lanes share the GPU.
+// Three workers run concurrently, each with its own thread, CUDA stream and
+// third of the workspace arena:
+//  - small lane (m*n <= small_max_elems), one worker: every admitted small
+//    request is factored in one batched call (the lock-step batched kernels,
+//    whose short launches interleave with the large lane, addressing each
+//    request's state in place through per-matrix offsets).  Requests that
+//    arrive meanwhile join the next batch (continuous batching);
+//  - large lane, two workers: each admits one large request at a time (first
+//    come, first served) and runs it through the single-matrix path, so two
+//    large factorizations overlap and fill each other's latency-bound steps
+//    (the sketch's LU and QR, the small panel kernels).
+// The batched kernels never wait on other work, and every cross-CTA wait of the
+// single-matrix path is bounded, so the lanes can share the GPU.
 //
 // Every request also gets its truncation rank: the smallest t with
 // ||R(t:rank, t:n)||_F <= tol ||A||_F.  Timestamps (submit, admit, start, done)
@@ -160,39 +162,41 @@ struct Server {
     double dry_gflops = 1000.0;
     bool dry = false;
     int device = 0;
-    char* base = nullptr;           // request arena, then workspace arena
-    char* wsbase[2] = {nullptr, nullptr};   // per lane: half of the workspace arena
+    static constexpr int kWorkers = 3;          // 0: small lane; 1, 2: large lane
+    char* base = nullptr;                         // request arena, then workspace arena
+    char* wsbase[kWorkers] = {nullptr, nullptr, nullptr};   // per worker: a third of the workspace arena
     size_t lane_ws = 0;
     FreeList arena{0};
-    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaStream_t st[kWorkers] = {nullptr, nullptr, nullptr};
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv, cv_done;
     std::deque<Req*> pending;       // submitted, waiting for admission
     std::vector<Req*> ready_small;  // admitted
-    std::deque<Req*> ready_large;
     std::deque<bqrrp_completion> done;
     std::atomic<bool> stop{false};
     i64 submitted = 0, completed = 0, batches = 0, max_batch = 0, larges = 0;
     char last_err[512] = {0};       // message of the last failed job (worker thread)
     size_t peak = 0;
-    std::thread worker[2];
+    std::thread worker[kWorkers];
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
-    void run(int lane);
-    int admit_locked(int lane, std::vector<Req*>& newly);
+    void run_small();
+    void run_large(int wk);
+    int admit_locked(int lane, std::vector<Req*>& newly, size_t max_new);
     int do_small(std::vector<Req*>& batch);
-    int do_large(Req* q);
+    int do_large(Req* q, int wk);
     void finish(std::vector<Req*>& reqs, int status);
 };
 
 size_t request_state_bytes(i64 m, i64 n) { return up((size_t)m * n * 8) + up((size_t)n * 8) * 2; }
 
-// Admit, in submission order, this lane's pending requests that fit.
-int Server::admit_locked(int lane, std::vector<Req*>& newly) {
-    for (auto it = pending.begin(); it != pending.end();) {
+// Admit, in submission order, up to max_new of this lane's pending requests
+// that fit.
+int Server::admit_locked(int lane, std::vector<Req*>& newly, size_t max_new) {
+    for (auto it = pending.begin(); it != pending.end() && newly.size() < max_new;) {
         Req* q = *it;
         size_t off;
         if (q->c.lane == lane && arena.alloc(q->bytes, &off)) {
@@ -303,7 +307,7 @@ int Server::do_small(std::vector<Req*>& batch) {
 }
 
 // One large request through the single-matrix path.
-int Server::do_large(Req* q) {
+int Server::do_large(Req* q, int wk) {
     q->c.t_start = now();
     const i64 m = q->r.m, n = q->r.n;
     if (dry) {
@@ -315,57 +319,56 @@ int Server::do_large(Req* q) {
     double* A = (double*)(base + q->offA);
     int64_t* J = (int64_t*)(base + q->offJ);
     double* tau = (double*)(base + q->offT);
-    char* w = wsbase[1];
+    char* w = wsbase[wk];
     double* part = (double*)w;   w += up(sizeof(double) * kNormParts);
     double* rn = (double*)w;     w += up(sizeof(double) * (size_t)std::max<i64>(n, 1));
     int64_t* trd = (int64_t*)w;  w += up(sizeof(int64_t));
-    const size_t have = lane_ws - (size_t)(w - wsbase[1]);
+    const size_t have = lane_ws - (size_t)(w - wsbase[wk]);
     const size_t need = bqrrp_workspace_query(m, n, q->r.b, q->r.d, nullptr);
     if (need > have) {
         set_error("large request needs %zu workspace bytes, the arena has %zu", need, have);
         return BQRRP_ENOMEM;
     }
-    norm_partial_kernel<<<kNormParts, 256, 0, st[1]>>>(A, m * n, part);
+    norm_partial_kernel<<<kNormParts, 256, 0, st[wk]>>>(A, m * n, part);
     BQ_LAUNCH_CHECK();
     int64_t rank = 0;
-    int rc = bqrrp_factor(m, n, A, m, q->r.b, q->r.d, q->r.seed, J, tau, &rank, nullptr, w, have, st[1]);
+    int rc = bqrrp_factor(m, n, A, m, q->r.b, q->r.d, q->r.seed, J, tau, &rank, nullptr, w, have, st[wk]);
     if (rc != 0) return rc;
     if (rank > 0) {
-        rownorm_kernel<<<(unsigned)cdiv(rank, 128), 128, 0, st[1]>>>(A, m, n, rank, rn);
+        rownorm_kernel<<<(unsigned)cdiv(rank, 128), 128, 0, st[wk]>>>(A, m, n, rank, rn);
         BQ_LAUNCH_CHECK();
     }
-    trunc_final_kernel<<<1, 32, 0, st[1]>>>(part, kNormParts, rn, rank, tol, trd);
+    trunc_final_kernel<<<1, 32, 0, st[wk]>>>(part, kNormParts, rn, rank, tol, trd);
     BQ_LAUNCH_CHECK();
     int64_t htr = 0;
-    cudaMemcpyAsync(&htr, trd, sizeof(int64_t), cudaMemcpyDeviceToHost, st[1]);
-    if (q->r.A_out_host) cudaMemcpyAsync(q->r.A_out_host, A, (size_t)m * n * 8, cudaMemcpyDeviceToHost, st[1]);
-    if (q->r.jpvt_out_host) cudaMemcpyAsync(q->r.jpvt_out_host, J, (size_t)n * 8, cudaMemcpyDeviceToHost, st[1]);
-    if (q->r.tau_out_host) cudaMemcpyAsync(q->r.tau_out_host, tau, (size_t)n * 8, cudaMemcpyDeviceToHost, st[1]);
-    BQ_CUDA(cudaStreamSynchronize(st[1]));
+    cudaMemcpyAsync(&htr, trd, sizeof(int64_t), cudaMemcpyDeviceToHost, st[wk]);
+    if (q->r.A_out_host) cudaMemcpyAsync(q->r.A_out_host, A, (size_t)m * n * 8, cudaMemcpyDeviceToHost, st[wk]);
+    if (q->r.jpvt_out_host) cudaMemcpyAsync(q->r.jpvt_out_host, J, (size_t)n * 8, cudaMemcpyDeviceToHost, st[wk]);
+    if (q->r.tau_out_host) cudaMemcpyAsync(q->r.tau_out_host, tau, (size_t)n * 8, cudaMemcpyDeviceToHost, st[wk]);
+    BQ_CUDA(cudaStreamSynchronize(st[wk]));
     q->c.rank = rank;
     q->c.trunc_rank = htr;
     return 0;
 }
 
-void Server::run(int lane) {
+void Server::run_small() {
     if (!dry) cudaSetDevice(device);
     for (;;) {
         std::vector<Req*> newly, work;
         {
             std::unique_lock<std::mutex> lk(mu);
             auto mine = [&] {
-                if (lane == 0 ? !ready_small.empty() : !ready_large.empty()) return true;
+                if (!ready_small.empty()) return true;
                 for (Req* q : pending)
-                    if (q->c.lane == lane) return true;
+                    if (q->c.lane == 0) return true;
                 return false;
             };
             cv.wait(lk, [&] { return stop.load() || mine(); });
-            admit_locked(lane, newly);
-            const bool idle = (lane == 0 ? ready_small.empty() : ready_large.empty()) && newly.empty();
-            if (idle) {
+            admit_locked(0, newly, (size_t)-1);
+            if (ready_small.empty() && newly.empty()) {
                 bool waiting = false;
                 for (Req* q : pending)
-                    if (q->c.lane == lane) waiting = true;
+                    if (q->c.lane == 0) waiting = true;
                 if (stop.load() && !waiting) break;
                 // this lane's requests do not fit yet: wait for a completion
                 cv.wait_for(lk, std::chrono::milliseconds(1));
@@ -376,30 +379,54 @@ void Server::run(int lane) {
         for (Req* q : newly) {
             if (!dry)
                 cudaMemcpyAsync(base + q->offA, q->r.A_host, (size_t)q->r.m * q->r.n * 8, cudaMemcpyHostToDevice,
-                                st[lane]);
+                                st[0]);
             std::lock_guard<std::mutex> lk(mu);
-            if (lane == 0) ready_small.push_back(q);
-            else ready_large.push_back(q);
+            ready_small.push_back(q);
         }
         {
             std::lock_guard<std::mutex> lk(mu);
-            if (lane == 0) {
-                work.swap(ready_small);
-            } else if (!ready_large.empty()) {
-                work.push_back(ready_large.front());
-                ready_large.pop_front();
-            }
+            work.swap(ready_small);
         }
         if (work.empty()) continue;
-        const int rc = (lane == 0) ? do_small(work) : do_large(work[0]);
+        const int rc = do_small(work);
         {
             std::lock_guard<std::mutex> lk(mu);
-            if (lane == 0) {
-                ++batches;
-                max_batch = std::max<i64>(max_batch, (i64)work.size());
-            } else {
-                ++larges;
+            ++batches;
+            max_batch = std::max<i64>(max_batch, (i64)work.size());
+        }
+        finish(work, rc);
+    }
+}
+
+// A large-lane worker: admits one large request when it fits, copies it in on
+// its own stream and factors it there.
+void Server::run_large(int wk) {
+    if (!dry) cudaSetDevice(device);
+    for (;;) {
+        std::vector<Req*> work;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            auto mine = [&] {
+                for (Req* q : pending)
+                    if (q->c.lane == 1) return true;
+                return false;
+            };
+            cv.wait(lk, [&] { return stop.load() || mine(); });
+            admit_locked(1, work, 1);
+            if (work.empty()) {
+                if (stop.load() && !mine()) break;
+                // no large request fits yet: wait for a completion
+                cv.wait_for(lk, std::chrono::milliseconds(1));
+                continue;
             }
+        }
+        Req* q = work[0];
+        if (!dry)
+            cudaMemcpyAsync(base + q->offA, q->r.A_host, (size_t)q->r.m * q->r.n * 8, cudaMemcpyHostToDevice, st[wk]);
+        const int rc = do_large(q, wk);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            ++larges;
         }
         finish(work, rc);
     }
@@ -428,7 +455,7 @@ int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t works
     bq::Server& S = h->s;
     S.budget = hbm_budget_bytes & ~(bq::kAlign - 1);
     S.ws_bytes = bq::up(workspace_bytes);
-    S.lane_ws = (S.ws_bytes / 2) & ~(bq::kAlign - 1);
+    S.lane_ws = (S.ws_bytes / bq::Server::kWorkers) & ~(bq::kAlign - 1);
     S.tol = trunc_tol;
     S.small_max = small_max_elems;
     S.flags = flags;
@@ -448,9 +475,10 @@ int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t works
             return BQRRP_ENOMEM;
         }
         S.wsbase[0] = S.base + (S.budget - S.ws_bytes);
-        S.wsbase[1] = S.wsbase[0] + S.lane_ws;
-        e = cudaStreamCreateWithFlags(&S.st[0], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.st[1], cudaStreamNonBlocking);
+        for (int k = 1; k < bq::Server::kWorkers; ++k) S.wsbase[k] = S.wsbase[k - 1] + S.lane_ws;
+        e = cudaSuccess;
+        for (int k = 0; k < bq::Server::kWorkers && e == cudaSuccess; ++k)
+            e = cudaStreamCreateWithFlags(&S.st[k], cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             cudaFree(S.base);
             bq::set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
@@ -458,8 +486,8 @@ int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t works
             return BQRRP_ECUDA;
         }
     }
-    S.worker[0] = std::thread([&S] { S.run(0); });
-    S.worker[1] = std::thread([&S] { S.run(1); });
+    S.worker[0] = std::thread([&S] { S.run_small(); });
+    for (int k = 1; k < bq::Server::kWorkers; ++k) S.worker[k] = std::thread([&S, k] { S.run_large(k); });
     *out = h;
     return 0;
 }
@@ -559,7 +587,6 @@ void bqrrp_server_destroy(bqrrp_server srv) {
     }
     for (auto* q : S.pending) delete q;
     for (auto* q : S.ready_small) delete q;
-    for (auto* q : S.ready_large) delete q;
     delete srv;
 }
 
