@@ -1051,6 +1051,16 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
                 Yc[rr * kb + i] = (rr < nr && i < k) ? V[(r0 + rr) + (i64)i * m] : 0.0;
             }
             __syncthreads();
+            // this thread's 4 x 4 block of C, loaded before the k loop so that the
+            // global-load latency overlaps the FMAs
+            double cpre[4][4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int col = 4 * jb + v;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    cpre[u][v] = (col < nc && 4 * rb + u < nr) ? C[(r0 + 4 * rb + u) + (i64)col * m] : 0.0;
+            }
             double u4[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -1073,7 +1083,7 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
                 if (col < nc)
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        if (4 * rb + u < nr) C[(r0 + 4 * rb + u) + (i64)col * m] -= u4[u][v];
+                        if (4 * rb + u < nr) C[(r0 + 4 * rb + u) + (i64)col * m] = cpre[u][v] - u4[u][v];
             }
         }
     }
