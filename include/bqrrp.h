@@ -36,7 +36,7 @@ extern "C" {
 #define BQRRP_ENOMEM 1      /* workspace smaller than bqrrp_workspace_query() */
 #define BQRRP_ECUDA 2       /* a CUDA runtime call failed                      */
 #define BQRRP_ENUMERIC 3    /* A holds NaN or Inf                              */
-#define BQRRP_ETIMEOUT 4    /* a grid-wide barrier gave up waiting             */
+#define BQRRP_ETIMEOUT 4    /* a bounded cross-CTA wait gave up                */
 #define BQRRP_EUNSUPPORTED 5 /* shape outside the supported range             */
 
 /* Sketching operator kinds (Alg. 1 sample step, Sec. 3.2). */

@@ -52,7 +52,7 @@ int finish(const Ctx& c) {
     DevStatus hs{};
     BQ_CUDA(cudaMemcpyAsync(&hs, c.st, sizeof(hs), cudaMemcpyDeviceToHost, c.stream));
     BQ_CUDA(cudaStreamSynchronize(c.stream));
-    if (hs.err_timeout) { set_error("a grid-wide barrier timed out"); return BQRRP_ETIMEOUT; }
+    if (hs.err_timeout) { set_error("a bounded cross-CTA wait timed out"); return BQRRP_ETIMEOUT; }
     return 0;
 }
 

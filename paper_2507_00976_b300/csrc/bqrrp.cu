@@ -337,7 +337,7 @@ int read_status(const Ctx& c, DevStatus* host) {
     BQ_CUDA(cudaMemcpyAsync(host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.stream));
     BQ_CUDA(cudaStreamSynchronize(c.stream));
     if (host->err_timeout) {
-        set_error("a grid-wide barrier timed out");
+        set_error("a bounded cross-CTA wait timed out");
         return BQRRP_ETIMEOUT;
     }
     return 0;
