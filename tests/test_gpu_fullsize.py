@@ -42,8 +42,8 @@ def test_full_size_factorization(problem, precision):
     assert rank == N
     j = jpvt.to(torch.int64) - 1
     assert torch.equal(torch.sort(j).values, torch.arange(N, device=j.device))
-    if margin > 1e-9:
-        assert np.array_equal(j[:BLK].cpu().numpy(), J0)
+    assert margin > 1e-9            # every LU step of this input is gapped (2.4e-4)
+    assert np.array_equal(j[:BLK].cpu().numpy(), J0)
     R = torch.triu(F)
     Q = torch.linalg.householder_product(F, tau[:N])
     del F
