@@ -105,9 +105,16 @@ size_t bqrrp_workspace_query(int64_t m, int64_t n, int64_t b, int64_t d, const b
  * bqrrp_factor_host -- the same factorization for HOST buffers: A_host
  * (m x n, ld lda, in/out), jpvt_host (n) and tau_host (n) live in host memory
  * (pinned memory gives full PCIe/C2C bandwidth).  The call copies A to the
- * device, factors it with bqrrp_factor, copies A, jpvt and tau back and
- * synchronizes `stream` before returning.  workspace must hold
- * bqrrp_workspace_query_host() bytes.
+ * device on `stream`, factors it as bqrrp_factor does, copies A, jpvt and tau
+ * back and synchronizes `stream` before returning; the results are bit for bit
+ * those of bqrrp_factor.  When A_host is pinned, each finished column block of
+ * R and the reflectors goes back on a private copy stream while the later
+ * blocks are factored (created and destroyed inside the call, synchronized
+ * before it returns); pageable A_host is copied back once at the end.
+ * workspace is device memory of at least bqrrp_workspace_query_host() bytes
+ * (A, jpvt and tau on the device, then bqrrp_factor's workspace).
+ * Errors: those of bqrrp_factor.  On BQRRP_ENUMERIC A_host is unchanged; on
+ * BQRRP_ETIMEOUT or BQRRP_ECUDA its contents are unspecified.
  */
 int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t b, int64_t d,
                       uint64_t seed, int64_t* jpvt_host, double* tau_host, int64_t* rank,

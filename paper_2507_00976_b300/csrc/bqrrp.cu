@@ -396,8 +396,33 @@ inline double lupp_flops(double N, double d) {      // GETRF on N x d: sum_j (N-
     return f;
 }
 
+// Host buffers of the host entry point.  Every column block goes back to the
+// host on the copy stream as soon as its iteration has finished it, so the
+// copy back overlaps the rest of the factorization: after the iteration on
+// columns [s, c), later iterations permute, update and read only columns >= c.
+struct HostIO {
+    double* A_host;     // out: R and the reflectors (ld lda_host); pinned
+    i64 lda_host;
+    cudaStream_t cs;    // copy stream
+    std::vector<cudaEvent_t>* events;
+    i64 copied = 0;     // columns [0, copied) queued for the copy back
+    // queue the copy back of columns [copied, upto) once the compute stream is past this point
+    int send_back(const Ctx& c, const double* A, i64 m, i64 lda, i64 upto) {
+        if (upto <= copied) return 0;
+        cudaEvent_t ev;
+        BQ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        events->push_back(ev);
+        BQ_CUDA(cudaEventRecord(ev, c.stream));
+        BQ_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+        BQ_CUDA(cudaMemcpy2DAsync(A_host + copied * lda_host, sizeof(double) * lda_host, A + copied * lda,
+                                  sizeof(double) * lda, sizeof(double) * m, upto - copied, cudaMemcpyDeviceToHost, cs));
+        copied = upto;
+        return 0;
+    }
+};
+
 int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i64* jpvt, double* tau, i64* rank,
-                const bqrrp_opts& o, const Bufs& B, Ctx& c, PhaseRec& pr) {
+                const bqrrp_opts& o, const Bufs& B, Ctx& c, PhaseRec& pr, HostIO* io) {
     enum { P_SKETCH = 0, P_LUPP, P_SKQR, P_PERM, P_PANEL, P_TRAIL, P_SKUPD, P_OTHER };
     DevStatus hs{};
     pr.begin(P_OTHER);
@@ -524,8 +549,10 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         BQ_TRY(trsm_ru(c, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
         BQ_TRY(pgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
         pr.flops(P_SKUPD, (double)w * w * w + 2.0 * (double)w * w * nc);
+        if (io) BQ_TRY(io->send_back(c, A, m, lda, cend));   // block [s, cend) is final
     }
     pr.begin(P_OTHER);
+    if (io) BQ_TRY(io->send_back(c, A, m, lda, n));          // the rest, after the last iteration
     plus_one_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c.stream>>>(n, B.J, jpvt);
     BQ_LAUNCH_CHECK();
     BQ_TRY(read_status(c, &hs));
@@ -582,10 +609,14 @@ size_t bqrrp_workspace_query(int64_t m, int64_t n, int64_t b, int64_t d, const b
     return ar.off + 256;
 }
 
-int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_t d, uint64_t seed, int64_t* jpvt,
+}  // extern "C"
+
+namespace bq {
+namespace {
+
+int factor_entry(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_t d, uint64_t seed, int64_t* jpvt,
                  double* tau, int64_t* rank, const bqrrp_opts* opts, void* workspace, size_t workspace_bytes,
-                 void* stream) {
-    set_error("");
+                 void* stream, HostIO* io) {
     if (rank) *rank = -1;
     if (m < 0 || m < n) { set_error("m must satisfy m >= n >= 0"); return -1; }
     if (n < 0) return -2;
@@ -628,12 +659,24 @@ int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_
         pr.on = g_prof.on;
     }
     pr.st = c.stream;
-    const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c, pr);
+    const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c, pr, io);
     if (rc == 0) {
         *rank = r;
         pr.resolve();
     }
     return rc;
+}
+
+}  // namespace
+}  // namespace bq
+
+extern "C" {
+
+int bqrrp_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_t d, uint64_t seed, int64_t* jpvt,
+                 double* tau, int64_t* rank, const bqrrp_opts* opts, void* workspace, size_t workspace_bytes,
+                 void* stream) {
+    set_error("");
+    return factor_entry(m, n, A, lda, b, d, seed, jpvt, tau, rank, opts, workspace, workspace_bytes, stream, nullptr);
 }
 
 size_t bqrrp_workspace_query_host(int64_t m, int64_t n, int64_t b, int64_t d, const bqrrp_opts* opts) {
@@ -672,17 +715,37 @@ int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t
     const size_t rest_bytes = workspace_bytes - (size_t)(rest - (char*)workspace);
     BQ_CUDA(cudaMemcpy2DAsync(dA, sizeof(double) * m, A_host, sizeof(double) * lda, sizeof(double) * m, n,
                               cudaMemcpyHostToDevice, st));
-    int rc = bqrrp_factor(m, n, dA, m, b, d, seed, dj, dt, rank, opts, rest, rest_bytes, stream);
-    if (rc != 0) {
-        cudaStreamSynchronize(st);
-        return rc;
+    // With pinned A_host the finished column blocks go back on a copy stream
+    // while the later blocks are factored; pageable memory (where an
+    // asynchronous copy to the host would block this thread) is copied once
+    // at the end.
+    cudaPointerAttributes pa{};
+    const bool pinned = cudaPointerGetAttributes(&pa, A_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    (void)cudaGetLastError();
+    std::vector<cudaEvent_t> events;
+    HostIO io{A_host, lda, nullptr, &events};
+    if (pinned) BQ_CUDA(cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking));
+    int rc = factor_entry(m, n, dA, m, b, d, seed, dj, dt, rank, opts, rest, rest_bytes, stream,
+                          pinned ? &io : nullptr);
+    if (rc == 0) {
+        if (!pinned) {
+            rc = cudaMemcpy2DAsync(A_host, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+                                   cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : BQRRP_ECUDA;
+        }
+        if (rc == 0 && (cudaMemcpyAsync(jpvt_host, dj, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaMemcpyAsync(tau_host, dt, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+            rc = BQRRP_ECUDA;
     }
-    BQ_CUDA(cudaMemcpy2DAsync(A_host, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
-                              cudaMemcpyDeviceToHost, st));
-    BQ_CUDA(cudaMemcpyAsync(jpvt_host, dj, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
-    BQ_CUDA(cudaMemcpyAsync(tau_host, dt, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    BQ_CUDA(cudaStreamSynchronize(st));
-    return 0;
+    // both streams finish before the events, the copy stream and the call go
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == 0) rc = BQRRP_ECUDA;
+    if (io.cs) {
+        if (cudaStreamSynchronize(io.cs) != cudaSuccess && rc == 0) rc = BQRRP_ECUDA;
+        cudaStreamDestroy(io.cs);
+    }
+    for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+    if (rc == BQRRP_ECUDA) set_error("bqrrp_factor_host: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc != 0 && rank) *rank = -1;
+    return rc;
 }
 
 int bqrrp_sketch_operator(int64_t d, int64_t m, uint64_t seed, int kind, int64_t nnz, double* S, int64_t lds,

@@ -115,7 +115,6 @@ def test_deterministic_and_host_entry_point_identical():
     F2, j2, t2, r2 = run_gpu(A, 100, 125, 9)
     assert np.array_equal(F1, F2) and np.array_equal(j1, j2) and np.array_equal(t1, t2) and r1 == r2
     m, n = A.shape
-    Ah = torch.as_tensor(A).t().contiguous().t().pin_memory() if False else None
     Ah = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
     Ah.copy_(torch.as_tensor(A))
     jh = torch.empty(n, dtype=torch.int64).pin_memory()
@@ -124,6 +123,33 @@ def test_deterministic_and_host_entry_point_identical():
     r3 = B.bqrrp_factor_host(Ah, 100, 125, 9, jh, th, ws)
     assert r3 == r1
     assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("rank_deficient", [False, True])
+def test_host_entry_point_padded_ld(pinned, rank_deficient):
+    """Host buffers with ld > m, pinned (column blocks copied back while later
+    blocks are factored) and pageable (one copy at the end), full rank and with
+    an early stop; the results equal the device entry point's bit for bit and
+    the padding rows are left alone."""
+    m, n, b, d = 1100, 700, 96, 120
+    A = W.low_rank(m, n, 250, 4) if rank_deficient else W.gaussian(m, n, 5)
+    F1, j1, t1, r1 = run_gpu(A, b, d, 17)
+    ld = m + 13
+    buf = torch.full((n, ld), -7.0, dtype=torch.float64)
+    if pinned:
+        buf = buf.pin_memory()
+    Ah = buf.t()[:m]
+    Ah.copy_(torch.as_tensor(A))
+    jh = torch.empty(n, dtype=torch.int64)
+    th = torch.empty(n, dtype=torch.float64)
+    if pinned:
+        jh, th = jh.pin_memory(), th.pin_memory()
+    ws = torch.empty(B.bqrrp_workspace_query_host(m, n, b, d), dtype=torch.uint8, device="cuda")
+    r2 = B.bqrrp_factor_host(Ah, b, d, 17, jh, th, ws)
+    assert r2 == r1 and (r1 < n) == rank_deficient
+    assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
+    assert torch.all(buf[:, m:] == -7.0)
 
 
 def test_error_codes():
