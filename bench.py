@@ -111,6 +111,9 @@ def parse():
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="mixed: sketch and trailing-update products on the bf16 tensor cores (exact slices)")
     p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--schedule", choices=["overlap", "serial"], default="overlap",
+                   help="overlap: the sketch update and the next block's Alg. 2 on a side stream during the "
+                        "trailing update; serial: one stream")
     p.add_argument("--skip-qr", action="store_true", help="do not time the own unpivoted QR")
     p.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer entry point")
     p.add_argument("--skip-cpu", action="store_true", help="do not time the CPU oracle sample")
@@ -145,6 +148,7 @@ def workload_name(a):
 def config(a, world):
     return {"workload": workload_name(a), "m": a.m, "n": a.n, "b": a.b, "d": a.d, "family": a.family,
             "sketch": a.sketch, "panel": a.panel, "precision": a.precision, "seed": a.seed,
+            "schedule": a.schedule if (a.precision == "fp64" and a.panel == "cholqr") else "serial",
             "l2": f"inputs larger than L2 (A is {a.m * a.n * 8 / 1e9:.2f} GB, L2 126 MB)",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -720,7 +724,8 @@ def main():
     tau = torch.empty(n, dtype=torch.float64, device="cuda")
     opts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
                        B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR,
-                       B.PRECISION_FP64 if a.precision == "fp64" else B.PRECISION_MIXED)
+                       B.PRECISION_FP64 if a.precision == "fp64" else B.PRECISION_MIXED,
+                       B.SCHEDULE_OVERLAP if a.schedule == "overlap" else B.SCHEDULE_SERIAL)
     ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     probe = B.bqrrp_probe_fp64_peak(4000)
@@ -857,6 +862,10 @@ def main():
                     "kernel": "dgemm_kernel (FP64 SIMT GEMMs of the trailing block-reflector update)",
                     "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
                     "dfma_probe_tflops": probe}
+        if config(a, world)["schedule"] == "overlap":
+            roofline["note"] = ("overlap schedule: the sketch update and the next block's LU and sketch QR run on a "
+                                "side stream during the trailing update and share its SMs' FP64 pipes; the "
+                                "trailing launches' event times include that sharing")
     cpu = None
     if not a.skip_cpu and world == 1:
         gf, sample, cores = cpu_sample(a)

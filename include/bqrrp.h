@@ -54,12 +54,21 @@ extern "C" {
                                     bqrrp_dgemm_ozaki); LU, sketch QR, panel, tau, R
                                     in FP64                                          */
 
+/* Order of the steps of consecutive blocks (the results are the same bit for bit). */
+#define BQRRP_SCHEDULE_OVERLAP 0 /* the sketch update and Alg. 2 of block i+1 run on a
+                                    high-priority side stream (created per call)
+                                    while rows k.. of block i's trailing update run
+                                    on `stream`; FP64 with the CholQR panel only
+                                    (the other forms run serially)                  */
+#define BQRRP_SCHEDULE_SERIAL 1  /* every step on `stream`, one after the other     */
+
 typedef struct bqrrp_opts {
     int sketch_kind;     /* BQRRP_SKETCH_DENSE (default) or BQRRP_SKETCH_SPARSE */
     int64_t sketch_nnz;  /* nonzeros per column of a sparse sketch (default 8)  */
     int panel_kind;      /* BQRRP_PANEL_CHOLQR (default) or BQRRP_PANEL_HQR    */
     int64_t precision;   /* BQRRP_PRECISION_FP64 (default) or _MIXED            */
-    int64_t reserved[4]; /* must be zero                                        */
+    int64_t schedule;    /* BQRRP_SCHEDULE_OVERLAP (default) or _SERIAL         */
+    int64_t reserved[3]; /* must be zero                                        */
 } bqrrp_opts;
 
 /*

@@ -25,6 +25,7 @@ OK, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 SKETCH_DENSE, SKETCH_SPARSE = 0, 1
 PANEL_CHOLQR, PANEL_HQR = 0, 1
 PRECISION_FP64, PRECISION_MIXED = 0, 1
+SCHEDULE_OVERLAP, SCHEDULE_SERIAL = 0, 1
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -37,7 +38,7 @@ _lib = None
 
 class Opts(ctypes.Structure):
     _fields_ = [("sketch_kind", ctypes.c_int), ("sketch_nnz", _i64), ("panel_kind", ctypes.c_int),
-                ("precision", _i64), ("reserved", _i64 * 4)]
+                ("precision", _i64), ("schedule", _i64), ("reserved", _i64 * 3)]
 
 
 NPHASES = 8
@@ -202,12 +203,14 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
 
 
-def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR, precision=PRECISION_FP64):
+def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR, precision=PRECISION_FP64,
+              schedule=SCHEDULE_OVERLAP):
     o = Opts()
     o.sketch_kind = sketch_kind
     o.sketch_nnz = nnz
     o.panel_kind = panel_kind
     o.precision = precision
+    o.schedule = schedule
     return o
 
 
@@ -441,7 +444,8 @@ def bqrrp_launch_counter():
 
 
 # ----------------------------------------------------------------- convenience
-def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64", stream=None):
+def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64", schedule="overlap",
+           stream=None):
     """Factor a copy of A (any 2-D float64 tensor/array); returns
     (F column-major with R and reflectors, jpvt, tau, rank) as device tensors."""
     torch = _torch()
@@ -451,7 +455,8 @@ def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64
     tau = torch.empty(max(n, 1), dtype=torch.float64, device=F.device)
     opts = make_opts(SKETCH_DENSE if sketch == "dense" else SKETCH_SPARSE, nnz,
                      PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR,
-                     PRECISION_FP64 if precision == "fp64" else PRECISION_MIXED)
+                     PRECISION_FP64 if precision == "fp64" else PRECISION_MIXED,
+                     SCHEDULE_OVERLAP if schedule == "overlap" else SCHEDULE_SERIAL)
     rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
     return F, jpvt[:n], tau[:n], rank
 

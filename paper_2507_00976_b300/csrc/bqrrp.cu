@@ -70,14 +70,19 @@ void profile_add(const double* ms, const double* flops) {
     g_prof.calls += 1;
 }
 
-// Per-call recorder (only active when the profiler is on).
+// Per-call phase timer (active when the profiler is on): CUDA events around
+// each phase, resolved after the call.  With the overlap schedule the phases
+// of the side stream (LU, sketch QR, sketch update: lane 1) are timed on that
+// stream, the others (lane 0) on the caller's stream, and the two lanes'
+// spans overlap in time.
 struct PhaseRec {
     bool on = false;
-    cudaStream_t st = nullptr;
+    bool split = false;                       // two lanes (overlap schedule)
+    cudaStream_t st[2] = {nullptr, nullptr};
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
     double fl[BQRRP_NPHASES] = {0};
-    int cur = -1;
-    cudaEvent_t cur_ev = nullptr;
+    int cur[2] = {-1, -1};
+    cudaEvent_t cur_ev[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> events;   // created per call, destroyed in resolve()
     cudaEvent_t take() {
         cudaEvent_t e = nullptr;
@@ -85,22 +90,28 @@ struct PhaseRec {
         events.push_back(e);
         return e;
     }
+    static int side_phase(int phase) { return phase == 1 || phase == 2 || phase == 6; }   // LUPP, SKQR, SKUPD
     void begin(int phase) {
         if (!on) return;
-        end();
-        cur = phase;
-        cur_ev = take();
-        cudaEventRecord(cur_ev, st);
+        const int l = split ? side_phase(phase) : 0;
+        end_lane(l);
+        cur[l] = phase;
+        cur_ev[l] = take();
+        cudaEventRecord(cur_ev[l], st[l]);
+    }
+    void end_lane(int l) {
+        if (!on || cur[l] < 0) return;
+        cudaEvent_t e = take();
+        cudaEventRecord(e, st[l]);
+        spans.push_back({cur[l], {cur_ev[l], e}});
+        cur[l] = -1;
     }
     void end() {
-        if (!on || cur < 0) return;
-        cudaEvent_t e = take();
-        cudaEventRecord(e, st);
-        spans.push_back({cur, {cur_ev, e}});
-        cur = -1;
+        end_lane(0);
+        end_lane(1);
     }
     void flops(int phase, double f) { if (on) fl[phase] += f; }
-    void resolve() {   // after the stream has been synchronized
+    void resolve() {   // after the streams have been synchronized
         if (!on) return;
         end();
         std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -315,6 +326,7 @@ bqrrp_opts defaults(const bqrrp_opts* o) {
         r.sketch_nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
         r.panel_kind = o->panel_kind;
         r.precision = o->precision;
+        r.schedule = o->schedule;
     }
     return r;
 }
@@ -328,7 +340,8 @@ int check_opts(const bqrrp_opts* o, i64 d) {
         if (nnz > d || nnz > 64) return 1;
     }
     if (o->precision != BQRRP_PRECISION_FP64 && o->precision != BQRRP_PRECISION_MIXED) return 1;
-    for (int i = 0; i < 4; ++i)
+    if (o->schedule != BQRRP_SCHEDULE_OVERLAP && o->schedule != BQRRP_SCHEDULE_SERIAL) return 1;
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return 1;
     return 0;
 }
@@ -421,6 +434,29 @@ struct HostIO {
     }
 };
 
+// The side stream of the overlap schedule: highest priority, non-blocking,
+// created and synchronized per call.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int open() {
+        int least = 0, greatest = 0;
+        BQ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BQ_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest));
+        BQ_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        BQ_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        return 0;
+    }
+    ~SideStream() {
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+    }
+};
+
 int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i64* jpvt, double* tau, i64* rank,
                 const bqrrp_opts& o, const Bufs& B, Ctx& c, PhaseRec& pr, HostIO* io) {
     enum { P_SKETCH = 0, P_LUPP, P_SKQR, P_PERM, P_PANEL, P_TRAIL, P_SKUPD, P_OTHER };
@@ -452,6 +488,69 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         pr.flops(P_SKETCH, 2.0 * (double)o.sketch_nnz * m * n);
     }
 
+    // Schedule (Sec. 3 leaves the order of independent steps open).  Alg. 2 of
+    // the next block needs only the sketch update, and that needs only R11 and
+    // the first k rows of the updated trailing block (R12).  So the trailing
+    // update forms those rows first; with the overlap schedule the sketch
+    // update and the next block's Alg. 2 then run on a high-priority side
+    // stream while the rest of the trailing update (rows k.. of C -= Y W2)
+    // runs on the caller's stream, and the latency-bound LU and small QR of
+    // the sketch take the FP64 cycles the trailing GEMM leaves.  Both
+    // schedules launch the same kernels on the same data, so their results
+    // are identical bit for bit.  The mixed form and the Householder panel use
+    // the serial schedule.
+    SideStream side;
+    const bool overlap = o.schedule == BQRRP_SCHEDULE_OVERLAP && o.precision == BQRRP_PRECISION_FP64 &&
+                         o.panel_kind == BQRRP_PANEL_CHOLQR;
+    Ctx cs = c;   // Alg. 2 and the sketch update
+    if (overlap) {
+        BQ_TRY(side.open());
+        cs.stream = side.st;
+        pr.end();
+        pr.split = true;
+        pr.st[1] = side.st;
+    }
+    auto fork = [&]() -> int {   // side stream after the caller's stream's work so far
+        if (!overlap) return 0;
+        BQ_CUDA(cudaEventRecord(side.ev_fork, c.stream));
+        BQ_CUDA(cudaStreamWaitEvent(cs.stream, side.ev_fork, 0));
+        return 0;
+    };
+    auto join = [&]() -> int {   // caller's stream after the side stream's work so far
+        if (!overlap) return 0;
+        pr.end_lane(0);   // the wait is no phase of the caller's stream
+        BQ_CUDA(cudaEventRecord(side.ev_join, cs.stream));
+        BQ_CUDA(cudaStreamWaitEvent(c.stream, side.ev_join, 0));
+        return 0;
+    };
+    // Alg. 2 on the sketch columns it*b..n-1: LUPP of Ssk^T, piv_transform,
+    // R^sk from the LU factors (Householder QR of U^T, then R1 L^T), tri_rank
+    auto alg2 = [&](i64 it) -> int {
+        const i64 s = it * b, N = n - s, w = imin(n, s + b) - s;
+        double* Ssk = B.Msk + s * d;
+        pr.begin(P_LUPP);
+        BQ_CUDA(cudaMemsetAsync(&B.st->sk_nonfinite, 0, sizeof(int), cs.stream));
+        BQ_CUDA(cudaMemsetAsync(&B.st->zero_col, 0, sizeof(int), cs.stream));
+        BQ_TRY(any_nonfinite(cs, d, N, Ssk, d, &B.st->sk_nonfinite));
+        BQ_CUDA(cudaMemcpy2DAsync(B.Xlu, sizeof(double) * d, Ssk, sizeof(double) * d, sizeof(double) * d, N,
+                                  cudaMemcpyDeviceToDevice, cs.stream));
+        const i64 steps = imin(N, d);
+        BQ_TRY(getrf_pivots(cs, N, d, B.Xlu, d, B.ipiv));
+        BQ_TRY(piv_transform_moved(cs, N, steps, B.ipiv, B.Jsk, &B.st->sk_nonfinite, B.pos, B.src, B.cnt));
+        pr.flops(P_LUPP, lupp_flops((double)N, (double)d));
+        pr.begin(P_SKQR);
+        // scratch of the blocked-QR fallback: W and the column stage, which the
+        // rest of the trailing update (Y, W2, C) does not touch
+        BQ_TRY(rsk_from_lu(cs, d, N, B.Xlu, d, Ssk, d, B.Ub, B.sktau, B.Vqr, B.Tqr, B.W, B.stage));
+        tri_rank_kernel<<<1, 1024, 0, cs.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
+        BQ_LAUNCH_CHECK();
+        pr.flops(P_SKQR, geqrf_flops((double)d, (double)N));
+        if (overlap) pr.end_lane(1);
+        return 0;
+    };
+
+    BQ_TRY(fork());
+    BQ_TRY(alg2(0));
     i64 ell = 0;
     for (i64 it = 0;; ++it) {
         const i64 s = it * b;
@@ -460,27 +559,10 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         const i64 N = n - s;
         const i64 rows = m - s;
         double* Ssk = B.Msk + s * d;
-
-        // ---- Alg. 2 on the sketch: LUPP of Ssk^T and piv_transform
-        pr.begin(P_LUPP);
-        BQ_CUDA(cudaMemsetAsync(&B.st->sk_nonfinite, 0, sizeof(int), c.stream));
-        BQ_CUDA(cudaMemsetAsync(&B.st->zero_col, 0, sizeof(int), c.stream));
-        BQ_TRY(any_nonfinite(c, d, N, Ssk, d, &B.st->sk_nonfinite));
-        BQ_CUDA(cudaMemcpy2DAsync(B.Xlu, sizeof(double) * d, Ssk, sizeof(double) * d, sizeof(double) * d, N,
-                                  cudaMemcpyDeviceToDevice, c.stream));
-        const i64 steps = imin(N, d);
-        BQ_TRY(getrf_pivots(c, N, d, B.Xlu, d, B.ipiv));
-        BQ_TRY(piv_transform_moved(c, N, steps, B.ipiv, B.Jsk, &B.st->sk_nonfinite, B.pos, B.src, B.cnt));
-        pr.flops(P_LUPP, lupp_flops((double)N, (double)d));
-        // ---- gather + Householder QR of the sketch, tri_rank
-        pr.begin(P_SKQR);
-        const i64 mm = imin(N, 2 * steps);
-        BQ_TRY(rsk_from_lu(c, d, N, B.Xlu, d, Ssk, d, B.Ub, B.sktau, B.Vqr, B.Tqr, B.W, B.W2));
-        tri_rank_kernel<<<1, 1024, 0, c.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
-        BQ_LAUNCH_CHECK();
-        pr.flops(P_SKQR, geqrf_flops((double)d, (double)N));
+        const i64 mm = imin(N, 2 * imin(N, d));
 
         // ---- permute A(:, s:) (all m rows: R rows and working rows, merged) and J(s:)
+        BQ_TRY(join());
         pr.begin(P_PERM);
         BQ_TRY(gather_cols(c, m, A + s * lda, lda, B.pos, B.src, B.cnt, mm, B.stage, B.ldst));
         BQ_TRY(gather_idx(c, B.J + s, B.pos, B.src, B.cnt, mm, B.Jstage));
@@ -494,6 +576,19 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
 
         double* Ap = A + s + s * lda;   // panel / working block origin
         const i64 nc = n - cend;
+        // ---- sketch update, Msk(0:w, c:) = Rsk12 - (Rsk11 R11^-1) R12 (Rsk22 stays),
+        // then Alg. 2 of the next block
+        auto next_block = [&]() -> int {
+            BQ_TRY(fork());
+            pr.begin(P_SKUPD);
+            BQ_TRY(copy_triu(cs, w, w, Ssk, d, B.Z, B.bb));
+            BQ_TRY(trsm_ru(cs, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
+            BQ_TRY(pgemm(cs, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0,
+                         B.Msk + cend * d, d));
+            pr.flops(P_SKUPD, (double)w * w * w + 2.0 * (double)w * w * nc);
+            return alg2(it + 1);
+        };
+        bool more = false;
         if (o.panel_kind == BQRRP_PANEL_HQR) {
             // Householder QR of all w panel columns, reflectors applied to the
             // whole trailing block; only the first k are kept (Sec. 3.5).
@@ -504,6 +599,8 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
                 BQ_LAUNCH_CHECK();
             }
             pr.flops(P_PANEL, geqrf_flops((double)rows, (double)w) + 4.0 * rows * w * nc);
+            more = cend < n && k == w;
+            if (more) BQ_TRY(next_block());
         } else {
             // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
             pr.begin(P_PANEL);
@@ -520,35 +617,40 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
                 pr.flops(P_PANEL, 4.0 * r * kk * kk + kk * kk * kk * (1.0 / 3.0 + 1.0 / 3.0) + 2.0 * kk * kk * w);
             }
             if (k <= 0) { ell = s; break; }
+            more = cend < n && k == w;
             // ---- trailing update with the block reflector (I - Y T Y^T)^T
-            if (nc > 0) {
+            double* C = A + s + cend * lda;
+            const i64 keep = (k == w) ? rows : k;
+            if (nc > 0 && o.precision == BQRRP_PRECISION_MIXED) {
                 pr.begin(P_TRAIL);
-                double* C = A + s + cend * lda;
-                const i64 keep = (k == w) ? rows : k;
-                if (o.precision == BQRRP_PRECISION_MIXED) {
-                    BQ_TRY(ozaki_gemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows,
-                                      B.oz_ws, B.oz_bytes));
-                    BQ_TRY(ozaki_gemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows,
-                                      B.oz_ws, B.oz_bytes));
-                    BQ_TRY(ozaki_gemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda,
-                                      B.oz_ws, B.oz_bytes));
-                } else {
-                    BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
-                    BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
-                    BQ_TRY(dgemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+                BQ_TRY(ozaki_gemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows,
+                                  B.oz_ws, B.oz_bytes));
+                BQ_TRY(ozaki_gemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows,
+                                  B.oz_ws, B.oz_bytes));
+                BQ_TRY(ozaki_gemm(c, false, false, keep, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda,
+                                  B.oz_ws, B.oz_bytes));
+                if (more) BQ_TRY(next_block());
+            } else if (nc > 0) {
+                pr.begin(P_TRAIL);
+                BQ_TRY(dgemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows));
+                BQ_TRY(dgemm(c, true, false, k, nc, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
+                // R12 rows first: the sketch update reads only these
+                BQ_TRY(dgemm(c, false, false, k, nc, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, C, lda));
+                if (more) BQ_TRY(next_block());
+                if (keep > k) {
+                    // rows k.. with no split-K, so that it shares no scratch with Alg. 2 on the side stream
+                    pr.begin(P_TRAIL);
+                    Ctx c3 = c;
+                    c3.splitk = nullptr;
+                    BQ_TRY(dgemm(c3, false, false, keep - k, nc, k, -1.0, B.Ypan + k, m, B.W2, B.wrows, 1.0, C + k,
+                                 lda));
                 }
+            }
+            if (nc > 0)
                 pr.flops(P_TRAIL, 2.0 * (double)k * nc * (double)rows + 2.0 * (double)k * k * nc +
                                       2.0 * (double)keep * nc * k);
-            }
         }
-        if (cend == n || k < w) { ell = s + k; break; }
-
-        // ---- sketch update: Msk(0:w, c:) = Rsk12 - (Rsk11 R11^-1) R12; Rsk22 stays
-        pr.begin(P_SKUPD);
-        BQ_TRY(copy_triu(c, w, w, Ssk, d, B.Z, B.bb));
-        BQ_TRY(trsm_ru(c, w, w, colmajor(Ap, lda), colmajor(B.Z, B.bb), false));
-        BQ_TRY(pgemm(c, false, false, w, nc, w, -1.0, B.Z, B.bb, A + s + cend * lda, lda, 1.0, B.Msk + cend * d, d));
-        pr.flops(P_SKUPD, (double)w * w * w + 2.0 * (double)w * w * nc);
+        if (!more) { ell = s + k; break; }
         if (io) BQ_TRY(io->send_back(c, A, m, lda, cend));   // block [s, cend) is final
     }
     pr.begin(P_OTHER);
@@ -658,7 +760,7 @@ int factor_entry(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_
         std::lock_guard<std::mutex> lk(g_prof.mu);
         pr.on = g_prof.on;
     }
-    pr.st = c.stream;
+    pr.st[0] = pr.st[1] = c.stream;
     const int rc = factor_impl(m, n, A, lda, b, d, seed, jpvt, tau, &r, o, B, c, pr, io);
     if (rc == 0) {
         *rank = r;

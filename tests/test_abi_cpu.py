@@ -49,6 +49,11 @@ def test_argument_errors_follow_info_convention():
     assert _factor_rc(10, 8, 4, 3)[0] == -6
     bad = B.make_opts(7, 8)
     assert _factor_rc(10, 8, 4, 5, opts=bad)[0] == -11
+    assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(schedule=2))[0] == -11
+    bad = B.make_opts()
+    bad.reserved[2] = 1
+    assert _factor_rc(10, 8, 4, 5, opts=bad)[0] == -11
+    assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(schedule=B.SCHEDULE_SERIAL))[0] == -3   # valid opts, A NULL
     assert _factor_rc(10, 8, 4, 5)[0] == -3                         # A is NULL
     rc, rank = _factor_rc(10, 0, 4, 5)
     assert rc == 0 and rank == 0                                     # empty: nothing to do

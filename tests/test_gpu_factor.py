@@ -125,6 +125,39 @@ def test_deterministic_and_host_entry_point_identical():
     assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
 
 
+@pytest.mark.parametrize("case", [
+    ("gaussian", 1500, 900, 100, 125),      # ragged last block
+    ("low_rank", 1100, 700, 96, 120),       # stops inside the third block
+    ("low_rank", 1024, 1024, 128, 160),     # rank 256: stops at a block boundary
+    ("sparse", 900, 800, 64, 80),           # sparse-sign sketch
+    ("gaussian", 3000, 500, 64, 80),        # tall
+    ("gaussian", 2000, 1500, 600, 700),     # d > 640: R^sk by the blocked Householder QR
+])
+def test_overlap_schedule_identical_to_serial(case):
+    """The overlap schedule (sketch update and the next block's Alg. 2 on a
+    side stream during the trailing update) gives the serial schedule's
+    results bit for bit, with the phase profiler off and on."""
+    kind, m, n, b, d = case
+    if kind == "low_rank":
+        A = W.low_rank(m, n, 250 if n == 700 else 256, 8)
+    else:
+        A = W.gaussian(m, n, 9)
+    sketch = "sparse" if kind == "sparse" else "dense"
+    ref = [np_(x) if torch.is_tensor(x) else x for x in bq.factor(A, b, d, 5, sketch=sketch, schedule="serial")]
+    for prof in (False, True):
+        B.bqrrp_profile_enable(prof)
+        try:
+            got = [np_(x) if torch.is_tensor(x) else x for x in bq.factor(A, b, d, 5, sketch=sketch)]
+        finally:
+            B.bqrrp_profile_enable(False)
+        torch.cuda.synchronize()
+        assert got[3] == ref[3]
+        for x, y in zip(got[:3], ref[:3]):
+            assert np.array_equal(x, y)
+    if kind == "low_rank":
+        assert ref[3] < n
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("rank_deficient", [False, True])
 def test_host_entry_point_padded_ld(pinned, rank_deficient):
