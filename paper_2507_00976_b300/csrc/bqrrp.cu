@@ -361,7 +361,8 @@ int read_status(const Ctx& c, DevStatus* host) {
 // Alg. 3 on one panel Mp (rows x w, ld ldm) with preconditioner Rsk (upper
 // triangle, ld ldr): Pre = Mp(:, 0:k) Rsk11^-1 in Y, G = Pre^T Pre, Rchol =
 // chol(G) (a breakdown lowers *k), Qc = Pre Rchol^-1, modified LU of Qc (Y
-// unit lower trapezoidal, U, D), T = -U D Y1^-T in Tb, R11 = D Rchol
+// unit lower trapezoidal, U, D; only the top k rows of Qc are formed, the
+// rows below come from one solve with U Rchol), T = -U D Y1^-T in Tb, R11 = D Rchol
 // Rsk(0:k, 0:w); R11 and the reflectors are written into Mp and diag(T) into
 // tau.  Y and Tb stay valid for the trailing update.  Synchronizes the stream
 // once (to read the Cholesky status).
@@ -382,10 +383,18 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
         *kio = k;
         if (k <= 0) return 0;
     }
-    BQ_TRY(trsm_ru(c, rows, k, colmajor(G, ldb), Yv, false));                         // Qc = Pre Rchol^-1
-    BQ_TRY(modlu(c, rows, k, Y, ldy, D));                                              // Qc - [S;0] = Y U
+    // The modified LU of Qc = Pre Rchol^-1 factors its top k x k block,
+    // Qc1 - S = Y1 U; the rows below follow from Qc2 = Y2 U, so
+    // Y2 = Pre2 Rchol^-1 U^-1 = Pre2 (U Rchol)^-1: one tall solve with the
+    // k x k upper triangle U Rchol instead of two (Rchol^-1, then U^-1)
+    BQ_TRY(trsm_ru(c, k, k, colmajor(G, ldb), Yv, false));                            // Qc1 = Pre1 Rchol^-1
+    BQ_TRY(modlu(c, k, k, Y, ldy, D));                                                 // Qc1 - S = Y1 U
     recon_split_kernel<<<gblocks(c, k * k), 256, 0, c.stream>>>(k, Y, ldy, D, U, Tb, ldb);
     BQ_LAUNCH_CHECK();
+    if (rows > k) {
+        BQ_TRY(dgemm(c, false, false, k, k, k, 1.0, U, ldb, G, ldb, 0.0, R11, ldb, kGemmAUpper));   // U Rchol
+        BQ_TRY(trsm_ru(c, rows - k, k, colmajor(R11, ldb), colmajor(Y + k, ldy), false));       // Y2
+    }
     BQ_TRY(trsm_ru(c, k, k, Yv.t(), colmajor(Tb, ldb), true));                        // T = -U S Y1^-T
     BQ_TRY(dgemm(c, false, false, k, w, k, 1.0, G, ldb, Rsk, ldr, 0.0, R11, ldb));     // Rchol Rsk(0:k, 0:w)
     panel_writeback_kernel<<<gblocks(c, rows * w), 256, 0, c.stream>>>(rows, w, k, Mp, ldm, Y, ldy, R11, D, Tb, ldb,
@@ -612,8 +621,9 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             }
             {
                 const double r = (double)rows, kk = (double)k;
-                // preconditioner TRSM, Gram (SYRK), TRSM, reconstruction: rows*k^2 FLOPs each
-                // (summed over the loop, 2 b n^2); + Cholesky, T (k^3/3 each) and R11 (2 k^2 w)
+                // the method's count: preconditioner TRSM, Gram (SYRK), TRSM, reconstruction:
+                // rows*k^2 FLOPs each (summed over the loop, 2 b n^2; the last two are one
+                // solve here); + Cholesky, T (k^3/3 each) and R11 (2 k^2 w)
                 pr.flops(P_PANEL, 4.0 * r * kk * kk + kk * kk * kk * (1.0 / 3.0 + 1.0 / 3.0) + 2.0 * kk * kk * w);
             }
             if (k <= 0) { ell = s; break; }

@@ -180,7 +180,8 @@ def test_col_perm_bitexact(m, N, moves):
 
 
 # ------------------------------------------------------------- Alg. 3 (CholQR panel)
-@pytest.mark.parametrize("rows,w,d", [(300, 32, 40), (1000, 100, 125), (2065, 128, 160), (4096, 64, 80)])
+@pytest.mark.parametrize("rows,w,d", [(300, 32, 40), (1000, 100, 125), (2065, 128, 160), (4096, 64, 80),
+                                      (100, 100, 125), (6000, 200, 250)])
 def test_cholqr_panel_matches_oracle(rows, w, d):
     Mp = W.spectrum(rows, w, W.geometric_sigma(w, -6), rows + w)
     S = oracle.sketch_operator(d, rows, 3)
