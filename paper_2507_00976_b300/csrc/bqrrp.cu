@@ -839,23 +839,27 @@ int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t
     if (pinned) BQ_CUDA(cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking));
     int rc = factor_entry(m, n, dA, m, b, d, seed, dj, dt, rank, opts, rest, rest_bytes, stream,
                           pinned ? &io : nullptr);
+    cudaError_t ce = cudaSuccess;   // of the copies back and the final synchronizations
     if (rc == 0) {
-        if (!pinned) {
-            rc = cudaMemcpy2DAsync(A_host, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
-                                   cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : BQRRP_ECUDA;
-        }
-        if (rc == 0 && (cudaMemcpyAsync(jpvt_host, dj, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                        cudaMemcpyAsync(tau_host, dt, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess))
-            rc = BQRRP_ECUDA;
+        if (!pinned)
+            ce = cudaMemcpy2DAsync(A_host, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+                                   cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(jpvt_host, dj, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(tau_host, dt, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
     }
     // both streams finish before the events, the copy stream and the call go
-    if (cudaStreamSynchronize(st) != cudaSuccess && rc == 0) rc = BQRRP_ECUDA;
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = se;
     if (io.cs) {
-        if (cudaStreamSynchronize(io.cs) != cudaSuccess && rc == 0) rc = BQRRP_ECUDA;
+        const cudaError_t ss = cudaStreamSynchronize(io.cs);
+        if (ce == cudaSuccess) ce = ss;
         cudaStreamDestroy(io.cs);
     }
     for (cudaEvent_t ev : events) cudaEventDestroy(ev);
-    if (rc == BQRRP_ECUDA) set_error("bqrrp_factor_host: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == 0 && ce != cudaSuccess) {
+        set_error("bqrrp_factor_host: %s", cudaGetErrorString(ce));
+        rc = BQRRP_ECUDA;
+    }
     if (rc != 0 && rank) *rank = -1;
     return rc;
 }
