@@ -116,10 +116,12 @@ size_t bqrrp_workspace_query(int64_t m, int64_t n, int64_t b, int64_t d, const b
  * (pinned memory gives full PCIe/C2C bandwidth).  The call copies A to the
  * device on `stream`, factors it as bqrrp_factor does, copies A, jpvt and tau
  * back and synchronizes `stream` before returning; the results are bit for bit
- * those of bqrrp_factor.  When A_host is pinned, each finished column block of
- * R and the reflectors goes back on a private copy stream while the later
- * blocks are factored (created and destroyed inside the call, synchronized
- * before it returns); pageable A_host is copied back once at the end.
+ * those of bqrrp_factor.  When A_host is pinned, the copies run on a private
+ * copy stream (created and destroyed inside the call, synchronized before it
+ * returns): with the dense FP64 sketch A comes in by column halves, each
+ * sketched as soon as it has arrived, and each finished column block of R and
+ * the reflectors goes back while the later blocks are factored.  Pageable
+ * A_host is copied in before the factorization and back after it.
  * workspace is device memory of at least bqrrp_workspace_query_host() bytes
  * (A, jpvt and tau on the device, then bqrrp_factor's workspace).
  * Errors: those of bqrrp_factor.  On BQRRP_ENUMERIC A_host is unchanged; on

@@ -418,23 +418,38 @@ inline double lupp_flops(double N, double d) {      // GETRF on N x d: sum_j (N-
     return f;
 }
 
-// Host buffers of the host entry point.  Every column block goes back to the
-// host on the copy stream as soon as its iteration has finished it, so the
-// copy back overlaps the rest of the factorization: after the iteration on
+// Pinned host buffers of the host entry point.  A comes in on the copy
+// stream; with the dense FP64 sketch it comes in two column halves, the
+// second copied while the first is sketched.  Every column block goes back
+// on the copy stream as soon as its iteration has finished it, so the copy
+// back overlaps the rest of the factorization: after the iteration on
 // columns [s, c), later iterations permute, update and read only columns >= c.
 struct HostIO {
-    double* A_host;     // out: R and the reflectors (ld lda_host); pinned
+    double* A_host;     // in: A; out: R and the reflectors (ld lda_host); pinned
     i64 lda_host;
     cudaStream_t cs;    // copy stream
     std::vector<cudaEvent_t>* events;
     i64 copied = 0;     // columns [0, copied) queued for the copy back
+    int record(cudaStream_t st, cudaEvent_t* ev) {
+        BQ_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        events->push_back(*ev);
+        BQ_CUDA(cudaEventRecord(*ev, st));
+        return 0;
+    }
+    // copy columns [c0, c0 + nc) of A in; the compute stream waits for them
+    int bring_in(const Ctx& c, double* A, i64 m, i64 lda, i64 c0, i64 nc) {
+        BQ_CUDA(cudaMemcpy2DAsync(A + c0 * lda, sizeof(double) * lda, A_host + c0 * lda_host,
+                                  sizeof(double) * lda_host, sizeof(double) * m, nc, cudaMemcpyHostToDevice, cs));
+        cudaEvent_t ev;
+        BQ_TRY(record(cs, &ev));
+        BQ_CUDA(cudaStreamWaitEvent(c.stream, ev, 0));
+        return 0;
+    }
     // queue the copy back of columns [copied, upto) once the compute stream is past this point
     int send_back(const Ctx& c, const double* A, i64 m, i64 lda, i64 upto) {
         if (upto <= copied) return 0;
         cudaEvent_t ev;
-        BQ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        events->push_back(ev);
-        BQ_CUDA(cudaEventRecord(ev, c.stream));
+        BQ_TRY(record(c.stream, &ev));
         BQ_CUDA(cudaStreamWaitEvent(cs, ev, 0));
         BQ_CUDA(cudaMemcpy2DAsync(A_host + copied * lda_host, sizeof(double) * lda_host, A + copied * lda,
                                   sizeof(double) * lda, sizeof(double) * m, upto - copied, cudaMemcpyDeviceToHost, cs));
@@ -473,12 +488,16 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
     pr.begin(P_OTHER);
     init_status_kernel<<<1, 1, 0, c.stream>>>(B.st);
     BQ_LAUNCH_CHECK();
-    // NaN/Inf in A -> BQRRP_ENUMERIC before anything is written
-    BQ_TRY(any_nonfinite(c, m, n, A, lda, &B.st->a_nonfinite));
-    BQ_TRY(read_status(c, &hs));
-    if (hs.a_nonfinite) {
-        set_error("A contains NaN or Inf");
-        return BQRRP_ENUMERIC;
+    const bool dense64 = o.sketch_kind == BQRRP_SKETCH_DENSE && o.precision == BQRRP_PRECISION_FP64;
+    if (io && !dense64) BQ_TRY(io->bring_in(c, A, m, lda, 0, n));
+    if (!io || !dense64) {
+        // NaN/Inf in A -> BQRRP_ENUMERIC before anything is written
+        BQ_TRY(any_nonfinite(c, m, n, A, lda, &B.st->a_nonfinite));
+        BQ_TRY(read_status(c, &hs));
+        if (hs.a_nonfinite) {
+            set_error("A contains NaN or Inf");
+            return BQRRP_ENUMERIC;
+        }
     }
     BQ_CUDA(cudaMemsetAsync(tau, 0, sizeof(double) * (size_t)n, c.stream));
     iota_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c.stream>>>(n, B.J);
@@ -486,7 +505,28 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
 
     // Alg. 1: sketch Msk = S * A (d x n)
     pr.begin(P_SKETCH);
-    if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
+    if (io && dense64) {
+        // A from the host in two column halves; each half is checked and
+        // sketched once it has arrived, with the split-K count of the whole
+        // product (so the bits are those of one launch).  The sketch writes
+        // only Msk, so the NaN/Inf verdict, read after it, still comes before
+        // anything of A is written.
+        const int sp = sketch_dense_splits(c, d, m, n);
+        const i64 half = n >= 1024 ? cdiv(cdiv(n, 2), 64) * 64 : n;
+        for (i64 c0 = 0; c0 < n; c0 += half) {
+            const i64 nc0 = imin(half, n - c0);
+            BQ_TRY(io->bring_in(c, A, m, lda, c0, nc0));
+            BQ_TRY(any_nonfinite(c, m, nc0, A + c0 * lda, lda, &B.st->a_nonfinite));
+            BQ_TRY(sketch_dense_gemm(c, d, m, nc0, seed, A + c0 * lda, lda, B.Msk + c0 * d, d, sp));
+        }
+        pr.flops(P_SKETCH, 2.0 * d * m * n);
+        pr.begin(P_OTHER);
+        BQ_TRY(read_status(c, &hs));
+        if (hs.a_nonfinite) {
+            set_error("A contains NaN or Inf");
+            return BQRRP_ENUMERIC;
+        }
+    } else if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
         if (o.precision == BQRRP_PRECISION_MIXED)
             BQ_TRY(ozaki_sketch(c, d, m, n, seed, A, lda, B.Msk, d, B.oz_ws, B.oz_bytes));
         else
@@ -825,18 +865,30 @@ int bqrrp_factor_host(int64_t m, int64_t n, double* A_host, int64_t lda, int64_t
     double* dt = (double*)(base + am + jv);
     char* rest = base + am + 2 * jv;
     const size_t rest_bytes = workspace_bytes - (size_t)(rest - (char*)workspace);
-    BQ_CUDA(cudaMemcpy2DAsync(dA, sizeof(double) * m, A_host, sizeof(double) * lda, sizeof(double) * m, n,
-                              cudaMemcpyHostToDevice, st));
-    // With pinned A_host the finished column blocks go back on a copy stream
-    // while the later blocks are factored; pageable memory (where an
-    // asynchronous copy to the host would block this thread) is copied once
-    // at the end.
+    // Pinned A_host is copied in and back on a copy stream, overlapped with
+    // the factorization; pageable memory (where an asynchronous copy may
+    // synchronize the stream or block this thread) is copied in before it
+    // and back after it.
     cudaPointerAttributes pa{};
     const bool pinned = cudaPointerGetAttributes(&pa, A_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
     (void)cudaGetLastError();
     std::vector<cudaEvent_t> events;
     HostIO io{A_host, lda, nullptr, &events};
-    if (pinned) BQ_CUDA(cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking));
+    if (pinned) {
+        BQ_CUDA(cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking));
+        // the copy stream starts after the work queued on `stream` so far
+        cudaEvent_t ev;
+        const int e = io.record(st, &ev);
+        if (e != 0 || cudaStreamWaitEvent(io.cs, ev, 0) != cudaSuccess) {
+            cudaStreamDestroy(io.cs);
+            for (cudaEvent_t x : events) cudaEventDestroy(x);
+            set_error("bqrrp_factor_host: copy stream setup failed");
+            return BQRRP_ECUDA;
+        }
+    } else {
+        BQ_CUDA(cudaMemcpy2DAsync(dA, sizeof(double) * m, A_host, sizeof(double) * lda, sizeof(double) * m, n,
+                                  cudaMemcpyHostToDevice, st));
+    }
     int rc = factor_entry(m, n, dA, m, b, d, seed, dj, dt, rank, opts, rest, rest_bytes, stream,
                           pinned ? &io : nullptr);
     cudaError_t ce = cudaSuccess;   // of the copies back and the final synchronizations

@@ -225,8 +225,12 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
 // problem is large enough (and its workspace fits), else the FP64 SIMT GEMM.
 int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
           const double* B, i64 ldb, double beta, double* C, i64 ldc, int flags = 0);
+// Msk = S A with the +-1 operator generated in the tile loader.  splits > 0
+// forces the split-K count (sketch_dense_splits(d, m, n) of the whole product
+// makes column slices of it give the whole product's bits).
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,
-                      i64 ldsk);
+                      i64 ldsk, int splits = 0);
+int sketch_dense_splits(const Ctx& c, i64 d, i64 m, i64 n);
 
 // dense.cu
 int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit);   // X <- X * R^{-1}

@@ -169,13 +169,9 @@ __global__ void splitk_reduce_kernel(i64 M, i64 N, int splits, const double* __r
     }
 }
 
-template <int AMODE, bool TB>
-int launch(const Ctx& c, GemmArgs a) {
-    const i64 tm = cdiv(a.M, BM), tn = cdiv(a.N, BN);
-    if (tm > 2147483647 || tn > 65535) {
-        set_error("dgemm: grid too large (%lld x %lld tiles)", (long long)tm, (long long)tn);
-        return BQRRP_EUNSUPPORTED;
-    }
+// Split count along K for an M x N x K product (1 = no split).
+int pick_splits(const Ctx& c, i64 M, i64 N, i64 K, int flags) {
+    const i64 tm = cdiv(M, BM), tn = cdiv(N, BN);
     // split-K balances the FP64 work over the SMs: one 64x64 tile with K = 64
     // is ~65 us on a single SM, and the tile count of a product is rarely a
     // multiple of the SM count (W = V^T C of a 256-wide block, 4 x nc/64 tiles,
@@ -187,12 +183,12 @@ int launch(const Ctx& c, GemmArgs a) {
     // upper-triangle-only C do no work.
     int splits = 1;
     const i64 tiles = tm * tn;
-    const i64 work_tiles = (a.flags & kGemmCUpper) ? imin(tm, tn) * (imin(tm, tn) + 1) / 2 + imax(0, tn - tm) * tm
-                                                   : tiles;
+    const i64 work_tiles = (flags & kGemmCUpper) ? imin(tm, tn) * (imin(tm, tn) + 1) / 2 + imax(0, tn - tm) * tm
+                                                 : tiles;
     const i64 sms = c.dev.sms;
-    if (a.K >= 2 * BK && c.splitk != nullptr) {
-        const i64 fit = (i64)(c.splitk_elems / (size_t)(a.M * a.N));
-        const i64 smax = imin(imin(a.K / BK, 64), fit);
+    if (K >= 2 * BK && c.splitk != nullptr) {
+        const i64 fit = (i64)(c.splitk_elems / (size_t)(M * N));
+        const i64 smax = imin(imin(K / BK, 64), fit);
         double best = 1e30;
         i64 bs = 1;
         for (i64 sc = 1; sc <= smax; ++sc) {
@@ -200,6 +196,25 @@ int launch(const Ctx& c, GemmArgs a) {
             if (cost < best * 0.99) { best = cost; bs = sc; }
         }
         splits = (int)bs;
+    }
+    if (K <= 0) return 1;
+    const i64 kchunk = cdiv(cdiv(K, splits), BK) * BK;
+    return (int)imax(1, cdiv(K, kchunk));
+}
+
+// force_splits > 0 launches with that split count (whose partials must fit
+// the split-K scratch); otherwise pick_splits decides.
+template <int AMODE, bool TB>
+int launch(const Ctx& c, GemmArgs a, int force_splits = 0) {
+    const i64 tm = cdiv(a.M, BM), tn = cdiv(a.N, BN);
+    if (tm > 2147483647 || tn > 65535) {
+        set_error("dgemm: grid too large (%lld x %lld tiles)", (long long)tm, (long long)tn);
+        return BQRRP_EUNSUPPORTED;
+    }
+    int splits = force_splits > 0 ? force_splits : pick_splits(c, a.M, a.N, a.K, a.flags);
+    if (splits > 1 && (c.splitk == nullptr || (size_t)splits * (size_t)(a.M * a.N) > c.splitk_elems)) {
+        set_error("dgemm: %d splits do not fit the split-K scratch", splits);
+        return BQRRP_EUNSUPPORTED;
     }
     a.kchunk = cdiv(cdiv(a.K, splits), BK) * BK;
     splits = (int)cdiv(a.K, a.kchunk);
@@ -270,8 +285,10 @@ int gemm_view(const Ctx& c, i64 M, i64 N, i64 K, double alpha, View A, View B, d
     return dgemm(c, tB, tA, N, M, K, alpha, Bt.p, lb, At.p, la, beta, C.p, lc);
 }
 
+int sketch_dense_splits(const Ctx& c, i64 d, i64 m, i64 n) { return pick_splits(c, d, n, m, 0); }
+
 int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk,
-                      i64 ldsk) {
+                      i64 ldsk, int splits) {
     if (d <= 0 || n <= 0) return 0;
     GemmArgs a{};
     a.M = d; a.N = n; a.K = m; a.alpha = 1.0; a.beta = 0.0;
@@ -284,7 +301,7 @@ int sketch_dense_gemm(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const do
         BQ_LAUNCH_CHECK();
         return 0;
     }
-    return launch<2, false>(c, a);
+    return launch<2, false>(c, a, splits);
 }
 
 }  // namespace bq

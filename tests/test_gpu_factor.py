@@ -161,11 +161,12 @@ def test_overlap_schedule_identical_to_serial(case):
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("rank_deficient", [False, True])
 def test_host_entry_point_padded_ld(pinned, rank_deficient):
-    """Host buffers with ld > m, pinned (column blocks copied back while later
-    blocks are factored) and pageable (one copy at the end), full rank and with
+    """Host buffers with ld > m, pinned (A copied in by column halves, each
+    sketched once it has arrived, and column blocks copied back while later
+    blocks are factored) and pageable (one copy each way), full rank and with
     an early stop; the results equal the device entry point's bit for bit and
     the padding rows are left alone."""
-    m, n, b, d = 1100, 700, 96, 120
+    m, n, b, d = 1300, 1100, 96, 120
     A = W.low_rank(m, n, 250, 4) if rank_deficient else W.gaussian(m, n, 5)
     F1, j1, t1, r1 = run_gpu(A, b, d, 17)
     ld = m + 13
@@ -183,6 +184,54 @@ def test_host_entry_point_padded_ld(pinned, rank_deficient):
     assert r2 == r1 and (r1 < n) == rank_deficient
     assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
     assert torch.all(buf[:, m:] == -7.0)
+
+
+@pytest.mark.parametrize("precision,sketch", [("fp64", "sparse"), ("mixed", "dense")])
+def test_host_entry_point_other_forms(precision, sketch):
+    """Pinned host buffers with the sparse sketch and with the mixed form (A
+    copied in whole before the sketch): the device entry point's results bit
+    for bit."""
+    m, n, b, d = 1200, 1100, 96, 120
+    A = W.gaussian(m, n, 6)
+    F1, j1, t1, r1 = [np_(x) if torch.is_tensor(x) else x
+                      for x in bq.factor(A, b, d, 7, sketch=sketch, precision=precision)]
+    Ah = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+    Ah.copy_(torch.as_tensor(A))
+    jh = torch.empty(n, dtype=torch.int64).pin_memory()
+    th = torch.empty(n, dtype=torch.float64).pin_memory()
+    opts = B.make_opts(B.SKETCH_DENSE if sketch == "dense" else B.SKETCH_SPARSE, 8, B.PANEL_CHOLQR,
+                       B.PRECISION_FP64 if precision == "fp64" else B.PRECISION_MIXED)
+    ws = torch.empty(B.bqrrp_workspace_query_host(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
+    assert B.bqrrp_factor_host(Ah, b, d, 7, jh, th, ws, opts=opts) == r1
+    assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1) and np.array_equal(th.numpy(), t1)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("col", [5, 1000])     # in the first or the second half of the columns
+def test_host_entry_point_nan_leaves_host_buffer_unchanged(pinned, col):
+    m, n = 1400, 1200
+    A = W.gaussian(m, n, 3)
+    A[11, col] = np.nan
+    buf = torch.empty((n, m), dtype=torch.float64)
+    if pinned:
+        buf = buf.pin_memory()
+    Ah = buf.t()
+    Ah.copy_(torch.as_tensor(A))
+    before = Ah.clone()
+    jh = torch.empty(n, dtype=torch.int64)
+    th = torch.empty(n, dtype=torch.float64)
+    ws = torch.empty(B.bqrrp_workspace_query_host(m, n, 64, 80), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.BqrrpError) as e:
+        B.bqrrp_factor_host(Ah, 64, 80, 1, jh, th, ws)
+    assert e.value.code == B.ENUMERIC
+    assert torch.equal(torch.isnan(Ah), torch.isnan(before))
+    assert torch.equal(torch.nan_to_num(Ah), torch.nan_to_num(before))
+    # the same workspace then factors a finite matrix correctly
+    A[11, col] = 0.5
+    Ah.copy_(torch.as_tensor(A))
+    F1, j1, t1, r1 = run_gpu(A, 64, 80, 1)
+    assert B.bqrrp_factor_host(Ah, 64, 80, 1, jh, th, ws) == r1
+    assert np.array_equal(Ah.numpy(), F1) and np.array_equal(jh.numpy(), j1)
 
 
 def test_error_codes():
