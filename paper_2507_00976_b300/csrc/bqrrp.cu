@@ -537,8 +537,8 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         pr.flops(P_SKETCH, 2.0 * (double)o.sketch_nnz * m * n);
     }
 
-    // Schedule (Sec. 3 leaves the order of independent steps open).  Alg. 2 of
-    // the next block needs only the sketch update, and that needs only R11 and
+    // Schedule: a reordering of independent steps of Alg. 1.  Alg. 2 of the
+    // next block needs only the sketch update, and that needs only R11 and
     // the first k rows of the updated trailing block (R12).  So the trailing
     // update forms those rows first; with the overlap schedule the sketch
     // update and the next block's Alg. 2 then run on a high-priority side
