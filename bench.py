@@ -228,6 +228,31 @@ def cpu_sample(a, budget_s=20.0):
     return gf, f"oracle BQRRP on {s}x{s} ({a.family}), b={b}, d={d}, 1 thread, {dt:.1f} s", 1
 
 
+def host_lapack_context(a, s=2560):
+    """Host LAPACK (scipy) on the same s x s sample: GEQP3 (the paper's CPU
+    comparison routine) and GEQRF, on all host cores.  Context, not a target."""
+    import numpy as np
+    import scipy.linalg as sla
+
+    from paper_2507_00976_b300 import workloads as W
+    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -12.0), a.seed)
+    threads = None
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max((p.get("num_threads", 0) for p in threadpool_info()), default=None)
+    except Exception:
+        threads = os.cpu_count()
+    out = {"size": f"{s}x{s}", "threads": threads, "library": "scipy.linalg (host LAPACK)",
+           "note": "the paper's CPU comparison routine on this host: context, not a target"}
+    for name, fn in (("geqp3", lambda: sla.qr(A, mode="r", pivoting=True)), ("geqrf", lambda: sla.qr(A, mode="r"))):
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        out[f"{name}_gflops"] = canonical_flops(s, s) / dt / 1e9
+        out[f"{name}_s"] = dt
+    return out
+
+
 def run_reference(a, world, rank):
     """--impl reference: the oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -869,7 +894,8 @@ def main():
     cpu = None
     if not a.skip_cpu and world == 1:
         gf, sample, cores = cpu_sample(a)
-        cpu = {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "host_lapack": host_lapack_context(a)}
     lat = sorted(step_ms)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
     line = {
