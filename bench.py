@@ -894,8 +894,12 @@ def main():
     cpu = None
     if not a.skip_cpu and world == 1:
         gf, sample, cores = cpu_sample(a)
+        try:
+            lapack = host_lapack_context(a)
+        except Exception as e:   # context only: never costs the bench line
+            lapack = {"unavailable": f"{type(e).__name__}: {e}"}
         cpu = {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample,
-               "host_lapack": host_lapack_context(a)}
+               "host_lapack": lapack}
     lat = sorted(step_ms)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
     line = {
