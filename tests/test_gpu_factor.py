@@ -71,7 +71,9 @@ def test_c1_parity():
 
 
 @pytest.mark.parametrize("m,n,b,d", [(777, 500, 64, 80), (300, 300, 300, 375), (1000, 100, 128, 160),
-                                     (513, 257, 32, 40), (4100, 130, 64, 80), (65, 65, 8, 10)])
+                                     (513, 257, 32, 40), (4100, 130, 64, 80), (65, 65, 8, 10),
+                                     # degenerate blocks: b = 1 (d = 1 and d > b), 1 x 1, one column, d = b
+                                     (40, 17, 1, 1), (40, 17, 1, 3), (1, 1, 1, 1), (50, 1, 4, 5), (30, 30, 7, 7)])
 def test_shapes_with_ragged_tails(m, n, b, d):
     A = W.gaussian(m, n, m * 3 + n)
     compare(A, b, d, 5, expect_rank=n)
