@@ -92,7 +92,10 @@ typedef struct bqrrp_opts {
  *  rank      HOST, out: the numerical rank l (Sec. 2.2).  Written before the
  *            call returns: the call synchronizes `stream` a few times per
  *            block (the block rank k decides the control flow).
- *  opts      nullable (defaults above).
+ *  opts      nullable (defaults above).  With the default overlap schedule
+ *            the call also creates a private high-priority stream, orders it
+ *            against `stream` with events, and synchronizes and destroys it
+ *            before returning (on error paths too).
  *  workspace device scratch of at least bqrrp_workspace_query() bytes,
  *            256-byte aligned; owned by the caller, contents undefined on exit.
  *
