@@ -509,7 +509,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         // A from the host in two column halves; each half is checked and
         // sketched once it has arrived, with the split-K count of the whole
         // product (so the bits are those of one launch).  The sketch writes
-        // only Msk, so the NaN/Inf verdict, read after it, still comes before
+        // only Msk, so the NaN/Inf result, read after it, still comes before
         // anything of A is written.
         const int sp = sketch_dense_splits(c, d, m, n);
         const i64 half = n >= 1024 ? cdiv(cdiv(n, 2), 64) * 64 : n;
