@@ -462,7 +462,12 @@ int64_t bqrrp_ref_cholqr_panel(int64_t rows, int64_t w, int64_t k, double* Mp, i
     return kc;
 }
 
-/* trace (nullable): for iteration i, trace[4*i + 0] = k, [1] = min LU margin,
+/* sketch_kind: 0 dense +-1 Philox operator, 1 sparse sign (nnz per column),
+ * 2 test hook only: S = I_m (requires d = m) together with qrcp_wide by
+ * Businger-Golub, the special case in which BQRRP reduces to Businger-Golub
+ * QRCP (derived from the sketch update of Alg. 1; pinned against LAPACK's
+ * dgeqp3 in the tests).
+ * trace (nullable): for iteration i, trace[4*i + 0] = k, [1] = min LU margin,
  * [2] = 1 if the sketch was non-finite (identity pivots), [3] = w.
  * Test hooks: max_iters > 0 stops after that many full iterations (the sketch
  * update of the last one included) and returns rank = s of the next block;
@@ -477,8 +482,9 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
     if (lda < (m > 1 ? m : 1)) return -4;
     if (b < 1) return -5;
     if (d < b) return -6;
-    if (sketch_kind != 0 && sketch_kind != 1) return -8;
+    if (sketch_kind != 0 && sketch_kind != 1 && sketch_kind != 2) return -8;
     if (sketch_kind == 1 && (nnz < 1 || nnz > d)) return -9;
+    if (sketch_kind == 2 && d != m) return -6;
     *rank = 0;
     if (n == 0) return REF_OK;
     if (has_nonfinite(m, n, A, lda)) return REF_ENUMERIC;
@@ -506,6 +512,10 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
         !R11 || !Z || !scratch || !sktau) { rc = REF_ENOMEM; goto done; }
 
     if (sketch_kind == 0) bqrrp_ref_sketch_dense(d, m, seed, S);
+    else if (sketch_kind == 2) {                       /* S = I_m (test hook, see below) */
+        for (int64_t j = 0; j < m; ++j)
+            for (int64_t r = 0; r < d; ++r) AT(S, r, j, d) = (r == j) ? 1.0 : 0.0;
+    }
     else { int e = bqrrp_ref_sketch_sparse(d, m, seed, nnz, S); if (e) { rc = e == REF_ENOMEM ? e : -9; goto done; } }
     bqrrp_ref_sketch_apply(d, m, n, S, A, lda, Msk, d);
 
@@ -526,16 +536,25 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
         double margin = 1.0;
         if (nonfinite) {
             for (int64_t t = 0; t < N; ++t) Jsk[t] = t;       /* identity pivots */
+        } else if (sketch_kind == 2) {
+            /* Test hook: qrcp_wide by Businger-Golub instead of Alg. 2.  With
+             * S = I the sketch is M itself, Rsk11 = D R11 (D = +-1), so the
+             * sketch update zeroes rows 0..w-1 and leaves the trailing R of
+             * the pivoted QR: BQRRP then makes Businger-Golub's choices. */
+            bqrrp_ref_qrcp_bg(d, N, Ssk, d, Jsk, sktau);     /* R of the permuted sketch, in place */
+            for (int64_t t = 0; t < N; ++t) Jsk[t] -= 1;
         } else {
             for (int64_t t = 0; t < N; ++t)                    /* X = Ssk^T, N x d */
                 for (int64_t r = 0; r < d; ++r) AT(X, t, r, N) = AT(Ssk, r, t, d);
             int64_t steps = bqrrp_ref_lupp(N, d, X, N, ipiv, &margin);
             bqrrp_ref_piv_transform(N, steps, ipiv, Jsk);
         }
-        col_gather(d, N, Ssk, d, Jsk, tmp, d);
-        for (int64_t t = 0; t < N; ++t)
-            for (int64_t r = 0; r < d; ++r) AT(Ssk, r, t, d) = AT(tmp, r, t, d);
-        bqrrp_ref_geqrf(d, N, Ssk, d, sktau);                 /* Rsk in place */
+        if (sketch_kind != 2 || nonfinite) {
+            col_gather(d, N, Ssk, d, Jsk, tmp, d);
+            for (int64_t t = 0; t < N; ++t)
+                for (int64_t r = 0; r < d; ++r) AT(Ssk, r, t, d) = AT(tmp, r, t, d);
+            bqrrp_ref_geqrf(d, N, Ssk, d, sktau);             /* Rsk in place */
+        }
         for (int64_t t = 0; t < N; ++t)
             for (int64_t r = t + 1; r < d; ++r) AT(Ssk, r, t, d) = 0.0;
 

@@ -131,6 +131,29 @@ def test_qrcp_bg_matches_lapack_dgeqp3():
     np.testing.assert_allclose(np.triu(F)[:40], R_l[:40], atol=1e-12 * np.abs(A).max())
 
 
+@pytest.mark.parametrize("b", [1, 7, 8, 40])
+@pytest.mark.parametrize("panel", ["cholqr", "hqr"])
+def test_identity_sketch_with_bg_reduces_bqrrp_to_dgeqp3(b, panel):
+    """Special case derived from the sketch update of Alg. 1: with S = I_m
+    (d = m) and qrcp_wide by Businger-Golub, R^sk11 = D R11 with D = +-1, so
+    the update zeroes the first w sketch rows and leaves the trailing R of the
+    pivoted QR.  The whole loop (block pivots, composition of J, panel,
+    trailing update, sketch update) then makes Businger-Golub's choices: the
+    pivots equal LAPACK dgeqp3's and R equals its R up to row signs."""
+    A = W.gaussian(60, 40, 8)
+    fo = oracle.bqrrp(A, b, 60, 0, sketch_kind=2, panel=panel)
+    R_l, P = sla.qr(A, pivoting=True, mode="r")
+    assert fo.rank == 40
+    assert list(fo.jpvt - 1) == list(P)
+    np.testing.assert_allclose(np.abs(np.triu(fo.A)[:40]), np.abs(R_l[:40]), atol=1e-12 * np.abs(A).max())
+    res, orth, ok = metrics(A, fo.A, fo.jpvt, fo.tau, fo.rank)
+    assert res < 1e-13 and orth < 1e-13 and ok
+
+
+def test_identity_sketch_hook_requires_d_equal_m():
+    assert oracle.bqrrp_status(W.gaussian(30, 20, 1), 4, 29, sketch_kind=2) == -6
+
+
 # ----------------------------------------------------------------- LUPP
 @pytest.mark.parametrize("shape", [(200, 30), (30, 30), (20, 40)])
 def test_lupp_matches_lapack_dgetrf(shape):
