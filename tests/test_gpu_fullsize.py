@@ -8,6 +8,8 @@ form.  The oracle cannot factor 16384^2 in a test's time, so it is held to:
   - a sampled oracle output: the first block's b pivots, recomputed on the host
     from the oracle's own sketch operator (a library matmul for S A) and the
     oracle's LU with partial pivoting, compared where every LU step is gapped.
+The largest configured size, 32768^2, is held to the same properties through
+Gaussian probes (below).
 """
 import numpy as np
 import pytest
@@ -54,3 +56,61 @@ def test_full_size_factorization(problem, precision):
     QtQ.diagonal().sub_(1.0)
     orth = torch.linalg.norm(QtQ)
     assert res.item() <= 1e-12 and orth.item() <= 1e-12, (precision, res.item(), orth.item())
+
+
+def apply_q(F, tau, Z, transpose=False, nb=256):
+    """Q Z (or Q^T Z) for Q = H_0 H_1 ... H_{k-1}, the reflectors stored
+    GEQRF-style below the diagonal of F, applied by blocks of nb in the
+    compact WY form H_s ... H_{e-1} = I - V T V^T, with T upper triangular and
+    T^{-1} = diag(1/tau) + the strict upper triangle of V^T V (the relation of
+    Puglisi; Joffrain et al., "Accumulating Householder transformations,
+    revisited", 2006).  Needs tau != 0."""
+    k = tau.numel()
+    Z = Z.clone()
+    starts = list(range(0, k, nb))
+    for s in (starts if transpose else reversed(starts)):
+        e = min(k, s + nb)
+        V = torch.tril(F[s:, s:e], -1)
+        V.diagonal().fill_(1.0)
+        Tinv = torch.triu(V.T @ V, 1) + torch.diag(1.0 / tau[s:e])
+        W = V.T @ Z[s:]
+        if transpose:       # (I - V T V^T)^T = I - V T^T V^T
+            W = torch.linalg.solve_triangular(Tinv.T, W, upper=False)
+        else:
+            W = torch.linalg.solve_triangular(Tinv, W, upper=True)
+        Z[s:] -= V @ W
+    return Z
+
+
+# The configuration's largest size, m = n = 32768 (b = 256, d = 320, iid
+# N(0,1), FP64), held to the same properties.  No 32768^2 Q is formed: for a
+# matrix E and a probe block X with iid N(0,1) entries (p columns),
+# E ||E X||_F^2 = p ||E||_F^2, so ||E X||_F / sqrt(p) estimates ||E||_F (within
+# a small factor with overwhelming probability at p = 16).  Q is applied to
+# the probes from the reflectors block by block (apply_q).
+def test_largest_size_factorization_probes():
+    m = n = 32768
+    p = 16
+    A0 = W.gaussian_torch(m, n, 2)                                   # column-major, on the device
+    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1)
+    torch.cuda.synchronize()
+    assert rank == n
+    j = jpvt.to(torch.int64) - 1
+    assert torch.equal(torch.sort(j).values, torch.arange(n, device=j.device))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    X = torch.randn(n, p, generator=g, dtype=torch.float64, device="cuda")
+    PX = torch.zeros_like(X)
+    PX[j] = X                                                         # (A P) X = A (P X)
+    lhs = A0 @ PX
+    nA = torch.linalg.norm(A0)
+    del A0, PX
+    RX = torch.triu(F) @ X
+    res = torch.linalg.norm(lhs - apply_q(F, tau, RX)) / (p ** 0.5 * nA)
+    del lhs, RX
+    Y = torch.randn(m, p, generator=g, dtype=torch.float64, device="cuda")
+    QtQY = apply_q(F, tau, apply_q(F, tau, Y), transpose=True)
+    orth = torch.linalg.norm(QtQY - Y) / p ** 0.5
+    del F
+    torch.cuda.empty_cache()
+    assert res.item() <= 1e-12 and orth.item() <= 1e-12, (res.item(), orth.item())
