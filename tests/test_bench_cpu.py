@@ -25,3 +25,19 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_config_names_the_schedule_and_host_lapack_context_runs():
+    import argparse
+    import sys as _sys
+    _sys.path.insert(0, ROOT)
+    import bench
+    a = argparse.Namespace(m=16384, n=16384, b=256, d=320, family="gaussian", sketch="dense", panel="cholqr",
+                           precision="fp64", seed=2, schedule="overlap", workload="single")
+    assert bench.config(a, 1)["schedule"] == "overlap"
+    a.panel = "hqr"
+    assert bench.config(a, 1)["schedule"] == "serial"           # the Householder panel runs serially
+    a.panel, a.precision = "cholqr", "mixed"
+    assert bench.config(a, 1)["schedule"] == "serial"           # so does the mixed form
+    ctx = bench.host_lapack_context(a, s=256)
+    assert ctx["geqp3_gflops"] > 0 and ctx["geqrf_gflops"] > 0 and ctx["size"] == "256x256"
