@@ -369,7 +369,7 @@ size_t bqrrp_batch_workspace_bytes(bqrrp_batch_plan plan);
 
 /* Factor the whole batch (device pointers; trunc_rank and info may be NULL).
  * The first call with a given workspace uploads the plan into it
- * (synchronous copy); later calls reuse it, so the workspace must not be
+ * (copies queued on `stream` ahead of the launches); later calls reuse it, so the workspace must not be
  * modified between calls.  use_graph != 0 captures the launch sequence into a
  * CUDA graph on the first call (on a private stream of the plan) and replays it
  * on `stream` while (A, jpvt, tau, rank, trunc_rank, info, workspace) stay the
@@ -382,6 +382,19 @@ int bqrrp_batch_factor(bqrrp_batch_plan plan, double* A, int64_t* jpvt, double* 
 
 /* Release a plan (and its captured graph).  NULL is ignored. */
 void bqrrp_batch_plan_destroy(bqrrp_batch_plan plan);
+
+/* Launch form of a plan (the arithmetic, and so every result, is the same bit
+ * for bit in both forms):
+ *  BQRRP_BATCH_PERSISTENT (default): one persistent kernel whose thread blocks
+ *    take tasks from device queues, each matrix advancing phase by phase as
+ *    soon as its previous phase is done;
+ *  BQRRP_BATCH_LOCKSTEP: one short kernel per phase and block iteration over
+ *    the whole batch (leaves SMs to concurrent work between launches; the
+ *    serving loop's small lane uses it).
+ * Changing the form drops a captured graph.  Errors: -1 null plan, -2 form. */
+#define BQRRP_BATCH_PERSISTENT 0
+#define BQRRP_BATCH_LOCKSTEP 1
+int bqrrp_batch_plan_set_form(bqrrp_batch_plan plan, int form);
 
 /* Number of kernel launches one bqrrp_batch_factor call issues. */
 int bqrrp_batch_launches(bqrrp_batch_plan plan);

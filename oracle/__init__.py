@@ -33,12 +33,13 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (plain -O2, IEEE
-    arithmetic: no fast-math and no FMA contraction)."""
+    arithmetic: no fast-math and no FMA contraction; OpenMP for the loops over
+    independent columns, which leaves every result bit for bit unchanged)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -68,8 +69,20 @@ def lib():
             L.bqrrp_ref_trunc_rank.restype = _i64
             L.bqrrp_ref_fro_norm.argtypes = [_i64, _i64, _dp, _i64]
             L.bqrrp_ref_fro_norm.restype = ctypes.c_double
+            L.bqrrp_ref_set_threads.argtypes = [ctypes.c_int]
+            L.bqrrp_ref_get_threads.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+def set_threads(t):
+    """Threads of the oracle's parallel loops (1, the default, runs serially).
+    The results are identical for every thread count."""
+    lib().bqrrp_ref_set_threads(int(t))
+
+
+def get_threads():
+    return int(lib().bqrrp_ref_get_threads())
 
 
 def _f(a):

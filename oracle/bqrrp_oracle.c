@@ -35,12 +35,18 @@
  *    ||R(i:, i:)||_F <= tol * ||A||_F, the residual measure of Sec. 6, with the
  *    rows at and below the factorization's rank counted as zero.
  *
+ * Threads: the loops over independent columns (or rows) carry an OpenMP
+ * "parallel for"; each iteration runs the same plain loop in the same order
+ * as before, so the results are bit for bit the same for any thread count.
+ * The thread count is 1 unless bqrrp_ref_set_threads() raises it.
+ *
  * Parity status: every routine here is pinned by tests/test_oracle_*.py
  * (library cross-checks, closed forms, brute force, invariants) except the
  * numeric ratio curves of the Kahan experiment (Sec. 6), whose figures are
  * not in the text: parity unpinned for that experiment only.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -49,6 +55,12 @@
 
 /* Return codes, mirrored (not shared) by the CUDA library's own header. */
 enum { REF_OK = 0, REF_ENOMEM = 1, REF_ENUMERIC = 3 };
+
+/* Thread count of the parallel loops (1 = serial, the default). */
+static int g_threads = 1;
+void bqrrp_ref_set_threads(int t) { g_threads = t > 0 ? t : 1; }
+int bqrrp_ref_get_threads(void) { return g_threads; }
+#define PAR_FOR _Pragma("omp parallel for schedule(static) num_threads(g_threads)")
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
@@ -85,6 +97,7 @@ void bqrrp_ref_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 void bqrrp_ref_sketch_dense(int64_t d, int64_t m, uint64_t seed, double* S)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    PAR_FOR
     for (int64_t j = 0; j < m; ++j) {
         for (int64_t r = 0; r < d; ++r) {
             uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(r / 128), 0u, 0u};
@@ -133,6 +146,7 @@ int bqrrp_ref_sketch_sparse(int64_t d, int64_t m, uint64_t seed, int64_t nnz, do
 void bqrrp_ref_sketch_apply(int64_t d, int64_t m, int64_t n, const double* S,
                             const double* A, int64_t lda, double* Msk, int64_t ldsk)
 {
+    PAR_FOR
     for (int64_t j = 0; j < n; ++j)
         for (int64_t r = 0; r < d; ++r) {
             double acc = 0.0;
@@ -166,6 +180,7 @@ static void apply_house(int64_t len, const double* vtail, double tau,
                         double* C, int64_t ldc, int64_t ncols)
 {
     if (tau == 0.0) return;
+    PAR_FOR
     for (int64_t c = 0; c < ncols; ++c) {
         double* col = C + (size_t)c * (size_t)ldc;
         double w = col[0];
@@ -257,6 +272,7 @@ int64_t bqrrp_ref_lupp(int64_t N, int64_t d, double* X, int64_t ldx, int64_t* ip
         double piv = AT(X, j, j, ldx);
         if (piv != 0.0) {
             for (int64_t t = j + 1; t < N; ++t) AT(X, t, j, ldx) /= piv;
+            PAR_FOR
             for (int64_t c = j + 1; c < d; ++c) {
                 double u = AT(X, j, c, ldx);
                 for (int64_t t = j + 1; t < N; ++t) AT(X, t, c, ldx) -= AT(X, t, j, ldx) * u;
@@ -283,6 +299,7 @@ void bqrrp_ref_piv_transform(int64_t N, int64_t steps, const int64_t* ipiv, int6
 static void col_gather(int64_t rows, int64_t ncols, const double* in, int64_t ldin,
                        const int64_t* J, double* out, int64_t ldout)
 {
+    PAR_FOR
     for (int64_t t = 0; t < ncols; ++t)
         for (int64_t i = 0; i < rows; ++i) AT(out, i, t, ldout) = AT(in, i, J[t], ldin);
 }
@@ -295,6 +312,7 @@ static void col_gather(int64_t rows, int64_t ncols, const double* in, int64_t ld
  * row-wise forward substitution. */
 static void trsm_right_upper(int64_t rows, int64_t k, const double* R, int64_t ldr, double* X, int64_t ldx)
 {
+    PAR_FOR
     for (int64_t i = 0; i < rows; ++i)
         for (int64_t j = 0; j < k; ++j) {
             double s = AT(X, i, j, ldx);
@@ -342,6 +360,7 @@ void bqrrp_ref_orhr_col(int64_t rows, int64_t k, double* Q, int64_t ldq, double*
         AT(Q, j, j, ldq) = a - s;
         double piv = AT(Q, j, j, ldq);
         for (int64_t i = j + 1; i < rows; ++i) AT(Q, i, j, ldq) /= piv;
+        PAR_FOR
         for (int64_t c = j + 1; c < k; ++c) {
             double u = AT(Q, j, c, ldq);
             for (int64_t i = j + 1; i < rows; ++i) AT(Q, i, c, ldq) -= AT(Q, i, j, ldq) * u;
@@ -355,6 +374,7 @@ void bqrrp_ref_orhr_col(int64_t rows, int64_t k, double* Q, int64_t ldq, double*
         }
     /* T = -U*S*Y1^{-T}:  solve T * Y1^T = B with B = -U*S (columns of U
      * scaled by -s_j); Y1^T is unit upper, so T is found row by row. */
+    PAR_FOR
     for (int64_t i = 0; i < k; ++i)
         for (int64_t j = 0; j < k; ++j) {
             double bij = -AT(U, i, j, k) * D[j];
@@ -381,19 +401,38 @@ static int has_nonfinite(int64_t rows, int64_t cols, const double* X, int64_t ld
 /* Apply Q_curr^T = (H_1 ... H_k)^T to C (rows x ncols): H_1 first (ORMQR,
  * Sec. 2.4).  Y holds the reflectors (unit diagonal explicit), tau their
  * scalars.  Only the first `keep_rows` rows of the result are written back. */
+static void apply_qt_col(int64_t rows, int64_t k, const double* Y, int64_t ldy, const double* tau,
+                         double* col, int64_t keep_rows, double* scratch)
+{
+    for (int64_t i = 0; i < rows; ++i) scratch[i] = col[i];
+    for (int64_t j = 0; j < k; ++j) {
+        double w = 0.0;
+        for (int64_t i = j; i < rows; ++i) w += AT(Y, i, j, ldy) * scratch[i];
+        w *= tau[j];
+        for (int64_t i = j; i < rows; ++i) scratch[i] -= w * AT(Y, i, j, ldy);
+    }
+    for (int64_t i = 0; i < keep_rows; ++i) col[i] = scratch[i];
+}
+
 static void apply_qt(int64_t rows, int64_t k, const double* Y, int64_t ldy, const double* tau,
                      double* C, int64_t ldc, int64_t ncols, int64_t keep_rows, double* scratch)
 {
-    for (int64_t c = 0; c < ncols; ++c) {
-        for (int64_t i = 0; i < rows; ++i) scratch[i] = AT(C, i, c, ldc);
-        for (int64_t j = 0; j < k; ++j) {
-            double w = 0.0;
-            for (int64_t i = j; i < rows; ++i) w += AT(Y, i, j, ldy) * scratch[i];
-            w *= tau[j];
-            for (int64_t i = j; i < rows; ++i) scratch[i] -= w * AT(Y, i, j, ldy);
-        }
-        for (int64_t i = 0; i < keep_rows; ++i) AT(C, i, c, ldc) = scratch[i];
+    const int nt = g_threads;
+    double* all = nt > 1 ? (double*)malloc(sizeof(double) * (size_t)(rows > 0 ? rows : 1) * (size_t)nt) : NULL;
+    if (!all) {
+        for (int64_t c = 0; c < ncols; ++c)
+            apply_qt_col(rows, k, Y, ldy, tau, &AT(C, 0, c, ldc), keep_rows, scratch);
+        return;
     }
+    /* one scratch column per thread */
+    #pragma omp parallel num_threads(nt)
+    {
+        double* sc = all + (size_t)omp_get_thread_num() * (size_t)(rows > 0 ? rows : 1);
+        #pragma omp for schedule(static)
+        for (int64_t c = 0; c < ncols; ++c)
+            apply_qt_col(rows, k, Y, ldy, tau, &AT(C, 0, c, ldc), keep_rows, sc);
+    }
+    free(all);
 }
 
 /* Alg. 3 on one panel.  Mp: rows x w permuted panel (read only); Rsk: upper
@@ -410,6 +449,7 @@ static int64_t ref_cholqr_panel(int64_t rows, int64_t w, int64_t k, const double
     for (int64_t j = 0; j < k; ++j)
         for (int64_t i = 0; i < rows; ++i) AT(Y, i, j, ldy) = AT(Mp, i, j, ldm);
     trsm_right_upper(rows, k, Rsk, ldr, Y, ldy);                  /* Pre = M(:,0:k) Rsk11^{-1} */
+    PAR_FOR
     for (int64_t j = 0; j < k; ++j)                                /* G = Pre^T Pre */
         for (int64_t l = 0; l < k; ++l) {
             double acc = 0.0;
@@ -421,6 +461,7 @@ static int64_t ref_cholqr_panel(int64_t rows, int64_t w, int64_t k, const double
     trsm_right_upper(rows, k, Rc, ldb, Y, ldy);                   /* Qc = Pre Rchol^{-1} */
     bqrrp_ref_orhr_col(rows, k, Y, ldy, T, ldb, D);               /* Y, T, D */
     /* R11 = diag(D) * Rchol * Rsk(0:k, 0:w)  (k x w) */
+    PAR_FOR
     for (int64_t j = 0; j < w; ++j)
         for (int64_t i = 0; i < k; ++i) {
             double acc = 0.0;
@@ -544,6 +585,7 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
             bqrrp_ref_qrcp_bg(d, N, Ssk, d, Jsk, sktau);     /* R of the permuted sketch, in place */
             for (int64_t t = 0; t < N; ++t) Jsk[t] -= 1;
         } else {
+            PAR_FOR
             for (int64_t t = 0; t < N; ++t)                    /* X = Ssk^T, N x d */
                 for (int64_t r = 0; r < d; ++r) AT(X, t, r, N) = AT(Ssk, r, t, d);
             int64_t steps = bqrrp_ref_lupp(N, d, X, N, ipiv, &margin);
@@ -573,6 +615,7 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
 
         /* ---- permute M(:, s:) and J(s:) (Alg. 1 permute steps, merged) ---- */
         col_gather(m, N, &AT(A, 0, s, lda), lda, Jsk, tmp, m);
+        PAR_FOR
         for (int64_t t = 0; t < N; ++t)
             for (int64_t i = 0; i < m; ++i) AT(A, i, s + t, lda) = AT(tmp, i, t, m);
         for (int64_t t = 0; t < N; ++t) Jt[t] = J[s + Jsk[t]];
@@ -637,6 +680,7 @@ int bqrrp_ref_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, in
         for (int64_t j = 0; j < w; ++j)                      /* Z = Rsk11 */
             for (int64_t i = 0; i < w; ++i) AT(Z, i, j, b) = (i <= j) ? AT(Ssk, i, j, d) : 0.0;
         trsm_right_upper(w, w, R11, b, Z, b);                 /* Z = Rsk11 R11^{-1} */
+        PAR_FOR
         for (int64_t t = 0; t < n - c; ++t)                   /* Rsk12 -= Z * R12 */
             for (int64_t i = 0; i < w; ++i) {
                 double acc = 0.0;

@@ -26,6 +26,7 @@ SKETCH_DENSE, SKETCH_SPARSE = 0, 1
 PANEL_CHOLQR, PANEL_HQR = 0, 1
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 SCHEDULE_OVERLAP, SCHEDULE_SERIAL = 0, 1
+BATCH_PERSISTENT, BATCH_LOCKSTEP = 0, 1
 
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
@@ -112,6 +113,7 @@ _SIGS = {
     "bqrrp_batch_factor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_int], ctypes.c_int),
     "bqrrp_batch_plan_destroy": ([_vp], None),
     "bqrrp_batch_launches": ([_vp], ctypes.c_int),
+    "bqrrp_batch_plan_set_form": ([_vp, ctypes.c_int], ctypes.c_int),
     "bqrrp_batch_flops": ([_vp, ctypes.c_int], _d),
     "bqrrp_batch_autotune_workspace_bytes": ([_i64, _vp, _vp], _sz),
     "bqrrp_batch_autotune": ([_i64, _vp, _vp, _vp, _vp, _d, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(_d)],
@@ -498,6 +500,10 @@ class BatchPlan:
     def launches(self):
         return int(lib().bqrrp_batch_launches(self.handle))
 
+    def set_form(self, form):
+        """BATCH_PERSISTENT (default) or BATCH_LOCKSTEP launch form."""
+        _check("bqrrp_batch_plan_set_form", lib().bqrrp_batch_plan_set_form(self.handle, int(form)))
+
     def flops(self, phase=-1):
         return float(lib().bqrrp_batch_flops(self.handle, int(phase)))
 
@@ -543,7 +549,8 @@ def bqrrp_batch_autotune(m, n, seeds, A, trunc_tol=1e-8, stream=None):
     return b, d, best.value
 
 
-def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False, stream=None):
+def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False, stream=None,
+                   form=BATCH_PERSISTENT):
     """Factor a copy of a packed batch.  Returns (F packed, jpvt, tau, rank,
     trunc_rank, info) as device tensors."""
     torch = _torch()
@@ -558,6 +565,7 @@ def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False,
     info = torch.empty(max(nb, 1), dtype=torch.int32, device=F.device)
     plan = BatchPlan(m, n, b, d, seeds, trunc_tol)
     try:
+        plan.set_form(form)
         plan.factor(F, jpvt, tau, rank, trunc, info, use_graph=use_graph, stream=stream)
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     finally:

@@ -1613,8 +1613,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
         if (cap + hcap >= (1ull << 31)) { set_error("batched: too many tasks"); delete P; return BQRRP_EUNSUPPORTED; }
         P->qcap = (unsigned int)std::max<unsigned long long>(cap, 1);
         P->hcap = (unsigned int)std::max<unsigned long long>(hcap, 1);
-        const char* env = getenv("BQRRP_BATCH_LOCKSTEP");
-        P->mega = !(env && env[0] && env[0] != '0');
+        P->mega = true;   // the dependency-driven form; bqrrp_batch_plan_set_form selects the other
     }
 
     // launch list and work queues
@@ -1732,16 +1731,23 @@ int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, co
 
 size_t batch_plan_bytes(const BatchPlan* P) { return P ? P->total : 0; }
 
-static int batch_upload(BatchPlan* P, char* ws) {
+// Copies on the caller's stream, so they are ordered after its earlier work
+// (a previous plan's kernels on the same workspace) and before this call's
+// launches.  The sources are host memory the plan owns, or `img`, which is
+// pageable: cudaMemcpyAsync stages pageable memory before it returns, so
+// `img` may go out of scope afterwards.
+static int batch_upload(BatchPlan* P, char* ws, cudaStream_t stream) {
     // records and launch queues up to the counters, then the initial task order
     std::vector<char> img(P->o_ctr);
     if (P->batch > 0) std::memcpy(img.data() + P->o_mats, P->mats.data(), sizeof(BatMat) * P->batch);
     if (!P->smat.empty()) std::memcpy(img.data() + P->o_smat, P->smat.data(), sizeof(int) * P->smat.size());
     if (!P->spre.empty()) std::memcpy(img.data() + P->o_spre, P->spre.data(), sizeof(int) * P->spre.size());
-    BQ_CUDA(cudaMemcpy(ws, img.data(), img.size(), cudaMemcpyHostToDevice));
+    BQ_CUDA(cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, stream));
     if (!P->order.empty()) {
-        BQ_CUDA(cudaMemcpy(ws + P->o_order, P->order.data(), sizeof(int) * P->order.size(), cudaMemcpyHostToDevice));
-        BQ_CUDA(cudaMemcpy(ws + P->o_hot, P->hot.data(), sizeof(int) * P->hot.size(), cudaMemcpyHostToDevice));
+        BQ_CUDA(cudaMemcpyAsync(ws + P->o_order, P->order.data(), sizeof(int) * P->order.size(),
+                                cudaMemcpyHostToDevice, stream));
+        BQ_CUDA(cudaMemcpyAsync(ws + P->o_hot, P->hot.data(), sizeof(int) * P->hot.size(), cudaMemcpyHostToDevice,
+                                stream));
     }
     P->uploaded_ws = ws;
     return 0;
@@ -1853,7 +1859,7 @@ int batch_factor(BatchPlan* P, double* A, int64_t* jpvt, double* tau, int64_t* r
             cudaGraphExecDestroy(P->gexec);
             P->gexec = nullptr;
         }
-        BQ_TRY(batch_upload(P, w));
+        BQ_TRY(batch_upload(P, w, stream));
     }
     BatArgs a;
     a.mats = (const BatMat*)(w + P->o_mats);
@@ -1913,7 +1919,12 @@ void batch_plan_set_grid_cap(BatchPlan* P, int ctas) {
 }
 
 void batch_plan_set_lockstep(BatchPlan* P, bool on) {
-    if (P) P->mega = !on;
+    if (!P || P->mega == !on) return;
+    P->mega = !on;
+    if (P->gexec) {   // a captured graph holds the other form's launches
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+    }
 }
 
 double batch_plan_flops(const BatchPlan* P, int phase) {
@@ -2141,6 +2152,14 @@ int bqrrp_batch_factor(bqrrp_batch_plan plan, double* A, int64_t* jpvt, double* 
 
 void bqrrp_batch_plan_destroy(bqrrp_batch_plan plan) {
     bq::batch_plan_destroy(reinterpret_cast<bq::BatchPlan*>(plan));
+}
+
+int bqrrp_batch_plan_set_form(bqrrp_batch_plan plan, int form) {
+    bq::set_error("");
+    if (!plan) return -1;
+    if (form != BQRRP_BATCH_PERSISTENT && form != BQRRP_BATCH_LOCKSTEP) return -2;
+    bq::batch_plan_set_lockstep(reinterpret_cast<bq::BatchPlan*>(plan), form == BQRRP_BATCH_LOCKSTEP);
+    return 0;
 }
 
 int bqrrp_batch_launches(bqrrp_batch_plan plan) {

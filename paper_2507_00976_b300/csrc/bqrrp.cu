@@ -129,6 +129,26 @@ struct PhaseRec {
     }
 };
 
+int kernel_attrs(const void* fn, int smem_bytes, bool nonportable_cluster) {
+    struct Rec {
+        int dev;
+        const void* fn;
+        int smem;
+        bool cluster;
+    };
+    static std::mutex mu;
+    static std::vector<Rec> done;
+    int id = 0;
+    BQ_CUDA(cudaGetDevice(&id));
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Rec& r : done)
+        if (r.dev == id && r.fn == fn && r.smem >= smem_bytes && (r.cluster || !nonportable_cluster)) return 0;
+    if (nonportable_cluster) BQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    BQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+    done.push_back(Rec{id, fn, smem_bytes, nonportable_cluster});
+    return 0;
+}
+
 int current_device(Device* dev) {
     static std::mutex mu;
     static int cached_sms[64] = {0};

@@ -111,6 +111,10 @@ struct Device {
     int sms = 148;
 };
 int current_device(Device* dev);
+// Kernel attributes are per device: raise `fn`'s dynamic shared-memory limit
+// to at least smem_bytes (and allow non-portable cluster sizes when asked) on
+// the current device, once per (device, kernel); the CUDA result is checked.
+int kernel_attrs(const void* fn, int smem_bytes, bool nonportable_cluster = false);
 
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11: two-word key, four-word counter, ten rounds.

@@ -22,10 +22,6 @@
 // products S A_q.
 #include <cuda_bf16.h>
 
-#include <cstdlib>
-
-#include <mutex>
-
 #include "common.cuh"
 
 namespace bq {
@@ -33,10 +29,7 @@ namespace bq {
 namespace {
 
 constexpr int kSlices = 9;     // 6-bit slices per FP64 operand (54 bits)
-constexpr int kTmax = 9;       // keep slice pairs with p + q <= kTmax
-constexpr int OBM = 64, OBN = 32, OBK = 32;
-constexpr int OPAD = 40;       // smem row length (bf16) of a 32-deep k tile: 80 bytes
-constexpr int ONT = 256;
+constexpr int OBM = 64, OBN = 32, OBK = 32;   // padding of the slice planes (rows, rows, k)
 
 __device__ __forceinline__ int exp_above(double m) {
     // smallest e with m < 2^e (m >= 0); 0 for m == 0
@@ -127,191 +120,11 @@ __global__ void sketch_slice_kernel(i64 d, i64 m, i64 Rp, i64 ldk, uint64_t seed
     }
 }
 
+inline i64 rup(i64 x, i64 m) { return (x + m - 1) / m * m; }
+
 __global__ void fill_int_kernel(int* x, i64 n, int v) {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = v;
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
-}
-
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                         unsigned b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-struct OzArgs {
-    i64 M, N, K;          // logical sizes
-    i64 ldk;              // padded K (row length of the slices), multiple of OBK
-    i64 sa_stride, sb_stride;   // elements between consecutive slices
-    const __nv_bfloat16* As;    // [SA][Mp][ldk]
-    const __nv_bfloat16* Bs;    // [SB][Np][ldk]
-    const int* ea;        // row exponents of op(A)
-    const int* eb;        // column exponents of op(B)
-    double alpha, beta;
-    double* C;
-    i64 ldc;
-    i64 kc;               // K chunk between FP64 flushes (multiple of OBK)
-};
-
-// C tile 64 x 32 per CTA; 8 warps as 4 (M) x 2 (N), each 16 x 16 (one m16,
-// two n8).  Per k16 step a warp keeps the fragments of all SA slices of its A
-// rows in registers and loads each B slice once; the products of group
-// t = p + q accumulate in acc[t] (FP32, exact), flushed to FP64 every p.kc.
-template <int SA, int SB, int TMAX>
-__global__ void __launch_bounds__(ONT, 1) ozaki_mma_kernel(OzArgs p) {
-    constexpr int NG = TMAX + 1;                       // groups t = 0..TMAX
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(smraw);
-    constexpr int A_ELEMS = SA * OBM * OPAD, B_ELEMS = SB * OBN * OPAD;
-    constexpr int STAGE = A_ELEMS + B_ELEMS;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 3, wn = warp >> 2;
-    const i64 m0 = (i64)blockIdx.x * OBM, n0 = (i64)blockIdx.y * OBN;
-
-    double acc64[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc64[j][r] = 0.0;
-
-    auto load_stage = [&](int buf, i64 k0) {
-        __nv_bfloat16* sa = sm + buf * STAGE;
-        __nv_bfloat16* sb = sa + A_ELEMS;
-        constexpr int CH_A = SA * OBM * (OBK / 8), CH_B = SB * OBN * (OBK / 8);
-        for (int c = tid; c < CH_A + CH_B; c += ONT) {
-            if (c < CH_A) {
-                const int s = c / (OBM * 4), rem = c % (OBM * 4), row = rem / 4, kk = (rem % 4) * 8;
-                cp_async16(sa + (s * OBM + row) * OPAD + kk,
-                           p.As + (size_t)s * p.sa_stride + (size_t)(m0 + row) * p.ldk + k0 + kk);
-            } else {
-                const int cc = c - CH_A;
-                const int s = cc / (OBN * 4), rem = cc % (OBN * 4), row = rem / 4, kk = (rem % 4) * 8;
-                cp_async16(sb + (s * OBN + row) * OPAD + kk,
-                           p.Bs + (size_t)s * p.sb_stride + (size_t)(n0 + row) * p.ldk + k0 + kk);
-            }
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-    };
-
-    const i64 K = p.ldk;
-    int buf = 0;
-    load_stage(0, 0);
-    for (i64 kc0 = 0; kc0 < K; kc0 += p.kc) {
-        const i64 kc1 = (kc0 + p.kc < K) ? kc0 + p.kc : K;
-        float acc[NG][2][4];
-#pragma unroll
-        for (int t = 0; t < NG; ++t)
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) acc[t][j][r] = 0.f;
-        for (i64 k0 = kc0; k0 < kc1; k0 += OBK) {
-            const i64 kn = k0 + OBK;
-            if (kn < K) {
-                load_stage(buf ^ 1, kn);
-                asm volatile("cp.async.wait_group 1;\n" ::);
-            } else {
-                asm volatile("cp.async.wait_group 0;\n" ::);
-            }
-            __syncthreads();
-            const __nv_bfloat16* sa = sm + buf * STAGE;
-            const __nv_bfloat16* sb = sa + A_ELEMS;
-#pragma unroll
-            for (int kk = 0; kk < OBK; kk += 16) {
-                unsigned a[SA][4];
-                const int arow = wm * 16 + (lane & 15);
-                const int akof = kk + ((lane >> 4) << 3);
-#pragma unroll
-                for (int pa = 0; pa < SA; ++pa)
-                    ldsm_x4(a[pa][0], a[pa][1], a[pa][2], a[pa][3], sa + (pa * OBM + arow) * OPAD + akof);
-                const int nrow = wn * 16 + ((lane >> 4) << 3) + (lane & 7);
-                const int bkof = kk + (((lane >> 3) & 1) << 3);
-#pragma unroll
-                for (int q = 0; q < SB; ++q) {
-                    unsigned b00, b01, b10, b11;
-                    ldsm_x4(b00, b01, b10, b11, sb + (q * OBN + nrow) * OPAD + bkof);
-#pragma unroll
-                    for (int pa = 0; pa < SA; ++pa) {
-                        if (pa + q > TMAX) continue;
-                        mma_bf16(acc[pa + q][0], a[pa][0], a[pa][1], a[pa][2], a[pa][3], b00, b01);
-                        mma_bf16(acc[pa + q][1], a[pa][0], a[pa][1], a[pa][2], a[pa][3], b10, b11);
-                    }
-                }
-            }
-            __syncthreads();
-            buf ^= 1;
-        }
-        // flush the exact group sums (integers below 2^24) into FP64 with weights
-        // 2^-6t.  Groups t <= 4 and t >= 5 are first combined exactly in 64-bit
-        // integers by Horner steps of 2^6 (each below 2^53), so the FP64 pipe
-        // sees two conversions and two FMAs per element instead of one per group.
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                long long hi = 0, lo = 0;
-#pragma unroll
-                for (int t = 0; t < NG && t <= 4; ++t) hi = hi * 64 + (long long)__float2int_rz(acc[t][j][r]);
-#pragma unroll
-                for (int t = 5; t < NG; ++t) lo = lo * 64 + (long long)__float2int_rz(acc[t][j][r]);
-                const int nhi = (NG < 5) ? NG : 5;
-                acc64[j][r] = fma((double)hi, ldexp(1.0, -6 * (nhi - 1)), acc64[j][r]);
-                if (NG > 5) acc64[j][r] = fma((double)lo, ldexp(1.0, -6 * (NG - 1)), acc64[j][r]);
-            }
-    }
-    // epilogue: C = alpha 2^(ea_i + eb_j - 12) acc + beta C
-    const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const i64 row = m0 + wm * 16 + g + ((r >> 1) << 3);
-            const i64 col = n0 + wn * 16 + j * 8 + 2 * tq + (r & 1);
-            if (row < p.M && col < p.N) {
-                const double v = p.alpha * ldexp(acc64[j][r], p.ea[row] + p.eb[col] - 12);
-                double* cp = p.C + row + col * p.ldc;
-                *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);
-            }
-        }
-    }
-}
-
-inline i64 rup(i64 x, i64 m) { return (x + m - 1) / m * m; }
-
-template <int SA, int SB, int TMAX>
-int launch_mma(const Ctx& c, OzArgs a, i64 Mp, i64 Np) {
-    const size_t smem = 2ull * (size_t)(SA * OBM + SB * OBN) * OPAD * sizeof(__nv_bfloat16);
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(ozaki_mma_kernel<SA, SB, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (Np / OBN > 65535) { set_error("ozaki: N too large"); return BQRRP_EUNSUPPORTED; }
-    dim3 grid((unsigned)(Mp / OBM), (unsigned)(Np / OBN));
-    ozaki_mma_kernel<SA, SB, TMAX><<<grid, ONT, smem, c.stream>>>(a);
-    BQ_LAUNCH_CHECK();
-    return 0;
-}
-
-// The tcgen05 kernel (ozaki_tc.cu) runs the slice products unless
-// BQRRP_OZAKI_MMA is set in the environment, which selects the mma.sync
-// kernel above (kept for side-by-side timing).
-bool use_tcgen05() {
-    static const bool tc = (getenv("BQRRP_OZAKI_MMA") == nullptr);
-    return tc;
 }
 
 // After a launch on a context without a status block: read the kernel's
@@ -367,13 +180,6 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
     split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32)), 256, 0, c.stream>>>(N, K, Np, Kp, B, ldb,
                                                                                       tb ? 0 : 1, eb, Bs);
     BQ_LAUNCH_CHECK();
-    OzArgs a{};
-    a.M = M; a.N = N; a.K = K; a.ldk = Kp;
-    a.sa_stride = Mp * Kp; a.sb_stride = Np * Kp;
-    a.As = As; a.Bs = Bs; a.ea = ea; a.eb = eb;
-    a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc;
-    a.kc = 256;
-    if (!use_tcgen05()) return launch_mma<kSlices, kSlices, kTmax>(c, a, Mp, Np);
     int* err = c.st ? &c.st->err_timeout : flag;
     if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
     BQ_TRY(ozaki_tc_gemm(c, As, Mp, Bs, Np, Kp, M, N, ea, eb, alpha, beta, C, ldc, err));
@@ -415,13 +221,6 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     BQ_LAUNCH_CHECK();
     split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32)), 256, 0, c.stream>>>(n, m, Np, Kp, A, lda, 1, eb, Bs);
     BQ_LAUNCH_CHECK();
-    OzArgs a{};
-    a.M = d; a.N = n; a.K = m; a.ldk = Kp;
-    a.sa_stride = Mp * Kp; a.sb_stride = Np * Kp;
-    a.As = Ss; a.Bs = Bs; a.ea = ea; a.eb = eb;
-    a.alpha = 1.0; a.beta = 0.0; a.C = Msk; a.ldc = ldsk;
-    a.kc = (i64)1 << 17;
-    if (!use_tcgen05()) return launch_mma<1, kSlices, kSlices - 1>(c, a, Mp, Np);
     int* err = c.st ? &c.st->err_timeout : flag;
     if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
     BQ_TRY(ozaki_tc_sketch(c, Ss, Mp, Bs, Np, Kp, d, n, ea, eb, Msk, ldsk, err));

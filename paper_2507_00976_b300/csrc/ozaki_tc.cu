@@ -419,10 +419,7 @@ int launch_tc(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16
     BQ_TRY(make_plane_map(&tmA, As, ldk, Mp, SA, TC_M, 1));
     BQ_TRY(make_plane_map(&tmB, Bs, ldk, Np, SB, TC_N, SB));
     const size_t smem = 1024 + (size_t)TC_NA * TC_ABYTES + (size_t)TC_NB * SB * TC_BPLANE + 8 * (2 * TC_NA + 2 * TC_NB + 3) + 16;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(ozaki_tc_kernel<SA, SB, TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    BQ_TRY(kernel_attrs((const void*)ozaki_tc_kernel<SA, SB, TMAX>, (int)smem));
     TcArgs a;
     a.M = M;
     a.N = N;

@@ -762,10 +762,7 @@ int getrf_pivots_ex(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv,
                     int stall_cta) {
     const i64 steps = imin(N, d);
     if (steps <= 0) return 0;
-    static std::once_flag attr_set_once;
-    std::call_once(attr_set_once, [&] {
-        cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemLu);
-    });
+    BQ_TRY(kernel_attrs((const void*)lu_panel_kernel, kMaxSmemLu));
     const i64 nbmax = 64;
     const int Gmax_all = (int)imin(c.dev.sms, 148);
     size_t need = 0;
@@ -834,11 +831,7 @@ constexpr i64 kClusterRowsMax = 16 * 280;   // 16 CTAs x 280 rows x 64 columns f
 // cooperative grid kernel), or an error code.
 static int hh_panel_cluster(const Ctx& c, i64 prow, int pw, double* Ap, i64 lda, double* tau, double* V, i64 ldv,
                             double* T, i64 ldt) {
-    static std::once_flag attr_set_once;
-    std::call_once(attr_set_once, [&] {
-        cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(hh_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
-    });
+    BQ_TRY(kernel_attrs((const void*)hh_panel_cluster_kernel, kMaxSmemHh, true));
     int C = (int)imin(16, imax(1, cdiv(prow, 32)));
     i64 R = cdiv(prow, C);
     C = (int)cdiv(prow, R);
@@ -881,10 +874,7 @@ int geqrf_blocked(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* 
     if (kstop >= 0) kk = imin(kk, kstop);   // factor only the first kstop columns, update all
     if (kk <= 0) return 0;
     if (nb > 64) nb = 64;
-    static std::once_flag attr_set_once;
-    std::call_once(attr_set_once, [&] {
-        cudaFuncSetAttribute(hh_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemHh);
-    });
+    BQ_TRY(kernel_attrs((const void*)hh_panel_kernel, kMaxSmemHh));
     const int Gmax_all = (int)imin(c.dev.sms, 148);
     size_t need = 0;
     coop_scratch_elems(nb, Gmax_all, &need);
@@ -1118,11 +1108,7 @@ int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
     int C = 16;
     size_t smem = (size_t)((s + C - 1) / C) * (size_t)d * sizeof(double);
     if (smem > 208 * 1024) return -1;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(small_qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(small_qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 208 * 1024);
-    });
+    BQ_TRY(kernel_attrs((const void*)small_qr_cluster_kernel, 208 * 1024, true));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(NT);

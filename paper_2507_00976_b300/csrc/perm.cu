@@ -156,10 +156,7 @@ int piv_transform_moved(const Ctx& c, i64 N, i64 steps, const i64* ipiv, i64* Js
     if (N <= 0) return 0;
     const size_t smem = (size_t)(N + steps) * sizeof(int);
     int use_smem = smem <= 200 * 1024 ? 1 : 0;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(piv_moved_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
+    BQ_TRY(kernel_attrs((const void*)piv_moved_kernel, 200 * 1024));
     piv_moved_kernel<<<1, PT, use_smem ? smem : 0, c.stream>>>(N, steps, ipiv, Jsk, identity_flag, pos, src, count,
                                                                use_smem, 0, imin(N, 2 * steps));
     BQ_LAUNCH_CHECK();
@@ -172,10 +169,7 @@ int moved_list_given(const Ctx& c, i64 N, i64* J, i64* pos, i64* src, i64* count
     if (N <= 0) return 0;
     const size_t smem = (size_t)N * sizeof(int);
     const int use_smem = smem <= 200 * 1024 ? 1 : 0;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(piv_moved_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
+    BQ_TRY(kernel_attrs((const void*)piv_moved_kernel, 200 * 1024));
     piv_moved_kernel<<<1, PT, use_smem ? smem : 0, c.stream>>>(N, 0, nullptr, J, nullptr, pos, src, count, use_smem, 1,
                                                                max_moved);
     BQ_LAUNCH_CHECK();

@@ -5,7 +5,7 @@
 // per column, the "fast sparse operator" the paper mentions for its tall
 // predecessor, Sec. 2 remark): applied as a deterministic sparse x dense
 // product, reading A once.
-#include <mutex>
+#include <climits>
 
 #include "common.cuh"
 
@@ -18,10 +18,25 @@ constexpr int kMaxNnz = 64;
 // Column j of the sparse-sign operator: nnz distinct rows with signs.  Draw t
 // uses counter (j, 1+t, 0, 0); each output word w proposes row
 // ((w >> 1) * d) >> 31 with sign -1 iff (w & 1); repeated rows are skipped.
+// The draw is bounded at 2^22 counters (2^24 proposals).  For nnz <= d the
+// chance that 2^24 uniform proposals miss one of nnz distinct rows is far
+// below 2^-1000, so the bound is never reached; if it were, the column is
+// completed with the smallest unused rows (sign +1), so that every row index
+// stays in [0, d) whatever happens.  Returns nnz.
 __device__ int sparse_column(uint64_t seed, i64 d, i64 j, int nnz, int* rows, double* sg) {
     int got = 0;
     for (uint32_t t = 0; got < nnz; ++t) {
-        if (t > (1u << 22)) return -1;   // bounded: cannot happen for nnz <= d
+        if (t > (1u << 22)) {
+            for (int r = 0; got < nnz && r < d; ++r) {
+                bool taken = false;
+                for (int e = 0; e < got; ++e) taken |= (rows[e] == r);
+                if (taken) continue;
+                rows[got] = r;
+                sg[got] = 1.0;
+                ++got;
+            }
+            return got;
+        }
         uint32_t o[4];
         philox4x32_10((uint32_t)j, 1u + t, 0u, 0u, (uint32_t)seed, (uint32_t)(seed >> 32), o);
 #pragma unroll
@@ -48,13 +63,12 @@ __global__ void dense_write_kernel(i64 d, i64 m, uint64_t seed, double* S, i64 l
     }
 }
 
-__global__ void sparse_csc_kernel(i64 d, i64 m, uint64_t seed, int nnz, int* rows, double* sg, int* err) {
+__global__ void sparse_csc_kernel(i64 d, i64 m, uint64_t seed, int nnz, int* rows, double* sg) {
     const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     int r[kMaxNnz];
     double s[kMaxNnz];
-    const int got = sparse_column(seed, d, j, nnz, r, s);
-    if (got != nnz) { atomicOr(err, 1); return; }
+    sparse_column(seed, d, j, nnz, r, s);   // always nnz distinct rows in [0, d)
     for (int q = 0; q < nnz; ++q) {
         rows[j * nnz + q] = r[q];
         sg[j * nnz + q] = s[q];
@@ -62,16 +76,13 @@ __global__ void sparse_csc_kernel(i64 d, i64 m, uint64_t seed, int nnz, int* row
 }
 
 // One thread per column: zero it, then write its nnz signed entries.
-__global__ void sparse_write_direct_kernel(i64 d, i64 m, uint64_t seed, int nnz, double* S, i64 lds, int* err) {
+__global__ void sparse_write_direct_kernel(i64 d, i64 m, uint64_t seed, int nnz, double* S, i64 lds) {
     const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     for (i64 r = 0; r < d; ++r) S[r + j * lds] = 0.0;
     int r[kMaxNnz];
     double s[kMaxNnz];
-    if (sparse_column(seed, d, j, nnz, r, s) != nnz) {
-        if (err) atomicOr(err, 1);
-        return;
-    }
+    sparse_column(seed, d, j, nnz, r, s);
     for (int q = 0; q < nnz; ++q) S[r[q] + j * lds] = s[q];
 }
 
@@ -111,38 +122,67 @@ __global__ void fill_rows_kernel(i64 m, int nnz, const int* rows, const double* 
     val[at] = sg[e];
 }
 
-// sort each CSR row by column (insertion sort; rows hold ~m*nnz/d entries)
-__global__ void sort_rows_kernel(i64 d, const int* ptr, int* col, double* val) {
-    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d) return;
-    const int lo = ptr[r], hi = ptr[r + 1];
-    for (int i = lo + 1; i < hi; ++i) {
-        const int c = col[i];
-        const double v = val[i];
-        int k = i - 1;
-        while (k >= lo && col[k] > c) { col[k + 1] = col[k]; val[k + 1] = val[k]; --k; }
-        col[k + 1] = c;
-        val[k + 1] = v;
+// Sort each CSR row by column, so that the row's sum runs in increasing i
+// whatever order the atomic fill produced (the columns of a row are distinct,
+// so the sorted order is unique).  In-place heapsort: O(k log k) for a row of
+// k entries (k is about m*nnz/d, up to m*nnz when d is small).
+__device__ void sift_down(int* col, double* val, int root, int n) {
+    while (true) {
+        int child = 2 * root + 1;
+        if (child >= n) return;
+        if (child + 1 < n && col[child + 1] > col[child]) ++child;
+        if (col[root] >= col[child]) return;
+        const int tc = col[root];
+        col[root] = col[child];
+        col[child] = tc;
+        const double tv = val[root];
+        val[root] = val[child];
+        val[child] = tv;
+        root = child;
     }
 }
 
-constexpr int SJ = 8;        // columns of A per CTA (each CSR entry feeds SJ FMAs)
-constexpr int SI = 1024;     // rows of A per staged chunk
+__global__ void sort_rows_kernel(i64 d, const int* ptr, int* col, double* val) {
+    const i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d) return;
+    const int lo = ptr[r], n = ptr[r + 1] - lo;
+    int* c = col + lo;
+    double* v = val + lo;
+    for (int i = n / 2 - 1; i >= 0; --i) sift_down(c, v, i, n);
+    for (int end = n - 1; end > 0; --end) {
+        const int tc = c[0];
+        c[0] = c[end];
+        c[end] = tc;
+        const double tv = v[0];
+        v[0] = v[end];
+        v[end] = tv;
+        sift_down(c, v, 0, end);
+    }
+}
+
+constexpr int SJ = 8;          // columns of A per CTA (each CSR entry feeds SJ FMAs)
+constexpr int SI = 1024;       // rows of A per staged chunk
+constexpr i64 kRowTile = 2048; // sketch rows per CTA (larger d is split over blockIdx.y)
 
 // Msk(r, j) = sum over the CSR entries (i, s) of row r, in increasing i, of s*A(i, j).
-// One thread per sketch row r (the block is sized to d, so every row is served
-// in a single pass); the CTA's SJ columns of A are staged in SI-row chunks.
-__global__ void __launch_bounds__(1024) sparse_apply_kernel(i64 d, i64 m, i64 n, const double* __restrict__ A,
+// One thread per sketch row r; CTA (x, y) takes columns [SJ x, SJ x + SJ) of
+// A and sketch rows [y rt, y rt + rt); its columns of A are staged in SI-row
+// chunks (read once per row tile: once in all when d <= kRowTile).
+__global__ void __launch_bounds__(1024) sparse_apply_kernel(i64 d, i64 rt, i64 m, i64 n, const double* __restrict__ A,
                                                             i64 lda, const int* __restrict__ ptr,
                                                             const int* __restrict__ col, const double* __restrict__ val,
                                                             double* Msk, i64 ldsk) {
     extern __shared__ double sm[];
     double* As = sm;                                  // [SJ][SI]
-    double* acc = sm + SJ * SI;                       // [d][SJ]
-    int* cur = reinterpret_cast<int*>(acc + d * SJ);  // [d]
+    double* acc = sm + SJ * SI;                       // [rt][SJ]
+    int* cur = reinterpret_cast<int*>(acc + rt * SJ); // [rt]
     const i64 j0 = (i64)blockIdx.x * SJ;
     const int nj = (int)((j0 + SJ <= n) ? SJ : n - j0);
-    for (i64 r = threadIdx.x; r < d; r += blockDim.x) {
+    const i64 r0 = (i64)blockIdx.y * rt;
+    const i64 nr = (r0 + rt <= d) ? rt : d - r0;      // rows of this tile
+    ptr += r0;
+    Msk += r0;
+    for (i64 r = threadIdx.x; r < nr; r += blockDim.x) {
         cur[r] = ptr[r];
         for (int q = 0; q < SJ; ++q) acc[r * SJ + q] = 0.0;
     }
@@ -154,7 +194,7 @@ __global__ void __launch_bounds__(1024) sparse_apply_kernel(i64 d, i64 m, i64 n,
             As[e] = (q < nj && i < ni) ? A[(i0 + i) + (j0 + q) * lda] : 0.0;
         }
         __syncthreads();
-        for (i64 r = threadIdx.x; r < d; r += blockDim.x) {
+        for (i64 r = threadIdx.x; r < nr; r += blockDim.x) {
             int e = cur[r];
             const int end = ptr[r + 1];
             double a[SJ];
@@ -173,11 +213,13 @@ __global__ void __launch_bounds__(1024) sparse_apply_kernel(i64 d, i64 m, i64 n,
         }
     }
     __syncthreads();
-    for (i64 r = threadIdx.x; r < d; r += blockDim.x)
+    for (i64 r = threadIdx.x; r < nr; r += blockDim.x)
         for (int q = 0; q < nj; ++q) Msk[r + (j0 + q) * ldsk] = acc[r * SJ + q];
 }
 
-size_t sparse_smem(i64 d) { return (size_t)SJ * SI * 8 + (size_t)d * SJ * 8 + (size_t)d * 4 + 64; }
+// Sketch rows per CTA: d split into equal tiles of at most kRowTile rows.
+i64 sparse_row_tile(i64 d) { return cdiv(d, cdiv(d, kRowTile)); }
+size_t sparse_smem(i64 rt) { return (size_t)SJ * SI * 8 + (size_t)rt * SJ * 8 + (size_t)rt * 4 + 64; }
 
 struct SparseWs {
     int* rows;
@@ -187,7 +229,6 @@ struct SparseWs {
     int* fillc;
     int* col;
     double* val;
-    int* err;
 };
 
 size_t carve_sparse(Arena& ar, i64 d, i64 m, i64 nnz, SparseWs* w) {
@@ -199,13 +240,11 @@ size_t carve_sparse(Arena& ar, i64 d, i64 m, i64 nnz, SparseWs* w) {
     w->fillc = ar.take<int>((size_t)d + 1);
     w->col = ar.take<int>(e);
     w->val = ar.take<double>(e);
-    w->err = ar.take<int>(4);
     return ar.off;
 }
 
 int build_csc(const Ctx& c, i64 d, i64 m, uint64_t seed, i64 nnz, SparseWs& w) {
-    BQ_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), c.stream));
-    sparse_csc_kernel<<<(unsigned)cdiv(m, 128), 128, 0, c.stream>>>(d, m, seed, (int)nnz, w.rows, w.sg, w.err);
+    sparse_csc_kernel<<<(unsigned)cdiv(m, 128), 128, 0, c.stream>>>(d, m, seed, (int)nnz, w.rows, w.sg);
     BQ_LAUNCH_CHECK();
     return 0;
 }
@@ -228,8 +267,7 @@ int sketch_write(const Ctx& c, i64 d, i64 m, uint64_t seed, int kind, i64 nnz, d
         return 0;
     }
     if (nnz < 1 || nnz > kMaxNnz || nnz > d) { set_error("sparse sketch: bad nnz"); return BQRRP_EUNSUPPORTED; }
-    sparse_write_direct_kernel<<<(unsigned)cdiv(m, 128), 128, 0, c.stream>>>(d, m, seed, (int)nnz, S, lds,
-                                                                             c.st ? &c.st->err_timeout : nullptr);
+    sparse_write_direct_kernel<<<(unsigned)cdiv(m, 128), 128, 0, c.stream>>>(d, m, seed, (int)nnz, S, lds);
     BQ_LAUNCH_CHECK();
     return 0;
 }
@@ -238,8 +276,9 @@ int sketch_sparse_apply(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, i64 nn
                         double* Msk, i64 ldsk, void* ws, size_t ws_bytes) {
     if (d <= 0 || n <= 0) return 0;
     if (nnz < 1 || nnz > kMaxNnz || nnz > d) { set_error("sparse sketch: bad nnz"); return BQRRP_EUNSUPPORTED; }
-    const size_t smem = sparse_smem(d);
-    if (smem > 220 * 1024) { set_error("sparse sketch: d too large"); return BQRRP_EUNSUPPORTED; }
+    if (d > (i64)1 << 30 || m * nnz >= (i64)1 << 31) { set_error("sparse sketch: shape too large"); return BQRRP_EUNSUPPORTED; }
+    const i64 rt = sparse_row_tile(d);
+    const size_t smem = sparse_smem(rt);
     Arena ar;
     ar.base = (char*)ws;
     ar.cap = ws_bytes;
@@ -259,13 +298,11 @@ int sketch_sparse_apply(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, i64 nn
     BQ_LAUNCH_CHECK();
     sort_rows_kernel<<<(unsigned)cdiv(d, 128), 128, 0, c.stream>>>(d, w.ptr, w.col, w.val);
     BQ_LAUNCH_CHECK();
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(sparse_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    });
-    const int threads = (int)imin(1024, cdiv(d, 32) * 32);
-    sparse_apply_kernel<<<(unsigned)cdiv(n, SJ), threads, smem, c.stream>>>(d, m, n, A, lda, w.ptr, w.col, w.val,
-                                                                             Msk, ldsk);
+    BQ_TRY(kernel_attrs((const void*)sparse_apply_kernel, (int)sparse_smem(kRowTile)));
+    const int threads = (int)imin(1024, cdiv(rt, 32) * 32);
+    if (cdiv(n, SJ) > (i64)INT32_MAX) { set_error("sparse sketch: n too large"); return BQRRP_EUNSUPPORTED; }
+    sparse_apply_kernel<<<dim3((unsigned)cdiv(n, SJ), (unsigned)cdiv(d, rt)), threads, smem, c.stream>>>(
+        d, rt, m, n, A, lda, w.ptr, w.col, w.val, Msk, ldsk);
     BQ_LAUNCH_CHECK();
     return 0;
 }

@@ -41,10 +41,11 @@ def unpack(F, jpvt, tau, m, n):
     return out
 
 
-def run_batch(mats, b, d, seeds, use_graph=False, tol=TOL):
+def run_batch(mats, b, d, seeds, use_graph=False, tol=TOL, form=B.BATCH_PERSISTENT):
     m = np.array([A.shape[0] for A in mats], dtype=np.int64)
     n = np.array([A.shape[1] for A in mats], dtype=np.int64)
-    F, jpvt, tau, rank, trunc, info = B.factor_batched(pack(mats), m, n, b, d, seeds, tol, use_graph=use_graph)
+    F, jpvt, tau, rank, trunc, info = B.factor_batched(pack(mats), m, n, b, d, seeds, tol, use_graph=use_graph,
+                                                       form=form)
     return m, n, np_(F), np_(jpvt), np_(tau), np_(rank), np_(trunc), np_(info)
 
 
@@ -201,18 +202,18 @@ def test_batched_autotune_choices_are_valid_and_meet_the_bar():
     check_against_oracle(sub, b[pick], d[pick], seeds[pick], run_batch(sub, b[pick], d[pick], seeds[pick]))
 
 
-def test_dependency_driven_and_lockstep_forms_agree_bitwise(monkeypatch):
+def test_dependency_driven_and_lockstep_forms_agree_bitwise():
     """The default form runs every phase from one device task queue; the
-    lock-step form (BQRRP_BATCH_LOCKSTEP=1) launches one kernel per phase and
-    iteration.  Both run the same per-phase arithmetic."""
+    lock-step form (bqrrp_batch_plan_set_form(BQRRP_BATCH_LOCKSTEP)) launches
+    one kernel per phase and iteration.  Both run the same per-phase
+    arithmetic."""
     m, n = W.batched_shapes(30, 17, m_hi=500)
     mats = [W.batched_matrix(int(a), int(c), 800 + i) for i, (a, c) in enumerate(zip(m, n))]
     b = np.array([[16, 32, 64][i % 3] for i in range(30)], dtype=np.int64)
     d = np.ceil(1.25 * b).astype(np.int64)
     seeds = np.arange(30, dtype=np.uint64) + 77
     mega = run_batch(mats, b, d, seeds, use_graph=True)
-    monkeypatch.setenv("BQRRP_BATCH_LOCKSTEP", "1")
-    lock = run_batch(mats, b, d, seeds, use_graph=True)
+    lock = run_batch(mats, b, d, seeds, use_graph=True, form=B.BATCH_LOCKSTEP)
     for x, y in zip(mega, lock):
         assert np.array_equal(x, y)
     check_against_oracle(mats[:6], b[:6], d[:6], seeds[:6],

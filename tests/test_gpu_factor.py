@@ -89,6 +89,21 @@ def test_low_rank_at_block_boundary():
     compare(A, 64, 80, 2, expect_rank=128)
 
 
+def test_sparse_sketch_at_the_largest_configured_block():
+    """b = 2048, d = ceil(1.25 b) = 2560 with the sparse sketch (the largest
+    block of the configuration's sweep): the sketch rows exceed one CTA's row
+    tile.  Held to the properties that hold at any size."""
+    import torch
+    from checks import metrics
+    m, n = 3000, 2600
+    A = W.gaussian(m, n, 21)
+    F, jpvt, tau, rank = bq.factor(A, 2048, 2560, 4, sketch="sparse")
+    torch.cuda.synchronize()
+    assert rank == n
+    res, orth, perm_ok = metrics(A, F.cpu().numpy(), jpvt.cpu().numpy(), tau.cpu().numpy(), rank)
+    assert perm_ok and res <= 1e-12 and orth <= 1e-12, (res, orth)
+
+
 def test_sparse_sign_sketch():
     A = W.c1_matrix()
     compare(A, 128, 160, 1, sketch="sparse")

@@ -83,16 +83,18 @@ def apply_q(F, tau, Z, transpose=False, nb=256):
 
 
 # The configuration's largest size, m = n = 32768 (b = 256, d = 320, iid
-# N(0,1), FP64), held to the same properties.  No 32768^2 Q is formed: for a
+# N(0,1), the bench's input), held to the same properties in the FP64 and the
+# mixed form.  No 32768^2 Q is formed: for a
 # matrix E and a probe block X with iid N(0,1) entries (p columns),
 # E ||E X||_F^2 = p ||E||_F^2, so ||E X||_F / sqrt(p) estimates ||E||_F (within
 # a small factor with overwhelming probability at p = 16).  Q is applied to
 # the probes from the reflectors block by block (apply_q).
-def test_largest_size_factorization_probes():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_largest_size_factorization_probes(precision):
     m = n = 32768
     p = 16
     A0 = W.gaussian_torch(m, n, 2)                                   # column-major, on the device
-    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1)
+    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1, precision=precision)
     torch.cuda.synchronize()
     assert rank == n
     j = jpvt.to(torch.int64) - 1
@@ -113,4 +115,4 @@ def test_largest_size_factorization_probes():
     orth = torch.linalg.norm(QtQY - Y) / p ** 0.5
     del F
     torch.cuda.empty_cache()
-    assert res.item() <= 1e-12 and orth.item() <= 1e-12, (res.item(), orth.item())
+    assert res.item() <= 1e-12 and orth.item() <= 1e-12, (precision, res.item(), orth.item())

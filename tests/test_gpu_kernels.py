@@ -41,7 +41,9 @@ def test_sketch_operator_sparse_bitexact(d, m, nnz):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("d,m,n", [(160, 2000, 1000), (37, 333, 21), (64, 4097, 65)])
+@pytest.mark.parametrize("d,m,n", [(160, 2000, 1000), (37, 333, 21), (64, 4097, 65),
+                                   (2560, 3000, 50),     # d = ceil(1.25 * 2048): the sparse kernel's rows in two tiles
+                                   (4100, 700, 9)])      # three row tiles, a ragged last one
 def test_sketch_apply_exact_on_integer_data(kind, d, m, n):
     rng = np.random.default_rng(d + m)
     A = rng.integers(-40, 40, size=(m, n)).astype(np.float64)

@@ -43,7 +43,7 @@ def _worker(rank, world, port, out):
 
 def test_replicas_aggregate_over_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this (possibly multi-threaded) process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     r0, r1 = out[0], out[1]
