@@ -41,8 +41,9 @@ SM_MAX_MHZ = 2032.0
 # FP64: 2 DFMA per clock per SM (the measured DFMA rate is 1.82-1.97 per clock
 # per SM; tcgen05 has no f64 kind), 2 FLOP per DFMA.
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# the FP64-accurate tensor-core product runs 53 bf16 slice products per FP64 product
-OZ_PRODUCTS = 53
+# the FP64-accurate tensor-core product runs 36 bf16 slice products per FP64
+# product (eight 7-bit slices per operand, the pairs with p + q <= 7)
+OZ_PRODUCTS = 36
 
 
 def bf16_peak():
@@ -58,17 +59,18 @@ def bf16_peak():
 
 
 def mixed_roofline(fp64eq_tflops):
-    """Tensor roofline of the slice GEMM: bf16 work = 53 x the FP64-equivalent rate."""
+    """Tensor roofline of the slice GEMM: bf16 work = 36 x the FP64-equivalent rate."""
     if not fp64eq_tflops:
         return None
     peak, src = bf16_peak()
     ach = OZ_PRODUCTS * fp64eq_tflops
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "kernel": ("ozaki_tc_kernel (bf16 slice products: persistent, tcgen05.mma kind::f16 "
-                                        "M=128 N<=256 stacked planes, TMA-fed 128B-swizzled smem, FP32 accumulators "
-                                        "in TMEM)"),
+            "traffic": None, "kernel": ("ozaki_tc_kernel (bf16 slice products: persistent 128x64 tiles, tcgen05.mma kind::f16 "
+                                        "M=128 N<=256 stacked planes, TMA-fed 128B-swizzled smem, FP32 group "
+                                        "accumulators in all 512 TMEM columns, epilogue of one half overlapping the "
+                                        "other half's MMAs)"),
             "fp64_equivalent_tflops": fp64eq_tflops, "peak_source": src,
-            "counting": "53 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
+            "counting": "36 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
 
 
 def canonical_flops(m, n):
@@ -397,7 +399,7 @@ def run_gemm(a):
     line = {"metric": name, "value": tf, "unit": "TFLOP/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
             "config": {"M": M, "N": N, "K": K}, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}
     if a.only == "ozaki":
-        # 53 bf16 slice products per FP64 product
+        # 36 bf16 slice products per FP64 product
         line["bf16_tensor_tflops"] = OZ_PRODUCTS * tf
         line["roofline"] = mixed_roofline(tf)
     print(json.dumps(line), flush=True)
@@ -883,7 +885,7 @@ def main():
         mtf = mtr_fl / (mtr_ms * 1e-3) / 1e12 if mtr_ms > 0 else None
         mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
-                 "arith": "FP64-accurate products on bf16 tensor cores (9 exact 6-bit slices, 53 pair products); "
+                 "arith": "FP64-accurate products on bf16 tensor cores (8 exact 7-bit slices, 36 pair products); "
                           "LU, sketch QR, panel, tau, R in FP64"}
         if not a.skip_qr:
             mq = time_own_qr(A, A0, "mixed", 3)[1:]   # one warm-up run, two timed

@@ -90,6 +90,91 @@ __global__ void probe_dfma_kernel(double* out, int iters, double a, double b) {
     if (s == 12345.678) out[0] = s;   // keeps the chains live
 }
 
+// Vo = the reflectors stored below the diagonal of A (rows x w, ld lda) with
+// a unit diagonal and zeros above it.
+__global__ void unit_lower_kernel(i64 rows, i64 w, const double* A, i64 lda, double* V, i64 ldv) {
+    const i64 total = rows * w;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % rows, j = e / rows;
+        V[i + j * ldv] = i > j ? A[i + j * lda] : (i == j ? 1.0 : 0.0);
+    }
+}
+
+// Copy a k x k upper triangle (zeros below) from T (ld ldt) into To (ld ldo).
+__global__ void copy_upper_kernel(i64 k, const double* T, i64 ldt, double* To, i64 ldo) {
+    const i64 total = k * k;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % k, j = e / k;
+        To[i + j * ldo] = i <= j ? T[i + j * ldt] : 0.0;
+    }
+}
+
+constexpr i64 kOuterQr = 256;   // outer block of the two-level QR
+
+struct TwoLevelWs {
+    double *V, *T, *W, *W2;         // inner panels (rows x 64, 64 x 64, 64 x n, 64 x n)
+    double *Vo, *To, *G, *X;        // outer block: rows x 256, 256 x 256, 256 x 256, 256 x 64
+    double *Wo, *Wo2;               // 256 x n each
+};
+
+void carve_two_level(Arena& ar, i64 m, i64 n, TwoLevelWs* w) {
+    w->V = ar.take<double>((size_t)imax(m, 1) * 64);
+    w->T = ar.take<double>(64 * 64);
+    w->W = ar.take<double>((size_t)64 * imax(n, 1));
+    w->W2 = ar.take<double>((size_t)64 * imax(n, 1));
+    w->Vo = ar.take<double>((size_t)imax(m, 1) * kOuterQr);
+    w->To = ar.take<double>((size_t)kOuterQr * kOuterQr);
+    w->G = ar.take<double>((size_t)kOuterQr * kOuterQr);
+    w->X = ar.take<double>((size_t)kOuterQr * 64);
+    w->Wo = ar.take<double>((size_t)kOuterQr * imax(n, 1));
+    w->Wo2 = ar.take<double>((size_t)kOuterQr * imax(n, 1));
+}
+
+// Two-level blocked Householder QR (GEQRF semantics): outer blocks of 256
+// columns, each factored by 64-wide panels whose updates stay inside the
+// block; the columns right of the block are updated once per block with the
+// block reflector I - Vo To Vo^T of all its reflectors, so that those products
+// have K = 256.  To is built from the panels' T factors by the compact-WY
+// recurrence [[T1, -T1 (V1^T V2) T2], [0, T2]], with G = Vo^T Vo.
+int geqrf_two_level(const Ctx& c, i64 rows, i64 cols, double* A, i64 lda, double* tau, const TwoLevelWs& w) {
+    const i64 kk = imin(rows, cols);
+    const unsigned gb = (unsigned)imax(1, imin(cdiv(rows * kOuterQr, 256), 16LL * c.dev.sms));
+    for (i64 jb = 0; jb < kk; jb += kOuterQr) {
+        const i64 bw = imin(kOuterQr, kk - jb), prow = rows - jb, nc = cols - jb - bw;
+        double* Ab = A + jb + jb * lda;
+        if (nc > 0) BQ_CUDA(cudaMemsetAsync(w.To, 0, sizeof(double) * kOuterQr * kOuterQr, c.stream));
+        // the block's panels; after each, its T goes to the diagonal of To
+        for (i64 p0 = 0; p0 < bw; p0 += 64) {
+            const i64 pw = imin(64, bw - p0);
+            BQ_TRY(geqrf_blocked(c, prow - p0, bw - p0, Ab + p0 + p0 * lda, lda, tau + jb + p0, w.V, w.T, w.W, w.W2,
+                                 64, pw));
+            if (nc > 0) {
+                copy_upper_kernel<<<(unsigned)cdiv(pw * pw, 256), 256, 0, c.stream>>>(pw, w.T, 64,
+                                                                                     w.To + p0 + p0 * kOuterQr,
+                                                                                     kOuterQr);
+                BQ_LAUNCH_CHECK();
+            }
+        }
+        if (nc <= 0) continue;
+        unit_lower_kernel<<<gb, 256, 0, c.stream>>>(prow, bw, Ab, lda, w.Vo, rows);
+        BQ_LAUNCH_CHECK();
+        BQ_TRY(pgemm(c, true, false, bw, bw, prow, 1.0, w.Vo, rows, w.Vo, rows, 0.0, w.G, kOuterQr, kGemmCUpper));
+        for (i64 p0 = 64; p0 < bw; p0 += 64) {
+            const i64 pw = imin(64, bw - p0);
+            // X = G(0:p0, p0:p0+pw) T_p ; To(0:p0, p0:p0+pw) = -To(0:p0, 0:p0) X
+            BQ_TRY(dgemm(c, false, false, p0, pw, pw, 1.0, w.G + p0 * kOuterQr, kOuterQr, w.To + p0 + p0 * kOuterQr,
+                         kOuterQr, 0.0, w.X, kOuterQr));
+            BQ_TRY(dgemm(c, false, false, p0, pw, p0, -1.0, w.To, kOuterQr, w.X, kOuterQr, 0.0,
+                         w.To + p0 * kOuterQr, kOuterQr, kGemmAUpper));
+        }
+        double* C = A + jb + (jb + bw) * lda;
+        BQ_TRY(pgemm(c, true, false, bw, nc, prow, 1.0, w.Vo, rows, C, lda, 0.0, w.Wo, kOuterQr));
+        BQ_TRY(pgemm(c, true, false, bw, nc, bw, 1.0, w.To, kOuterQr, w.Wo, kOuterQr, 0.0, w.Wo2, kOuterQr));
+        BQ_TRY(pgemm(c, false, false, prow, nc, bw, -1.0, w.Vo, rows, w.Wo2, kOuterQr, 1.0, C, lda));
+    }
+    return 0;
+}
+
 }  // namespace
 }  // namespace bq
 
@@ -311,7 +396,17 @@ int bqrrp_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau, int64
 
 size_t bqrrp_geqrf_mixed_workspace(int64_t m, int64_t n) {
     if (m < 0 || n < 0) return 0;
-    return bqrrp_geqrf_workspace(m, n, 0) + ozaki_ws_bytes(64, imax(n, 1), imax(m, 1), 9) + 512;
+    Arena ar;
+    Ctx c{};
+    begin(nullptr, 0, nullptr, &ar, &c, true, qr_split_elems(n));
+    TwoLevelWs w{};
+    carve_two_level(ar, m, n, &w);
+    const i64 mm = imax(m, 1), nn = imax(n, 1);
+    size_t oz = ozaki_ws_bytes(kOuterQr, nn, mm, kOzPlanes);             // Vo^T C, Vo^T Vo
+    oz = std::max(oz, ozaki_ws_bytes(mm, nn, kOuterQr, kOzPlanes));      // C -= Vo Wo2
+    oz = std::max(oz, ozaki_ws_bytes(64, nn, mm, kOzPlanes));            // the panels' own updates
+    ar.take<char>(oz);
+    return ar.off + 256;
 }
 
 int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau, void* workspace,
@@ -327,18 +422,18 @@ int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
     Arena ar;
     Ctx c{};
     BQ_TRY(begin(workspace, workspace_bytes, stream, &ar, &c, false, qr_split_elems(n)));
-    double* V = ar.take<double>((size_t)m * 64);
-    double* T = ar.take<double>(64 * 64);
-    double* W = ar.take<double>((size_t)64 * n);
-    double* W2 = ar.take<double>((size_t)64 * n);
-    const size_t oz = ozaki_ws_bytes(64, n, m, 9);
+    TwoLevelWs w{};
+    carve_two_level(ar, m, n, &w);
+    size_t oz = ozaki_ws_bytes(kOuterQr, n, m, kOzPlanes);
+    oz = std::max(oz, ozaki_ws_bytes(m, n, kOuterQr, kOzPlanes));
+    oz = std::max(oz, ozaki_ws_bytes(64, n, m, kOzPlanes));
     c.oz_ws = ar.take<char>(oz);
     c.oz_bytes = oz;
     c.mixed = true;
     if (!ar.ok()) { set_error("workspace too small"); return BQRRP_ENOMEM; }
     init_status_small<<<1, 1, 0, c.stream>>>(c.st);
     BQ_LAUNCH_CHECK();
-    BQ_TRY(geqrf_blocked(c, m, n, A, lda, tau, V, T, W, W2, 64));
+    BQ_TRY(geqrf_two_level(c, m, n, A, lda, tau, w));
     return finish(c);
 }
 
@@ -375,7 +470,7 @@ int bqrrp_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, doubl
 
 size_t bqrrp_dgemm_ozaki_workspace(int64_t M, int64_t N, int64_t K) {
     if (M < 0 || N < 0 || K < 0) return 0;
-    return ozaki_ws_bytes(M, N, K, 9) + 256;
+    return ozaki_ws_bytes(M, N, K, kOzPlanes) + 256;
 }
 
 int bqrrp_dgemm_ozaki(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -403,7 +498,7 @@ int bqrrp_dgemm_ozaki(char transa, char transb, int64_t M, int64_t N, int64_t K,
 
 size_t bqrrp_sketch_apply_tc_workspace(int64_t d, int64_t m, int64_t n) {
     if (d < 0 || m < 0 || n < 0) return 0;
-    return ozaki_ws_bytes(d, n, m, 1) + 256;
+    return ozaki_sketch_ws_bytes(d, m, n) + 256;
 }
 
 int bqrrp_sketch_apply_tc(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda, uint64_t seed, double* Msk,
@@ -415,7 +510,6 @@ int bqrrp_sketch_apply_tc(int64_t d, int64_t m, int64_t n, const double* A, int6
     if (lda < imax(1, m)) return -5;
     if (ldsk < imax(1, d)) return -8;
     if (d == 0 || n == 0) return 0;
-    if (m > (int64_t(1) << 17)) { set_error("sketch_apply_tc: m > 2^17 is not supported"); return BQRRP_EUNSUPPORTED; }
     if (workspace_bytes < bqrrp_sketch_apply_tc_workspace(d, m, n)) { set_error("workspace too small"); return BQRRP_ENOMEM; }
     Ctx c{};
     BQ_TRY(current_device(&c.dev));

@@ -318,15 +318,20 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
     B->oz_bytes = 0;
     B->oz_ws = nullptr;
     if (o.precision == BQRRP_PRECISION_MIXED) {
-        size_t z = ozaki_ws_bytes(bb, n, m, 9);                 // W = Y^T C
-        z = std::max(z, ozaki_ws_bytes(m, n, bb, 9));           // C -= Y W2
-        z = std::max(z, ozaki_ws_bytes(bb, n, bb, 9));          // W2 = T^T W
-        if (o.sketch_kind == BQRRP_SKETCH_DENSE) z = std::max(z, ozaki_ws_bytes(d, n, m, 1));   // S A
-        z = std::max(z, ozaki_ws_bytes(d, n, 64, 9));           // LU trailing updates
-        z = std::max(z, ozaki_ws_bytes(d, n, d, 9));            // R^sk = R1 L^T
-        z = std::max(z, ozaki_ws_bytes(64, n, m, 9));           // Householder panel updates (HQR panel)
+        size_t z = ozaki_ws_bytes(bb, n, m, kOzPlanes);         // W = Y^T C
+        z = std::max(z, ozaki_ws_bytes(m, n, bb, kOzPlanes));   // C -= Y W2
+        z = std::max(z, ozaki_ws_bytes(bb, n, bb, kOzPlanes));  // W2 = T^T W
+        if (o.sketch_kind == BQRRP_SKETCH_DENSE) z = std::max(z, ozaki_sketch_ws_bytes(d, m, n));   // S A
+        z = std::max(z, ozaki_ws_bytes(d, n, 64, kOzPlanes));   // LU trailing updates
+        z = std::max(z, ozaki_ws_bytes(d, n, d, kOzPlanes));    // R^sk = R1 L^T
+        z = std::max(z, ozaki_ws_bytes(64, n, m, kOzPlanes));           // Householder panel updates (HQR panel)
         B->oz_bytes = z;
         B->oz_ws = ar.take<char>(z);
+    } else if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
+        // the FP64 form's dense sketch also runs as exact slice products (S*A
+        // to FP64 accuracy on the tensor cores)
+        B->oz_bytes = ozaki_sketch_ws_bytes(d, m, n);
+        B->oz_ws = ar.take<char>(B->oz_bytes);
     }
     B->sparse_bytes = 0;
     B->sparse_ws = nullptr;
@@ -508,9 +513,9 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
     pr.begin(P_OTHER);
     init_status_kernel<<<1, 1, 0, c.stream>>>(B.st);
     BQ_LAUNCH_CHECK();
-    const bool dense64 = o.sketch_kind == BQRRP_SKETCH_DENSE && o.precision == BQRRP_PRECISION_FP64;
-    if (io && !dense64) BQ_TRY(io->bring_in(c, A, m, lda, 0, n));
-    if (!io || !dense64) {
+    const bool dense_in = o.sketch_kind == BQRRP_SKETCH_DENSE;   // A may come in by halves (see below)
+    if (io && !dense_in) BQ_TRY(io->bring_in(c, A, m, lda, 0, n));
+    if (!io || !dense_in) {
         // NaN/Inf in A -> BQRRP_ENUMERIC before anything is written
         BQ_TRY(any_nonfinite(c, m, n, A, lda, &B.st->a_nonfinite));
         BQ_TRY(read_status(c, &hs));
@@ -525,19 +530,18 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
 
     // Alg. 1: sketch Msk = S * A (d x n)
     pr.begin(P_SKETCH);
-    if (io && dense64) {
+    if (io && dense_in) {
         // A from the host in two column halves; each half is checked and
-        // sketched once it has arrived, with the split-K count of the whole
-        // product (so the bits are those of one launch).  The sketch writes
-        // only Msk, so the NaN/Inf result, read after it, still comes before
-        // anything of A is written.
-        const int sp = sketch_dense_splits(c, d, m, n);
+        // sketched once it has arrived (every sketch column depends only on
+        // its own column of A, so the bits are those of one call).  The
+        // sketch writes only Msk, so the NaN/Inf result, read after it, still
+        // comes before anything of A is written.
         const i64 half = n >= 1024 ? cdiv(cdiv(n, 2), 64) * 64 : n;
         for (i64 c0 = 0; c0 < n; c0 += half) {
             const i64 nc0 = imin(half, n - c0);
             BQ_TRY(io->bring_in(c, A, m, lda, c0, nc0));
             BQ_TRY(any_nonfinite(c, m, nc0, A + c0 * lda, lda, &B.st->a_nonfinite));
-            BQ_TRY(sketch_dense_gemm(c, d, m, nc0, seed, A + c0 * lda, lda, B.Msk + c0 * d, d, sp));
+            BQ_TRY(ozaki_sketch(c, d, m, nc0, seed, A + c0 * lda, lda, B.Msk + c0 * d, d, B.oz_ws, B.oz_bytes));
         }
         pr.flops(P_SKETCH, 2.0 * d * m * n);
         pr.begin(P_OTHER);
@@ -547,10 +551,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             return BQRRP_ENUMERIC;
         }
     } else if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
-        if (o.precision == BQRRP_PRECISION_MIXED)
-            BQ_TRY(ozaki_sketch(c, d, m, n, seed, A, lda, B.Msk, d, B.oz_ws, B.oz_bytes));
-        else
-            BQ_TRY(sketch_dense_gemm(c, d, m, n, seed, A, lda, B.Msk, d));
+        BQ_TRY(ozaki_sketch(c, d, m, n, seed, A, lda, B.Msk, d, B.oz_ws, B.oz_bytes));
         pr.flops(P_SKETCH, 2.0 * d * m * n);
     } else {
         BQ_TRY(sketch_sparse_apply(c, d, m, n, seed, o.sketch_nnz, A, lda, B.Msk, d, B.sparse_ws, B.sparse_bytes));

@@ -257,11 +257,14 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
                        double* tau);
 
 // ozaki.cu (FP64-accurate products on the bf16 tensor cores)
+constexpr int kOzPlanes = 8;              // 7-bit slices per FP64 operand (56 bits)
+constexpr i64 kOzMaxK = (i64)1 << 17;     // K per slice-GEMM launch (longer K is split)
 size_t ozaki_ws_bytes(i64 M, i64 N, i64 K, int sa);
 int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
                const double* B, i64 ldb, double beta, double* C, i64 ldc, void* ws, size_t ws_bytes);
 int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk, i64 ldsk,
                  void* ws, size_t ws_bytes);
+size_t ozaki_sketch_ws_bytes(i64 d, i64 m, i64 n);   // workspace of ozaki_sketch
 
 // panels.cu
 int getrf_pivots(const Ctx& c, i64 N, i64 d, double* X, i64 ldx, i64* ipiv); // LUPP in Sk layout

@@ -1,24 +1,25 @@
 // ozaki.cu -- FP64-accurate GEMM on the bf16 tensor cores (error-free
 // splitting, in the manner of the Ozaki scheme).
 //
-// B300 executes FP64 at ~1.2 TFLOP/s while its bf16 tensor cores run
-// mma.sync at ~570 TFLOP/s.  A product of FP64 matrices can be formed exactly
-// from integer slices:
+// B300 executes FP64 at ~1.2 TFLOP/s while its bf16 tensor cores run at
+// ~1.4 PFLOP/s (tcgen05, sustained).  A product of FP64 matrices can be formed
+// exactly from integer slices:
 //   * every row i of op(A) is scaled by 2^-ea_i and every column j of op(B) by
 //     2^-eb_j (ea_i, eb_j = exponent just above the row / column maximum);
-//   * the scaled value x is truncated to a 54-bit fixed-point integer X with
-//     integer bit operations, and X is cut into nine signed 6-bit slices
-//     q_0 .. q_8 (|q| <= 63, exact in bf16):  x ~ sum_p q_p 2^(e - 6 - 6p);
-//   * op(A) op(B) ~ sum_{p+q <= 9} 2^(ea_i + eb_j - 12 - 6(p+q)) (A_p B_q):
-//     the 53 slice products with p + q <= 9 keep everything above 2^-54 of
-//     max|row| * max|column| per term (FP64's own unit roundoff is 2^-53);
+//   * the scaled value x is truncated to a 56-bit fixed-point integer X with
+//     integer bit operations, and X is cut into eight signed 7-bit slices
+//     q_0 .. q_7 (|q| <= 127, exact in bf16):  x ~ sum_p q_p 2^(e - 7 - 7p);
+//   * op(A) op(B) ~ sum_{p+q <= 7} 2^(ea_i + eb_j - 14 - 7(p+q)) (A_p B_q):
+//     the 36 slice products with p + q <= 7; the dropped pairs and the
+//     truncation together stay below about 2^-53 of max|row| * max|column| per
+//     term (FP64's own unit roundoff is 2^-53);
 //   * the products of one group t = p + q are summed on the tensor cores in
 //     FP32.  Every partial sum is an integer of magnitude below
-//     (t+1) * Kc * 63^2 < 2^24 for a K chunk Kc = 256, so FP32 holds it
-//     exactly; after each chunk the ten group sums are added into FP64 with
-//     weights 2^-6t.
+//     8 * Kc * 127^2 < 2^24 for a K chunk Kc = 128, so FP32 holds it exactly;
+//     after each chunk the eight group sums are added exactly into two 64-bit
+//     integers (ozaki_tc.cu), which are rounded once to FP64 at the end.
 // The result matches an FP64 GEMM to a few units of roundoff (normwise).  A
-// sketch with +-1 entries is exact in one slice, so S*A needs only the nine
+// sketch with +-1 entries is exact in one slice, so S*A needs only the eight
 // products S A_q.
 #include <cuda_bf16.h>
 
@@ -28,7 +29,7 @@ namespace bq {
 
 namespace {
 
-constexpr int kSlices = 9;     // 6-bit slices per FP64 operand (54 bits)
+constexpr int kSlices = kOzPlanes;   // 7-bit slices per FP64 operand (56 bits)
 constexpr int OBM = 64, OBN = 32, OBK = 32;   // padding of the slice planes (rows, rows, k)
 
 __device__ __forceinline__ int exp_above(double m) {
@@ -39,13 +40,13 @@ __device__ __forceinline__ int exp_above(double m) {
     return e;
 }
 
-// x (|x| < 2^e) -> 54-bit fixed point X = trunc(x 2^(54-e)) using integer ops.
-__device__ __forceinline__ long long fixed54(double x, int e) {
+// x (|x| < 2^e) -> 56-bit fixed point X = trunc(x 2^(56-e)) using integer ops.
+__device__ __forceinline__ long long fixed56(double x, int e) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((bits >> 52) & 0x7FF);
     if (ex == 0) return 0;   // zero (subnormals are far below every slice)
     const long long mant = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    const int sh = ex - 1075 + 54 - e;   // <= 1 because |x| < 2^e
+    const int sh = ex - 1075 + 56 - e;   // <= 3 because |x| < 2^e
     long long X;
     if (sh >= 0) X = mant << sh;
     else if (sh > -63) X = mant >> (-sh);
@@ -98,12 +99,12 @@ __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ld
     for (int q = ty; q < 32; q += 8) {
         const i64 r = r0 + q, k = k0 + tx;
         if (r >= Rp || k >= ldk) continue;
-        const long long Xi = (r < R && k < K) ? fixed54(tile[q][tx], e[r]) : 0;
+        const long long Xi = (r < R && k < K) ? fixed56(tile[q][tx], e[r]) : 0;
         const unsigned long long a = (unsigned long long)(Xi < 0 ? -Xi : Xi);
         const bool neg = Xi < 0;
 #pragma unroll
         for (int p = 0; p < kSlices; ++p) {
-            const int v = (int)((a >> (48 - 6 * p)) & 63ull);
+            const int v = (int)((a >> (49 - 7 * p)) & 127ull);
             S[(size_t)p * slice + (size_t)r * ldk + k] = __int2bfloat16_rn(neg ? -v : v);
         }
     }
@@ -194,14 +195,23 @@ int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, con
     return dgemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
 }
 
+// Columns of A sliced at a time by ozaki_sketch (the slice planes of a block
+// take 16 bytes per element; 8192 columns give the sketch GEMM enough tiles).
+constexpr i64 kSketchCols = 8192;
+
+size_t ozaki_sketch_ws_bytes(i64 d, i64 m, i64 n) { return ozaki_ws_bytes(d, imin(imax(n, 1), kSketchCols), m, 1); }
+
 // Msk = S A with the dense +-1 operator S (d x m) as one exact slice:
-// nine tensor-core products S A_q; FP32 sums of |+-1 * q| over K = m stay
-// below 2^24 for m < 2^18, so one FP64 flush per 2^17 columns suffices.
+// eight tensor-core products S A_q; FP32 sums of |+-1 * q| <= 127 over 2^17
+// columns stay below 2^24, so one exact flush per 2^17 columns suffices.  A
+// is sliced and multiplied kSketchCols columns at a time (every column of Msk
+// depends only on its own column of A, so the blocking changes no bit).
 int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk, i64 ldsk,
                  void* ws, size_t ws_bytes) {
     if (d <= 0 || n <= 0) return 0;
-    const i64 Mp = rup(d, OBM), Np = rup(n, OBN), Kp = rup(imax(m, 1), OBK);
-    if (ws_bytes < ozaki_ws_bytes(d, n, m, 1)) { set_error("ozaki_sketch: workspace too small"); return BQRRP_ENOMEM; }
+    const i64 nb = imin(n, kSketchCols);
+    const i64 Mp = rup(d, OBM), Np = rup(nb, OBN), Kp = rup(imax(m, 1), OBK);
+    if (ws_bytes < ozaki_sketch_ws_bytes(d, m, n)) { set_error("ozaki_sketch: workspace too small"); return BQRRP_ENOMEM; }
     Arena ar;
     ar.base = (char*)ws;
     ar.cap = ws_bytes;
@@ -214,16 +224,21 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     const unsigned blocks = (unsigned)imax(1, imin(cdiv(Mp * Kp, 256), 16LL * c.dev.sms));
     sketch_slice_kernel<<<blocks, 256, 0, c.stream>>>(d, m, Mp, Kp, seed, Ss);
     BQ_LAUNCH_CHECK();
-    // S has one slice q_0 = +-1 with weight 2^(ea - 6) = 1: ea = 6 on every row
-    fill_int_kernel<<<(unsigned)cdiv(Mp, 256), 256, 0, c.stream>>>(ea, Mp, 6);
-    BQ_LAUNCH_CHECK();
-    row_exp_kernel<<<(unsigned)n, 256, 0, c.stream>>>(n, m, A, lda, 1, eb);
-    BQ_LAUNCH_CHECK();
-    split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32)), 256, 0, c.stream>>>(n, m, Np, Kp, A, lda, 1, eb, Bs);
+    // S has one slice q_0 = +-1 with weight 2^(ea - 7) = 1: ea = 7 on every row
+    fill_int_kernel<<<(unsigned)cdiv(Mp, 256), 256, 0, c.stream>>>(ea, Mp, 7);
     BQ_LAUNCH_CHECK();
     int* err = c.st ? &c.st->err_timeout : flag;
     if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
-    BQ_TRY(ozaki_tc_sketch(c, Ss, Mp, Bs, Np, Kp, d, n, ea, eb, Msk, ldsk, err));
+    for (i64 j0 = 0; j0 < n; j0 += nb) {
+        const i64 nj = imin(nb, n - j0), Npj = rup(nj, OBN);
+        const double* Aj = A + j0 * lda;
+        row_exp_kernel<<<(unsigned)nj, 256, 0, c.stream>>>(nj, m, Aj, lda, 1, eb);
+        BQ_LAUNCH_CHECK();
+        split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Npj / 32)), 256, 0, c.stream>>>(nj, m, Npj, Kp, Aj, lda, 1,
+                                                                                           eb, Bs);
+        BQ_LAUNCH_CHECK();
+        BQ_TRY(ozaki_tc_sketch(c, Ss, Mp, Bs, Npj, Kp, d, nj, ea, eb, Msk + j0 * ldsk, ldsk, err));
+    }
     return check_flag(c, flag);
 }
 

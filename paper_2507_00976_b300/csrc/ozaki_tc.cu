@@ -2,32 +2,44 @@
 // the 5th-generation tensor cores: tcgen05.mma with operands staged in shared
 // memory by TMA and FP32 accumulators in tensor memory (TMEM).
 //
-// Each tile of C = alpha op(A) op(B) + beta C is 128 x 32; one persistent CTA
-// per SM walks the tiles.  The operands are the
-// bf16 slice planes As[p][row][k] (p < SA) and Bs[q][col][k] (q < SB), both
-// K-contiguous.  Warp roles (320 threads):
-//   warp 0      TMA producer: per 64-deep k block, one 3-D load of all SB
-//               B planes (32 x 64 each) and SA loads of A planes (128 x 64),
-//               128-byte swizzled, into rings of shared-memory stages;
-//   warp 1      allocates 512 TMEM columns; one thread issues the MMAs.
-//               The B planes q = 0..7 of a stage lie back to back, so one
-//               tcgen05.mma.kind::f16 with M = 128, N = 256, K = 16 whose
-//               accumulator starts at TMEM column 32 p multiplies A plane p by
-//               all eight at once and lands block q in columns 32 (p + q):
-//               the accumulator of group t = p + q.  The MMA for plane p
-//               takes only the planes with p + q <= TMAX (N = 32 per plane,
-//               at most eight); plane q = 8 adds one N = 32 MMA where
-//               p + 8 <= TMAX.  Exactly the 53 products are formed;
-//   warps 2-9   epilogue (two warps per 32-lane TMEM quarter, 16 columns
-//               each): zeroes the group accumulators before every K chunk
-//               (all MMAs accumulate) and after each chunk (Kc deep, every group sum an
-//               integer below 2^24, so exact in FP32) it reads the ten
-//               group accumulators with tcgen05.ld and adds them into two
-//               64-bit integers per element, exactly:
-//                 HI += sum_{t <= 4} acc_t 2^(6(4-t)),
-//                 LO += sum_{t >= 5} acc_t 2^(6(TMAX-t));
-//               at the end C = alpha 2^(ea+eb-12) (HI 2^-24 + LO 2^-6TMAX)
-//               + beta C, one FP64 rounding per term.
+// Operands are bf16 slice planes, K-contiguous: As[p][row][k] (p < SA; SA = 8
+// for an FP64 operand, 1 for the +-1 sketch) and Bs[q][col][k] (q < 8).  Every
+// slice is an integer in [-127, 127].  The product of planes p and q has
+// weight 2^-7(p+q); the pairs with p + q <= 7 are formed (36 of them for
+// SA = 8, 8 for the sketch) and the products of one group t = p + q are summed
+// in one FP32 accumulator, exactly: within a K chunk of CL k blocks every
+// partial sum is an integer below 8 * 128 * 127^2 < 2^24 (SA = 8, CL = 2) or
+// 2^17 * 127 < 2^24 (sketch, CL = 2048).
+//
+// Tile: 128 rows x 64 columns; one persistent CTA per SM walks the tiles in
+// the grouped raster of tc_schedule.cuh.  TMEM (512 columns of 32 bits) holds
+// the tile's accumulators: column half h (C columns 32h .. 32h+31) owns TMEM
+// columns [256 h, 256 h + 256), group t of it [256 h + 32 t, + 32).
+//
+// Shared memory (225 KiB): eight A slots of one 128 x 64 plane tile (16 KiB,
+// 128-byte swizzled) and three B slots of one half-stage (the 8 planes of 32
+// columns x 64 k, 32 KiB), with full/empty mbarriers.
+//
+// Warp roles (576 threads); the order of their work is tc_schedule.cuh's:
+//   warp 0      TMA producer (one thread): per 64-deep k block the B half of
+//               the first segment, the SA A planes, the B half of the second;
+//   warp 1      allocates the 512 TMEM columns; one thread issues the MMAs.
+//               Segment (k block, half h), A plane p: the B planes q = 0..7-p of
+//               the half lie back to back in its B slot, so one
+//               tcgen05.mma.kind::f16 (M = 128, N = 32 (8 - p), K = 16) whose
+//               accumulator starts at TMEM column 256 h + 32 p lands plane q in
+//               group p + q; four such MMAs cover the k block.  The half whose
+//               chunk ends in a k block goes first, so the epilogue of one half
+//               overlaps the other half's MMAs;
+//   warps 2-17  epilogue, eight warps per half (warp w reads TMEM lanes
+//               32 (w % 4) ..; two warps share a lane quarter, 16 columns
+//               each).  After each chunk a warp reads the eight groups with
+//               tcgen05.ld, zeroes them with tcgen05.st, releases the half and
+//               adds the sums into two 64-bit integers per element, exactly:
+//                 HI += sum_{t <= 3} G_t 2^(7(3-t)),  LO += sum_{t >= 4} G_t 2^(7(7-t));
+//               after a tile's last chunk (the half is already released for the
+//               next tile) C = alpha (HI 2^28 + LO) 2^(ea+eb-63) + beta C, the
+//               128-bit integer rounded once to FP64 with integer operations.
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error
 // flag, the roles stop issuing work, in-flight copies and MMAs are waited for
 // (bounded), TMEM is freed and the CTA returns.
@@ -37,16 +49,23 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tc_schedule.cuh"
 
 namespace bq {
 namespace {
 
-constexpr int TC_M = 128, TC_N = 32, TC_KB = 64;   // tile rows, tile columns, k block
-constexpr int TC_THREADS = 320;
-constexpr int TC_NA = 4, TC_NB = 2;                // A and B ring stages
-constexpr int TC_ABYTES = TC_M * TC_KB * 2;        // 16 KiB per A stage
-constexpr int TC_BPLANE = TC_N * TC_KB * 2;        // 4 KiB per B plane
+constexpr int TC_M = 128, TC_N = 64, TC_HN = 32, TC_KB = 64;   // tile rows, columns, half columns, k block
+constexpr int TC_NP = 8;                                        // planes of op(B)
+constexpr int TC_NG = 8;                                        // groups t = 0..7
+constexpr int TC_EPI = 16;                                      // epilogue warps
+constexpr int TC_THREADS = 64 + 32 * TC_EPI;
+constexpr int TC_APLANE = TC_M * TC_KB * 2;                     // 16 KiB per A slot
+constexpr int TC_BHALF = TC_NP * TC_HN * TC_KB * 2;             // 32 KiB per B slot
+constexpr int TC_NBAR = 2 * tcs::kNAS + 2 * tcs::kNBS + 2 + 2 + 1;
+constexpr size_t TC_SMEM =
+    1024 + (size_t)tcs::kNAS * TC_APLANE + (size_t)tcs::kNBS * TC_BHALF + 8 * TC_NBAR + 16;
 constexpr unsigned long long kTcSpin = 1ull << 26;
+static_assert(TC_SMEM <= 232448, "shared memory of the slice GEMM exceeds the per-CTA limit");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -77,7 +96,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, int* err)
     atomicExch(err, 1);
     return false;
 }
-
 // Bounded wait that ignores the error flag: used to drain in-flight copies and
 // MMAs before the CTA releases its shared memory and TMEM.
 __device__ __forceinline__ void mbar_drain(uint32_t b, uint32_t parity) {
@@ -107,7 +125,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_f16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
-constexpr uint32_t kIdesc32 = idesc_f16(TC_N);
 
 // D (TMEM) += A (smem) B (smem)
 __device__ __forceinline__ void mma_f16_acc(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc) {
@@ -131,21 +148,52 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
-// 16 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
+// 4 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// w * 2^e rounded to the nearest double (ties to even), w a 64-bit integer,
+// with integer operations only.  Results outside the normal range (never met
+// by the products of this library's inputs) take a plain conversion.
+__device__ __forceinline__ double i64_scaled(long long w, int e) {
+    if (w == 0) return 0.0;
+    const bool neg = w < 0;
+    const unsigned long long a = neg ? 0ull - (unsigned long long)w : (unsigned long long)w;
+    const int nb = 64 - __clzll((long long)a);   // bit length of a
+    unsigned long long mant;
+    int ex = nb - 1 + e;   // exponent of the leading bit
+    if (nb <= 53) {
+        mant = a << (53 - nb);
+    } else {
+        const int s = nb - 53;
+        const unsigned long long rem = a & ((1ull << s) - 1), half = 1ull << (s - 1);
+        mant = a >> s;
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            ++mant;
+            if (mant == (1ull << 53)) {
+                mant >>= 1;
+                ++ex;
+            }
+        }
+    }
+    const int be = ex + 1023;
+    if (be <= 0 || be >= 2047) {
+        const double v = ldexp((double)a, e);
+        return neg ? -v : v;
+    }
+    const unsigned long long bits =
+        ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
 struct TcArgs {
+    tcs::Plan plan;
+    int dsh;   // bits dropped (rounded) from each chunk's sum: ceil(log2 K) + 1, at least 11
     i64 M, N;
-    int KB;            // 64-deep k blocks
-    int kbpc;          // k blocks per exact chunk
-    int mt, ntiles;    // row tiles, all tiles (tile = row tile + mt * column tile)
     const int* ea;
     const int* eb;
     double alpha, beta;
@@ -154,49 +202,187 @@ struct TcArgs {
     int* err;
 };
 
-// Planes of B multiplied by A plane pa in one MMA: q = 0 .. nq-1 with
-// pa + q <= TMAX, at most eight (the ninth plane gets its own MMA).
-template <int TMAX>
-__device__ __forceinline__ int stacked_planes(int pa) {
-    const int nq = TMAX - pa + 1;
-    return nq < 8 ? nq : 8;
-}
+// Barrier addresses: full_a[8], empty_a[8], full_b[3], empty_b[3], acc_full[2], acc_empty[2], drain.
+struct Bars {
+    uint32_t base;
+    __device__ uint32_t full_a(int s) const { return base + 8 * s; }
+    __device__ uint32_t empty_a(int s) const { return base + 8 * (tcs::kNAS + s); }
+    __device__ uint32_t full_b(int s) const { return base + 8 * (2 * tcs::kNAS + s); }
+    __device__ uint32_t empty_b(int s) const { return base + 8 * (2 * tcs::kNAS + tcs::kNBS + s); }
+    __device__ uint32_t acc_full(int h) const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + h); }
+    __device__ uint32_t acc_empty(int h) const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + 2 + h); }
+    __device__ uint32_t drain() const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + 4); }
+};
 
-// Persistent: CTA b handles tiles b, b + gridDim.x, ...  The accumulators of a
-// tile are released as soon as the epilogue has read its last chunk, so the
-// final FP64 conversion and the stores of C overlap the next tile's MMAs.
-template <int SA, int SB, int TMAX>
+// ---------------------------------------------------------------- role visitors
+struct ProducerV {
+    const TcArgs* p;
+    Bars bar;
+    uint32_t sA, sB;
+    const CUtensorMap* tmA;
+    const CUtensorMap* tmB;
+    long long last_a[tcs::kNAS];   // last fill issued per slot (-1: none)
+    long long last_b[tcs::kNBS];
+    __device__ __forceinline__ bool load_a(int tile, int kb, int pl, int slot, long long fill) {
+        if (!mbar_wait(bar.empty_a(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
+        int rt, ct;
+        tcs::tile_coords(p->plan, tile, &rt, &ct);
+        mbar_expect_tx(bar.full_a(slot), TC_APLANE);
+        tma_load_3d(sA + slot * TC_APLANE, tmA, kb * TC_KB, rt * TC_M, pl, bar.full_a(slot));
+        last_a[slot] = fill;
+        return true;
+    }
+    __device__ __forceinline__ bool load_b(int tile, int kb, int h, int slot, long long fill) {
+        if (!mbar_wait(bar.empty_b(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
+        int rt, ct;
+        tcs::tile_coords(p->plan, tile, &rt, &ct);
+        mbar_expect_tx(bar.full_b(slot), TC_BHALF);
+        tma_load_3d(sB + slot * TC_BHALF, tmB, kb * TC_KB, ct * TC_N + h * TC_HN, 0, bar.full_b(slot));
+        last_b[slot] = fill;
+        return true;
+    }
+};
+
+struct MmaV {
+    const TcArgs* p;
+    Bars bar;
+    uint32_t sA, sB, tmem;
+    __device__ __forceinline__ bool wait_acc_empty(int h, long long chunk) {
+        if (!mbar_wait(bar.acc_empty(h), (uint32_t)(chunk & 1), p->err)) return false;
+        tc_fence_after();
+        return true;
+    }
+    __device__ __forceinline__ bool wait_full_b(int sb, long long fill) {
+        if (!mbar_wait(bar.full_b(sb), (uint32_t)(fill & 1), p->err)) return false;
+        tc_fence_after();
+        return true;
+    }
+    __device__ __forceinline__ bool wait_full_a(int sa, long long fill) {
+        if (!mbar_wait(bar.full_a(sa), (uint32_t)(fill & 1), p->err)) return false;
+        tc_fence_after();
+        return true;
+    }
+    __device__ __forceinline__ void mma(int, int, int h, int pl, int sa, int sb) {
+        const uint64_t ad = sdesc(sA + sa * TC_APLANE);
+        const uint64_t bd = sdesc(sB + sb * TC_BHALF);   // planes 0 .. 7 - pl stacked along N
+        const uint32_t idn = idesc_f16(TC_HN * (TC_NG - pl));
+        const uint32_t d = tmem + (uint32_t)(256 * h + TC_HN * pl);
+#pragma unroll
+        for (int ks = 0; ks < TC_KB / 16; ++ks)   // +32 bytes per 16-deep k step inside the swizzled rows
+            mma_f16_acc(d, ad + (uint64_t)(ks * 2), bd + (uint64_t)(ks * 2), idn);
+    }
+    __device__ __forceinline__ void release_a(int sa) { mma_commit(bar.empty_a(sa)); }
+    __device__ __forceinline__ void release_b(int sb) { mma_commit(bar.empty_b(sb)); }
+    __device__ __forceinline__ void acc_ready(int h) { mma_commit(bar.acc_full(h)); }
+};
+
+// Per element the epilogue keeps one 64-bit integer: the sum over chunks of
+// the chunk's exact value W (in units of 2^(ea+eb-63)) rounded to a multiple
+// of 2^dsh.  |sum| stays below K 2^63 / 2^dsh < 2^62, and the rounding adds at
+// most K/128 * 2^(dsh-1) units, under K 2^-53 max|A(i,:)| max|B(:,j)| for
+// K <= 2^17 (the launcher's limit): the normwise error of an FP64 GEMM.
+struct EpilogueV {
+    const TcArgs* p;
+    Bars bar;
+    uint32_t tl;   // this warp's TMEM address: lane quarter, half, 16-column sub-block
+    int lane, lq, sub;
+    long long acc[16];
+    __device__ __forceinline__ void zero_all() {
+#pragma unroll
+        for (int t = 0; t < TC_NG; ++t) tmem_zero16(tl + (uint32_t)(TC_HN * t));
+    }
+    __device__ __forceinline__ void release_acc(int h) {
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar.acc_empty(h));
+    }
+    __device__ __forceinline__ bool wait_acc_full(int h, long long chunk) {
+        // lane 0 waits; the outcome is shared so that the warp-collective
+        // tcgen05.ld always runs with the whole warp
+        int got = 0;
+        if (lane == 0) got = mbar_wait(bar.acc_full(h), (uint32_t)(chunk & 1), p->err) ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, got, 0) == 0) return false;
+        tc_fence_after();
+        return true;
+    }
+    __device__ __forceinline__ void tile_begin() {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = 0;
+    }
+    // W = HI 2^28 + LO with HI = sum_{t <= 3} G_t 2^(7(3-t)) and
+    // LO = sum_{t >= 4} G_t 2^(7(7-t)) (Horner steps of 2^7, exact), four
+    // columns at a time; HI 2^28 is a multiple of 2^dsh, so only LO is rounded.
+    __device__ __forceinline__ void read_chunk(int) {
+        const int dsh = p->dsh;
+        const long long half = 1ll << (dsh - 1);
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int t = 0; t < TC_NG; ++t) {
+                uint32_t v[4];
+                tmem_ld4(tl + (uint32_t)(TC_HN * t + 4 * cb), v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long x = (long long)__float2int_rz(__uint_as_float(v[j]));
+                    if (t <= 3) hi[j] = hi[j] * 128 + x;
+                    else lo[j] = lo[j] * 128 + x;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[4 * cb + j] += (hi[j] << (28 - dsh)) + ((lo[j] + half) >> dsh);
+        }
+#pragma unroll
+        for (int t = 0; t < TC_NG; ++t) tmem_zero16(tl + (uint32_t)(TC_HN * t));
+    }
+    __device__ __forceinline__ void tile_end(int tile, int h) {
+        int rt, ct;
+        tcs::tile_coords(p->plan, tile, &rt, &ct);
+        const i64 row = (i64)rt * TC_M + 32 * lq + lane;
+        if (row >= p->M) return;
+        const int er = p->ea[row];
+        const double alpha = p->alpha, beta = p->beta;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const i64 col = (i64)ct * TC_N + TC_HN * h + 16 * sub + j;
+            if (col < p->N) {
+                double out = i64_scaled(acc[j], er + p->eb[col] - 63 + p->dsh);
+                if (alpha != 1.0) out = (alpha == -1.0) ? -out : alpha * out;
+                double* cp = p->C + row + col * p->ldc;
+                *cp = (beta == 0.0) ? out : (beta == 1.0 ? *cp + out : fma(beta, *cp, out));
+            }
+        }
+    }
+};
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
-    constexpr int NG = TMAX + 1;
-    static_assert(NG * TC_N <= 512, "group accumulators exceed TMEM");
-    static_assert(SB == 9 && SA <= 9, "the stacked-B MMA covers B planes 0..7 plus plane 8");
-    constexpr int BBYTES = SB * TC_BPLANE;
+    ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ TcArgs p) {
     extern __shared__ unsigned char smraw[];
-    // 1024-byte aligned stage buffers (the 128-byte swizzle atom)
+    // 1024-byte aligned slots (the 128-byte swizzle atom)
     unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = sm;                              // TC_NA x 16 KiB
-    unsigned char* sB = sA + TC_NA * TC_ABYTES;          // TC_NB x BBYTES
-    uint64_t* bars = (uint64_t*)(sB + TC_NB * BBYTES);   // full_a, empty_a, full_b, empty_b, acc_full, acc_empty, drain
-    uint32_t* tslot = (uint32_t*)(bars + 2 * TC_NA + 2 * TC_NB + 3);
-    const uint32_t bfa = su32(bars), bea = bfa + 8 * TC_NA, bfb = bea + 8 * TC_NA, beb = bfb + 8 * TC_NB;
-    const uint32_t bacc_full = beb + 8 * TC_NB, bacc_empty = bacc_full + 8, bdrain = bacc_empty + 8;
-
+    unsigned char* sA = sm;
+    unsigned char* sB = sA + tcs::kNAS * TC_APLANE;
+    uint64_t* bars = (uint64_t*)(sB + tcs::kNBS * TC_BHALF);
+    uint32_t* tslot = (uint32_t*)(bars + TC_NBAR);
+    const Bars bar{su32(bars)};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nchunks = (p.KB + p.kbpc - 1) / p.kbpc;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_NA; ++s) {
-            mbar_init(bfa + 8 * s, 1);
-            mbar_init(bea + 8 * s, 1);
+        for (int s = 0; s < tcs::kNAS; ++s) {
+            mbar_init(bar.full_a(s), 1);
+            mbar_init(bar.empty_a(s), 1);
         }
-        for (int s = 0; s < TC_NB; ++s) {
-            mbar_init(bfb + 8 * s, 1);
-            mbar_init(beb + 8 * s, 1);
+        for (int s = 0; s < tcs::kNBS; ++s) {
+            mbar_init(bar.full_b(s), 1);
+            mbar_init(bar.empty_b(s), 1);
         }
-        mbar_init(bacc_full, 1);
-        mbar_init(bacc_empty, 8);
-        mbar_init(bdrain, 1);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(bar.acc_full(h), 1);
+            mbar_init(bar.acc_empty(h), TC_EPI / 2);
+        }
+        mbar_init(bar.drain(), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -210,165 +396,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
-        // ---------------- TMA producer
         if (lane == 0) {
-            int sa = 0, sb = 0;
-            uint32_t pha = 0, phb = 0;
-            // stages loaded at least once (bit s) and the parity of their last load
-            uint32_t used_a = 0, par_a = 0, used_b = 0, par_b = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-                const int m0 = (tile % p.mt) * TC_M, n0 = (tile / p.mt) * TC_N;
-                for (int kb = 0; kb < p.KB && ok; ++kb) {
-                    if (!(ok = mbar_wait(beb + 8 * sb, phb ^ 1, p.err))) break;
-                    mbar_expect_tx(bfb + 8 * sb, BBYTES);
-                    tma_load_3d(su32(sB + sb * BBYTES), &tmB, kb * TC_KB, n0, 0, bfb + 8 * sb);
-                    used_b |= 1u << sb;
-                    par_b = (par_b & ~(1u << sb)) | (phb << sb);
-                    for (int pa = 0; pa < SA; ++pa) {
-                        if (!(ok = mbar_wait(bea + 8 * sa, pha ^ 1, p.err))) break;
-                        mbar_expect_tx(bfa + 8 * sa, TC_ABYTES);
-                        tma_load_3d(su32(sA + sa * TC_ABYTES), &tmA, kb * TC_KB, m0, pa, bfa + 8 * sa);
-                        used_a |= 1u << sa;
-                        par_a = (par_a & ~(1u << sa)) | (pha << sa);
-                        if (++sa == TC_NA) {
-                            sa = 0;
-                            pha ^= 1;
-                        }
-                    }
-                    if (++sb == TC_NB) {
-                        sb = 0;
-                        phb ^= 1;
-                    }
-                }
-            }
-            // every issued copy has landed before the CTA may exit (the phase a
-            // stage was last loaded in completes when its bytes arrive)
-            for (int s = 0; s < TC_NA; ++s)
-                if (used_a >> s & 1u) mbar_drain(bfa + 8 * s, (par_a >> s) & 1u);
-            for (int s = 0; s < TC_NB; ++s)
-                if (used_b >> s & 1u) mbar_drain(bfb + 8 * s, (par_b >> s) & 1u);
+            ProducerV v{&p, bar, su32(sA), su32(sB), &tmA, &tmB, {}, {}};
+            for (int s = 0; s < tcs::kNAS; ++s) v.last_a[s] = -1;
+            for (int s = 0; s < tcs::kNBS; ++s) v.last_b[s] = -1;
+            tcs::producer(p.plan, blockIdx.x, v);
+            // every issued copy lands before the CTA may exit (fill n of a slot
+            // completes phase n of its full barrier)
+            for (int s = 0; s < tcs::kNAS; ++s)
+                if (v.last_a[s] >= 0) mbar_drain(bar.full_a(s), (uint32_t)(v.last_a[s] & 1));
+            for (int s = 0; s < tcs::kNBS; ++s)
+                if (v.last_b[s] >= 0) mbar_drain(bar.full_b(s), (uint32_t)(v.last_b[s] & 1));
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
         if (lane == 0) {
-            int sa = 0, sb = 0;
-            uint32_t pha = 0, phb = 0;
-            unsigned g = 0;                              // chunks issued so far (all tiles)
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-                for (int c = 0; c < nchunks && ok; ++c, ++g) {
-                    // the epilogue has zeroed the accumulators (initially, and
-                    // right after reading every chunk)
-                    if (!(ok = mbar_wait(bacc_empty, g & 1u, p.err))) break;
-                    tc_fence_after();
-                    const int kb0 = c * p.kbpc, kb1 = min(p.KB, kb0 + p.kbpc);
-                    for (int kb = kb0; kb < kb1 && ok; ++kb) {
-                        if (!(ok = mbar_wait(bfb + 8 * sb, phb, p.err))) break;
-                        tc_fence_after();
-                        const uint32_t bbase = su32(sB + sb * BBYTES);
-                        const uint64_t b8 = sdesc(bbase);                    // planes 0..7 stacked along N
-                        const uint64_t b1 = sdesc(bbase + 8 * TC_BPLANE);    // plane 8
-                        for (int pa = 0; pa < SA; ++pa) {
-                            if (!(ok = mbar_wait(bfa + 8 * sa, pha, p.err))) break;
-                            tc_fence_after();
-                            const uint64_t ad = sdesc(su32(sA + sa * TC_ABYTES));
-                            const int nq = stacked_planes<TMAX>(pa);
-                            const uint32_t idn = idesc_f16(nq * TC_N);
-#pragma unroll
-                            for (int ks = 0; ks < TC_KB / 16; ++ks) {
-                                // +32 bytes per 16-deep k step inside the swizzled 128-byte rows
-                                mma_f16_acc(tmem + (uint32_t)(pa * TC_N), ad + (uint64_t)(ks * 2),
-                                            b8 + (uint64_t)(ks * 2), idn);
-                                if (pa + 8 <= TMAX)
-                                    mma_f16_acc(tmem + (uint32_t)((pa + 8) * TC_N), ad + (uint64_t)(ks * 2),
-                                                b1 + (uint64_t)(ks * 2), kIdesc32);
-                            }
-                            mma_commit(bea + 8 * sa);
-                            if (++sa == TC_NA) {
-                                sa = 0;
-                                pha ^= 1;
-                            }
-                        }
-                        mma_commit(beb + 8 * sb);
-                        if (++sb == TC_NB) {
-                            sb = 0;
-                            phb ^= 1;
-                        }
-                    }
-                    if (ok) mma_commit(bacc_full);
-                }
-            }
-            // wait for every issued MMA before TMEM is released
-            mma_commit(bdrain);
-            mbar_drain(bdrain, 0);
+            MmaV v{&p, bar, su32(sA), su32(sB), tmem};
+            tcs::mma_issuer(p.plan, blockIdx.x, v);
+            // every issued MMA completes before TMEM is released
+            mma_commit(bar.drain());
+            mbar_drain(bar.drain(), 0);
         }
     } else {
-        // ---------------- epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 and
-        // columns 16 h .. 16 h + 15 of every group, h = (w - 2) / 4
-        constexpr int HN = TC_N / 2;
-        const int wq = warp & 3, h = (warp - 2) >> 2;
-        const uint32_t tl = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(HN * h);
-        // zero this warp's share of the group accumulators for the first chunk
-#pragma unroll
-        for (int t = 0; t < NG; ++t) tmem_zero16(tl + (uint32_t)(t * TC_N));
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bacc_empty);
-        unsigned g = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            const int m0 = (tile % p.mt) * TC_M, n0 = (tile / p.mt) * TC_N;
-            long long HI[HN], LO[HN];
-#pragma unroll
-            for (int j = 0; j < HN; ++j) {
-                HI[j] = 0;
-                LO[j] = 0;
-            }
-            for (int c = 0; c < nchunks && ok; ++c, ++g) {
-                // lane 0 waits; the outcome is shared so that the warp-collective
-                // tcgen05.ld below always runs with the whole warp
-                int got = 0;
-                if (lane == 0) got = mbar_wait(bacc_full, g & 1u, p.err) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, got, 0) != 0;
-                if (!ok) break;
-                tc_fence_after();
-#pragma unroll
-                for (int t = 0; t < NG; ++t) {
-                    uint32_t v[HN];
-                    tmem_ld16(tl + (uint32_t)(t * TC_N), v);
-#pragma unroll
-                    for (int j = 0; j < HN; ++j) {
-                        const long long x = (long long)__float2int_rz(__uint_as_float(v[j]));
-                        if (t <= 4) HI[j] += x * (1ll << (6 * (4 - t)));
-                        else LO[j] += x * (1ll << (6 * (TMAX - t)));
-                    }
-                    tmem_zero16(tl + (uint32_t)(t * TC_N));
-                }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bacc_empty);
-            }
-            // the accumulators are free again: convert and store while the next
-            // tile's MMAs run
-            const i64 row = m0 + 32 * wq + lane;
-            if (ok && row < p.M) {
-                const int er = p.ea[row];
-#pragma unroll
-                for (int j = 0; j < HN; ++j) {
-                    const i64 col = n0 + HN * h + j;
-                    if (col < p.N) {
-                        double v = ldexp((double)HI[j], -24);
-                        if (TMAX >= 5) v += ldexp((double)LO[j], -6 * TMAX);
-                        const double out = p.alpha * ldexp(v, er + p.eb[col] - 12);
-                        double* cp = p.C + row + col * p.ldc;
-                        *cp = (p.beta == 0.0) ? out : fma(p.beta, *cp, out);
-                    }
-                }
-            }
-        }
+        const int e = warp - 2;                 // epilogue warp 0..15
+        const int h = e / 8, sub = (e / 4) % 2, lq = warp % 4;
+        EpilogueV v;
+        v.p = &p;
+        v.bar = bar;
+        v.lane = lane;
+        v.lq = lq;
+        v.sub = sub;
+        v.tl = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(256 * h + 16 * sub);
+        tcs::epilogue(p.plan, blockIdx.x, h, v);
     }
     tc_fence_before();
     __syncthreads();
@@ -397,11 +455,14 @@ EncodeTiledFn encode_fn() {
 }
 
 // 3-D map over slice planes S[plane][row][k] (k contiguous, ldk elements per
-// row, rows_p rows per plane), box {64, box_rows, box_planes}, 128-byte swizzle.
-int make_plane_map(CUtensorMap* tm, const void* base, i64 ldk, i64 rows_p, int planes, int box_rows, int box_planes) {
+// row, rows_p rows per plane; the map covers k < kext from `base`), box
+// {64, box_rows, box_planes}, 128-byte swizzle.  Rows and k beyond the
+// extent read as zeros.
+int make_plane_map(CUtensorMap* tm, const void* base, i64 ldk, i64 kext, i64 rows_p, int planes, int box_rows,
+                   int box_planes) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) { set_error("cuTensorMapEncodeTiled is unavailable"); return BQRRP_ECUDA; }
-    cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows_p, (cuuint64_t)planes};
+    cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)rows_p, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)rows_p};
     cuuint32_t box[3] = {(cuuint32_t)TC_KB, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -412,19 +473,20 @@ int make_plane_map(CUtensorMap* tm, const void* base, i64 ldk, i64 rows_p, int p
     return 0;
 }
 
-template <int SA, int SB, int TMAX>
-int launch_tc(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M, i64 N,
-              i64 kc, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err) {
+// One launch over k in [0, kext) of the planes starting at As, Bs (row
+// stride ldk): C = alpha (sum over those k) + beta C.
+int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np,
+              i64 ldk, i64 kext, i64 M, i64 N, const int* ea, const int* eb, double alpha, double beta, double* C,
+              i64 ldc, int* err) {
+    if (ldk % 8 != 0) { set_error("ozaki_tc: slice rows must be a multiple of 8 elements"); return BQRRP_EUNSUPPORTED; }
+    if (kext > kOzMaxK) { set_error("ozaki_tc: K above %lld per launch", (long long)kOzMaxK); return BQRRP_EUNSUPPORTED; }
     CUtensorMap tmA, tmB;
-    BQ_TRY(make_plane_map(&tmA, As, ldk, Mp, SA, TC_M, 1));
-    BQ_TRY(make_plane_map(&tmB, Bs, ldk, Np, SB, TC_N, SB));
-    const size_t smem = 1024 + (size_t)TC_NA * TC_ABYTES + (size_t)TC_NB * SB * TC_BPLANE + 8 * (2 * TC_NA + 2 * TC_NB + 3) + 16;
-    BQ_TRY(kernel_attrs((const void*)ozaki_tc_kernel<SA, SB, TMAX>, (int)smem));
+    BQ_TRY(make_plane_map(&tmA, As, ldk, kext, Mp, SA, TC_M, 1));
+    BQ_TRY(make_plane_map(&tmB, Bs, ldk, kext, Np, TC_NP, TC_HN, TC_NP));
+    BQ_TRY(kernel_attrs((const void*)ozaki_tc_kernel, (int)TC_SMEM));
     TcArgs a;
     a.M = M;
     a.N = N;
-    a.KB = (int)cdiv(ldk, TC_KB);
-    a.kbpc = (int)imax(1, kc / TC_KB);
     a.ea = ea;
     a.eb = eb;
     a.alpha = alpha;
@@ -432,28 +494,44 @@ int launch_tc(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16
     a.C = C;
     a.ldc = ldc;
     a.err = err;
-    const i64 mt = cdiv(M, TC_M), tiles = mt * cdiv(N, TC_N);
-    if (tiles > (i64)1 << 30) { set_error("ozaki_tc: too many tiles"); return BQRRP_EUNSUPPORTED; }
-    a.mt = (int)mt;
-    a.ntiles = (int)tiles;
-    const unsigned grid = (unsigned)imin(tiles, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
-    ozaki_tc_kernel<SA, SB, TMAX><<<grid, TC_THREADS, smem, c.stream>>>(tmA, tmB, a);
+    const i64 KB = cdiv(kext, TC_KB), mt = cdiv(M, TC_M), nct = cdiv(N, TC_N);
+    if (mt * nct > (i64)1 << 30 || KB > (i64)1 << 30) { set_error("ozaki_tc: too many tiles"); return BQRRP_EUNSUPPORTED; }
+    a.plan.SA = SA;
+    a.plan.KB = (int)KB;
+    a.plan.CL = CL;
+    a.plan.mt = (int)mt;
+    a.plan.nct = (int)nct;
+    a.plan.ntiles = (int)(mt * nct);
+    a.plan.grid = (int)imin(mt * nct, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
+    int lg = 0;
+    while (((i64)1 << lg) < kext) ++lg;
+    a.dsh = lg + 1 < 11 ? 11 : lg + 1;
+    ozaki_tc_kernel<<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
     BQ_LAUNCH_CHECK();
     return 0;
 }
 
 }  // namespace
 
-// Slice products on tcgen05: the 9 x 9 FP64 split (53 pairs) and the +-1
-// sketch (one A plane, nine B planes).
+// Slice products on tcgen05: the 8 x 8 FP64 split (the 36 pairs with
+// p + q <= 7, exact in chunks of two k blocks) and the +-1 sketch (one A
+// plane, eight B planes, exact in chunks of 2048 k blocks).
+// K beyond kOzMaxK runs as consecutive launches over K pieces, each adding
+// its FP64-rounded part into C.
 int ozaki_tc_gemm(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
                   i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err) {
-    return launch_tc<9, 9, 9>(c, As, Mp, Bs, Np, ldk, M, N, 256, ea, eb, alpha, beta, C, ldc, err);
+    for (i64 k0 = 0; k0 < ldk; k0 += kOzMaxK)
+        BQ_TRY(launch_tc(c, kOzPlanes, 2, As + k0, Mp, Bs + k0, Np, ldk, imin(kOzMaxK, ldk - k0), M, N, ea, eb,
+                         alpha, k0 == 0 ? beta : 1.0, C, ldc, err));
+    return 0;
 }
 
 int ozaki_tc_sketch(const Ctx& c, const __nv_bfloat16* Ss, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
                     i64 N, const int* ea, const int* eb, double* C, i64 ldc, int* err) {
-    return launch_tc<1, 9, 8>(c, Ss, Mp, Bs, Np, ldk, M, N, (i64)1 << 17, ea, eb, 1.0, 0.0, C, ldc, err);
+    for (i64 k0 = 0; k0 < ldk; k0 += kOzMaxK)
+        BQ_TRY(launch_tc(c, 1, (int)(kOzMaxK / TC_KB), Ss + k0, Mp, Bs + k0, Np, ldk, imin(kOzMaxK, ldk - k0), M, N,
+                         ea, eb, 1.0, k0 == 0 ? 0.0 : 1.0, C, ldc, err));
+    return 0;
 }
 
 }  // namespace bq

@@ -1,12 +1,15 @@
 """The mixed-precision form: FP64-accurate products on the bf16 tensor cores
-(exact 6-bit slices, FP32 sums that stay below 2^24, FP64 recombination),
-through the C ABI.
+(exact 7-bit slices, FP32 sums that stay below 2^24, exact integer
+recombination rounded once to FP64), through the C ABI.
 
 Bar: integer data, whose slice products are exact, must come out bit-exact.
-General data must stay within 4 K 2^-53 max|op(A)(i,:)| max|op(B)(:,j)| of the
-exact product: that is the splitting's error model (truncation below 2^-54 of
-the row / column maxima, plus the FP64 recombination).  The factorization in
-mixed precision is held to the same bar as the FP64 form.
+General data must stay within 8 K 2^-53 max|op(A)(i,:)| max|op(B)(:,j)| of the
+exact product: the splitting's error model is truncation below 2^-56 of the
+row / column maxima, the dropped slice pairs (p + q >= 8, below 2^-53.2 of
+max|a| max|b| per term) and the rounding of each 128-deep chunk's sum (at most
+K/128 2^(dsh-1) 2^-63 relative, dsh = ceil(log2 K) + 1), together under
+2 K 2^-53.  The factorization in mixed precision is held to the same bar as the
+FP64 form.
 """
 import numpy as np
 import pytest
@@ -57,10 +60,45 @@ def test_ozaki_within_fp64_error_model(ta, tb, M, N, K):
     ref = -0.75 * (oA @ oB) + 1.5 * C0
     amax = np.abs(oA).max(axis=1)[:, None]
     bmax = np.abs(oB).max(axis=0)[None, :]
-    # splitting error (below 2^-54 of the row/column maxima per term, ten groups)
+    # splitting error (below about 2^-53 of the row/column maxima per term)
     # plus the FP64 rounding of the reference product itself
     bound = 8 * K * U * 0.75 * amax * bmax + 4 * U * (0.75 * (np.abs(oA) @ np.abs(oB)) + np.abs(1.5 * C0))
     assert np.all(np.abs(np_(C) - ref) <= bound)
+
+
+def test_ozaki_long_k_runs_in_pieces():
+    """K above 2^17 runs as consecutive launches over K pieces (integer data:
+    exact; general data: within the error model)."""
+    rng = np.random.default_rng(11)
+    M, N, K = 70, 66, (1 << 17) + 3000
+    A = rng.integers(-(1 << 12), 1 << 12, size=(M, K)).astype(np.float64)
+    Bm = rng.integers(-(1 << 12), 1 << 12, size=(K, N)).astype(np.float64)
+    C = dev(np.zeros((M, N)))
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
+    assert np.array_equal(np_(C), (A.astype(np.int64) @ Bm.astype(np.int64)).astype(np.float64))
+    A = rng.standard_normal((M, K))
+    Bm = rng.standard_normal((K, N))
+    C0 = rng.standard_normal((M, N))
+    C = dev(C0)
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 1.0, C)
+    ref = A @ Bm + C0
+    bound = 8 * K * U * np.abs(A).max(axis=1)[:, None] * np.abs(Bm).max(axis=0)[None, :]
+    assert np.all(np.abs(np_(C) - ref) <= bound + 4 * U * (np.abs(A) @ np.abs(Bm) + np.abs(C0)))
+
+
+def test_ozaki_same_sign_data_near_the_exactness_bound():
+    """All entries positive with every slice large: the group sums of a chunk
+    approach the FP32 exactness bound (8 * 128 * 127^2 < 2^24)."""
+    rng = np.random.default_rng(12)
+    M, N, K = 256, 192, 4096
+    # 1 - j 2^-53 with j < 2^10: the 56-bit fixed-point value is 2^56 - 8j, so
+    # slices 0..5 are all 127 (and the dropped pairs are as large as they get)
+    A = 1.0 - rng.integers(1, 1 << 10, size=(M, K)) * 2.0 ** -53
+    Bm = 1.0 - rng.integers(1, 1 << 10, size=(K, N)) * 2.0 ** -53
+    C = dev(np.zeros((M, N)))
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
+    ref = A @ Bm
+    assert np.all(np.abs(np_(C) - ref) <= 8 * K * U + 4 * U * ref)
 
 
 def test_ozaki_wide_dynamic_range_rows_and_columns():
@@ -131,9 +169,14 @@ def test_mixed_factorization_meets_the_fp64_bar(case):
                   + 1e-13 * np.linalg.norm(A))
 
 
-@pytest.mark.parametrize("m,n", [(300, 200), (2049, 130), (1000, 1000), (5000, 300)])
-def test_own_qr_mixed_matches_oracle(m, n):
+@pytest.mark.parametrize("m,n,zero_col", [(300, 200, None), (2049, 130, None), (1000, 1000, None),
+                                          (5000, 300, None), (700, 600, 300)])
+def test_own_qr_mixed_matches_oracle(m, n, zero_col):
+    """The two-level blocked QR (outer blocks of 256; the last case has a zero
+    column, so a reflector with tau = 0 enters a block reflector)."""
     A = W.gaussian(m, n, m + 2 * n)
+    if zero_col is not None:
+        A[:, zero_col] = 0.0
     Ad = dev(A)
     tau = np_(bq.binding.bqrrp_geqrf_mixed(Ad))
     F = np_(Ad)
