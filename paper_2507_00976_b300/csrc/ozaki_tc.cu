@@ -64,7 +64,7 @@ constexpr int TC_BHALF = TC_NP * TC_HN * TC_KB * 2;             // 32 KiB per B 
 constexpr int TC_NBAR = 2 * tcs::kNAS + 2 * tcs::kNBS + 2 + 2 + 1;
 constexpr size_t TC_SMEM =
     1024 + (size_t)tcs::kNAS * TC_APLANE + (size_t)tcs::kNBS * TC_BHALF + 8 * TC_NBAR + 16;
-constexpr unsigned long long kTcSpin = 1ull << 26;
+constexpr unsigned long long kTcSpin = 1ull << 26;   // test_wait polls: a few seconds
 static_assert(TC_SMEM <= 232448, "shared memory of the slice GEMM exceeds the per-CTA limit");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,7 +87,9 @@ __device__ __forceinline__ bool mbar_test(uint32_t b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with this parity; false (and *err set) on timeout.
+// Bounded wait for the phase with this parity; false (and *err set) on
+// timeout, or when another role has set it.  (Polling with test_wait measured
+// faster here than try_wait with a suspend-time hint.)
 __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, int* err) {
     for (unsigned long long i = 0; i < kTcSpin; ++i) {
         if (mbar_test(b, parity)) return true;
@@ -96,6 +98,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, int* err)
     atomicExch(err, 1);
     return false;
 }
+// The same wait with a back-off of about 100 ns between polls, for the
+// epilogue warps: their waits are long, and spinning at full rate would take
+// issue slots from the MMA-issuing thread that shares their sub-partition.
+__device__ __forceinline__ bool mbar_wait_backoff(uint32_t b, uint32_t parity, int* err) {
+    for (unsigned long long i = 0; i < (kTcSpin >> 4); ++i) {
+        if (mbar_test(b, parity)) return true;
+        if ((i & 255) == 255 && *((volatile int*)err)) return false;
+        __nanosleep(100);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
 // Bounded wait that ignores the error flag: used to drain in-flight copies and
 // MMAs before the CTA releases its shared memory and TMEM.
 __device__ __forceinline__ void mbar_drain(uint32_t b, uint32_t parity) {
@@ -126,11 +141,18 @@ __host__ __device__ constexpr uint32_t idesc_f16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
-// D (TMEM) += A (smem) B (smem)
-__device__ __forceinline__ void mma_f16_acc(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc) {
+// D (TMEM) += A (smem) B (smem) for the four 16-deep k steps of a 64-deep k
+// block: the descriptors advance by 32 bytes (2 in 16-byte units) per step
+// inside the 128-byte swizzled rows.
+__device__ __forceinline__ void mma_f16_kblock(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc) {
     asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            dtmem),
+        "{\n.reg .pred p;\n.reg .b64 a1, a2, a3, b1, b2, b3;\nsetp.ne.b32 p, 1, 0;\n"
+        "add.s64 a1, %1, 2;\nadd.s64 a2, %1, 4;\nadd.s64 a3, %1, 6;\n"
+        "add.s64 b1, %2, 2;\nadd.s64 b2, %2, 4;\nadd.s64 b3, %2, 6;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, p;\n}\n" ::"r"(dtmem),
         "l"(ad), "l"(bd), "r"(idesc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -148,12 +170,23 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
         : "memory");
 }
 
-// 4 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+// 4 consecutive 32-bit TMEM columns of this thread's lane (no wait: the
+// caller issues tcgen05.wait::ld before using them).
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t& v0, uint32_t& v1, uint32_t& v2, uint32_t& v3) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3)
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Integer-valued FP32 (|v| < 2^24) to int32: exact.
+__device__ __forceinline__ int f2i(uint32_t v) { return __float2int_rz(__uint_as_float(v)); }
+
+// The out-of-range case of i64_scaled (kept out of line so that its FP64
+// instructions are not executed speculatively on the common path).
+__device__ __noinline__ double i64_scaled_slow(unsigned long long a, bool neg, int e) {
+    const double v = ldexp((double)a, e);
+    return neg ? -v : v;
 }
 
 // w * 2^e rounded to the nearest double (ties to even), w a 64-bit integer,
@@ -181,10 +214,7 @@ __device__ __forceinline__ double i64_scaled(long long w, int e) {
         }
     }
     const int be = ex + 1023;
-    if (be <= 0 || be >= 2047) {
-        const double v = ldexp((double)a, e);
-        return neg ? -v : v;
-    }
+    if (be <= 0 || be >= 2047) return i64_scaled_slow(a, neg, e);
     const unsigned long long bits =
         ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
     return __longlong_as_double((long long)bits);
@@ -221,23 +251,26 @@ struct ProducerV {
     uint32_t sA, sB;
     const CUtensorMap* tmA;
     const CUtensorMap* tmB;
+    int m0, n0;                    // origin of the current tile
     long long last_a[tcs::kNAS];   // last fill issued per slot (-1: none)
     long long last_b[tcs::kNBS];
-    __device__ __forceinline__ bool load_a(int tile, int kb, int pl, int slot, long long fill) {
-        if (!mbar_wait(bar.empty_a(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
+    __device__ __forceinline__ void tile_begin(int tile) {
         int rt, ct;
         tcs::tile_coords(p->plan, tile, &rt, &ct);
+        m0 = rt * TC_M;
+        n0 = ct * TC_N;
+    }
+    __device__ __forceinline__ bool load_a(int, int kb, int pl, int slot, long long fill) {
+        if (!mbar_wait(bar.empty_a(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
         mbar_expect_tx(bar.full_a(slot), TC_APLANE);
-        tma_load_3d(sA + slot * TC_APLANE, tmA, kb * TC_KB, rt * TC_M, pl, bar.full_a(slot));
+        tma_load_3d(sA + slot * TC_APLANE, tmA, kb * TC_KB, m0, pl, bar.full_a(slot));
         last_a[slot] = fill;
         return true;
     }
-    __device__ __forceinline__ bool load_b(int tile, int kb, int h, int slot, long long fill) {
+    __device__ __forceinline__ bool load_b(int, int kb, int h, int slot, long long fill) {
         if (!mbar_wait(bar.empty_b(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
-        int rt, ct;
-        tcs::tile_coords(p->plan, tile, &rt, &ct);
         mbar_expect_tx(bar.full_b(slot), TC_BHALF);
-        tma_load_3d(sB + slot * TC_BHALF, tmB, kb * TC_KB, ct * TC_N + h * TC_HN, 0, bar.full_b(slot));
+        tma_load_3d(sB + slot * TC_BHALF, tmB, kb * TC_KB, n0 + h * TC_HN, 0, bar.full_b(slot));
         last_b[slot] = fill;
         return true;
     }
@@ -246,7 +279,8 @@ struct ProducerV {
 struct MmaV {
     const TcArgs* p;
     Bars bar;
-    uint32_t sA, sB, tmem;
+    uint64_t ad0, bd0;   // descriptors of A slot 0 and B slot 0
+    uint32_t tmem;
     __device__ __forceinline__ bool wait_acc_empty(int h, long long chunk) {
         if (!mbar_wait(bar.acc_empty(h), (uint32_t)(chunk & 1), p->err)) return false;
         tc_fence_after();
@@ -262,14 +296,12 @@ struct MmaV {
         tc_fence_after();
         return true;
     }
+    // slot offsets go straight into the descriptors' start-address field (16-byte
+    // units; every slot address stays below 2^18)
     __device__ __forceinline__ void mma(int, int, int h, int pl, int sa, int sb) {
-        const uint64_t ad = sdesc(sA + sa * TC_APLANE);
-        const uint64_t bd = sdesc(sB + sb * TC_BHALF);   // planes 0 .. 7 - pl stacked along N
-        const uint32_t idn = idesc_f16(TC_HN * (TC_NG - pl));
-        const uint32_t d = tmem + (uint32_t)(256 * h + TC_HN * pl);
-#pragma unroll
-        for (int ks = 0; ks < TC_KB / 16; ++ks)   // +32 bytes per 16-deep k step inside the swizzled rows
-            mma_f16_acc(d, ad + (uint64_t)(ks * 2), bd + (uint64_t)(ks * 2), idn);
+        const uint64_t ad = ad0 + (uint64_t)(sa * (TC_APLANE >> 4));
+        const uint64_t bd = bd0 + (uint64_t)(sb * (TC_BHALF >> 4));   // planes 0 .. 7 - pl stacked along N
+        mma_f16_kblock(tmem + (uint32_t)(256 * h + TC_HN * pl), ad, bd, idesc_f16(TC_HN * (TC_NG - pl)));
     }
     __device__ __forceinline__ void release_a(int sa) { mma_commit(bar.empty_a(sa)); }
     __device__ __forceinline__ void release_b(int sb) { mma_commit(bar.empty_b(sb)); }
@@ -301,7 +333,7 @@ struct EpilogueV {
         // lane 0 waits; the outcome is shared so that the warp-collective
         // tcgen05.ld always runs with the whole warp
         int got = 0;
-        if (lane == 0) got = mbar_wait(bar.acc_full(h), (uint32_t)(chunk & 1), p->err) ? 1 : 0;
+        if (lane == 0) got = mbar_wait_backoff(bar.acc_full(h), (uint32_t)(chunk & 1), p->err) ? 1 : 0;
         if (__shfl_sync(0xffffffffu, got, 0) == 0) return false;
         tc_fence_after();
         return true;
@@ -311,27 +343,30 @@ struct EpilogueV {
         for (int j = 0; j < 16; ++j) acc[j] = 0;
     }
     // W = HI 2^28 + LO with HI = sum_{t <= 3} G_t 2^(7(3-t)) and
-    // LO = sum_{t >= 4} G_t 2^(7(7-t)) (Horner steps of 2^7, exact), four
+    // LO = sum_{t >= 4} G_t 2^(7(7-t)), exact; the group sums obey
+    // |G_t| <= (t + 1) 128 127^2 < (t + 1) 2^21, so the pairs G_0 2^7 + G_1,
+    // G_2 2^7 + G_3, G_4 2^7 + G_5 and G_6 2^7 + G_7 fit in 32 bits.  Four
     // columns at a time; HI 2^28 is a multiple of 2^dsh, so only LO is rounded.
     __device__ __forceinline__ void read_chunk(int) {
-        const int dsh = p->dsh;
+        const int dsh = p->dsh, sh = 28 - dsh;
         const long long half = 1ll << (dsh - 1);
 #pragma unroll
         for (int cb = 0; cb < 4; ++cb) {
-            long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+            uint32_t v[TC_NG][4];
 #pragma unroll
-            for (int t = 0; t < TC_NG; ++t) {
-                uint32_t v[4];
-                tmem_ld4(tl + (uint32_t)(TC_HN * t + 4 * cb), v);
+            for (int t = 0; t < TC_NG; ++t)
+                tmem_ld4(tl + (uint32_t)(TC_HN * t + 4 * cb), v[t][0], v[t][1], v[t][2], v[t][3]);
+            tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const long long x = (long long)__float2int_rz(__uint_as_float(v[j]));
-                    if (t <= 3) hi[j] = hi[j] * 128 + x;
-                    else lo[j] = lo[j] * 128 + x;
-                }
+            for (int j = 0; j < 4; ++j) {
+                const int p01 = f2i(v[0][j]) * 128 + f2i(v[1][j]);
+                const int p23 = f2i(v[2][j]) * 128 + f2i(v[3][j]);
+                const int p45 = f2i(v[4][j]) * 128 + f2i(v[5][j]);
+                const int p67 = f2i(v[6][j]) * 128 + f2i(v[7][j]);
+                const long long hi = (long long)p01 * 16384 + p23;
+                const long long lo = (long long)p45 * 16384 + p67;
+                acc[4 * cb + j] += (hi << sh) + ((lo + half) >> dsh);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[4 * cb + j] += (hi[j] << (28 - dsh)) + ((lo[j] + half) >> dsh);
         }
 #pragma unroll
         for (int t = 0; t < TC_NG; ++t) tmem_zero16(tl + (uint32_t)(TC_HN * t));
@@ -341,21 +376,42 @@ struct EpilogueV {
         tcs::tile_coords(p->plan, tile, &rt, &ct);
         const i64 row = (i64)rt * TC_M + 32 * lq + lane;
         if (row >= p->M) return;
-        const int er = p->ea[row];
+        const int er = p->ea[row] - 63 + p->dsh;
         const double alpha = p->alpha, beta = p->beta;
+        const i64 col0 = (i64)ct * TC_N + TC_HN * h + 16 * sub;
+        const int ncol = (int)(p->N - col0 < 16 ? p->N - col0 : 16);
+        double* cp = p->C + row + col0 * p->ldc;
+        // alpha = +-1 (a negation of the integer) and beta = 0 or 1 (the
+        // library's products) take loops of their own, so that the only FP64
+        // instruction is the addition into C; anything else takes the general
+        // loop.  (A select between the forms inside one loop would execute the
+        // FP64 multiply and FMA of every form.)
+        if ((alpha == 1.0 || alpha == -1.0) && beta == 0.0) {
+            const bool neg = alpha == -1.0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const i64 col = (i64)ct * TC_N + TC_HN * h + 16 * sub + j;
-            if (col < p->N) {
-                double out = i64_scaled(acc[j], er + p->eb[col] - 63 + p->dsh);
-                if (alpha != 1.0) out = (alpha == -1.0) ? -out : alpha * out;
-                double* cp = p->C + row + col * p->ldc;
-                *cp = (beta == 0.0) ? out : (beta == 1.0 ? *cp + out : fma(beta, *cp, out));
-            }
+            for (int j = 0; j < 16; ++j)
+                if (j < ncol) cp[j * p->ldc] = i64_scaled(neg ? -acc[j] : acc[j], er + p->eb[col0 + j]);
+        } else if ((alpha == 1.0 || alpha == -1.0) && beta == 1.0) {
+            const bool neg = alpha == -1.0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < ncol) {
+                    double* cj = cp + j * p->ldc;
+                    *cj = *cj + i64_scaled(neg ? -acc[j] : acc[j], er + p->eb[col0 + j]);
+                }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < ncol) {
+                    double* cj = cp + j * p->ldc;
+                    const double out = alpha * i64_scaled(acc[j], er + p->eb[col0 + j]);
+                    *cj = (beta == 0.0) ? out : fma(beta, *cj, out);
+                }
         }
     }
 };
 
+template <int SA>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ TcArgs p) {
@@ -397,10 +453,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            ProducerV v{&p, bar, su32(sA), su32(sB), &tmA, &tmB, {}, {}};
+            ProducerV v{&p, bar, su32(sA), su32(sB), &tmA, &tmB, 0, 0, {}, {}};
             for (int s = 0; s < tcs::kNAS; ++s) v.last_a[s] = -1;
             for (int s = 0; s < tcs::kNBS; ++s) v.last_b[s] = -1;
-            tcs::producer(p.plan, blockIdx.x, v);
+            tcs::producer<SA>(p.plan, blockIdx.x, v);
             // every issued copy lands before the CTA may exit (fill n of a slot
             // completes phase n of its full barrier)
             for (int s = 0; s < tcs::kNAS; ++s)
@@ -410,8 +466,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            MmaV v{&p, bar, su32(sA), su32(sB), tmem};
-            tcs::mma_issuer(p.plan, blockIdx.x, v);
+            MmaV v{&p, bar, sdesc(su32(sA)), sdesc(su32(sB)), tmem};
+            tcs::mma_issuer<SA>(p.plan, blockIdx.x, v);
             // every issued MMA completes before TMEM is released
             mma_commit(bar.drain());
             mbar_drain(bar.drain(), 0);
@@ -480,10 +536,12 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
               i64 ldc, int* err) {
     if (ldk % 8 != 0) { set_error("ozaki_tc: slice rows must be a multiple of 8 elements"); return BQRRP_EUNSUPPORTED; }
     if (kext > kOzMaxK) { set_error("ozaki_tc: K above %lld per launch", (long long)kOzMaxK); return BQRRP_EUNSUPPORTED; }
+    if (CL < 2 || (CL & (CL - 1)) != 0) { set_error("ozaki_tc: chunk must be a power of two"); return BQRRP_EUNSUPPORTED; }
     CUtensorMap tmA, tmB;
     BQ_TRY(make_plane_map(&tmA, As, ldk, kext, Mp, SA, TC_M, 1));
     BQ_TRY(make_plane_map(&tmB, Bs, ldk, kext, Np, TC_NP, TC_HN, TC_NP));
-    BQ_TRY(kernel_attrs((const void*)ozaki_tc_kernel, (int)TC_SMEM));
+    const void* fn = SA == 1 ? (const void*)ozaki_tc_kernel<1> : (const void*)ozaki_tc_kernel<kOzPlanes>;
+    BQ_TRY(kernel_attrs(fn, (int)TC_SMEM));
     TcArgs a;
     a.M = M;
     a.N = N;
@@ -506,7 +564,10 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
     int lg = 0;
     while (((i64)1 << lg) < kext) ++lg;
     a.dsh = lg + 1 < 11 ? 11 : lg + 1;
-    ozaki_tc_kernel<<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
+    if (SA == 1)
+        ozaki_tc_kernel<1><<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
+    else
+        ozaki_tc_kernel<kOzPlanes><<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
     BQ_LAUNCH_CHECK();
     return 0;
 }

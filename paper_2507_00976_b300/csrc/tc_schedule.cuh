@@ -34,7 +34,7 @@ constexpr int kGroupRows = 64;   // row tiles per raster group
 struct Plan {
     int SA;       // planes of op(A): 8 (FP64 split) or 1 (the +-1 sketch)
     int KB;       // 64-deep k blocks per tile
-    int CL;       // k blocks per exact chunk (2, or a large value for the sketch)
+    int CL;       // k blocks per exact chunk, a power of two (2, or 2048 for the sketch)
     int mt, nct;  // row tiles, column tiles
     int ntiles;   // mt * nct
     int grid;     // persistent CTAs; CTA c takes tiles c, c + grid, ...
@@ -57,8 +57,8 @@ TC_HD void tile_coords(const Plan& P, int tile, int* rt, int* ct) {
 TC_HD int early_half(const Plan& P, int it) { return (P.CL == 2 && (P.KB % 2) == 0) ? (it & 1) : 0; }
 
 TC_HD bool natural_end(const Plan& P, int E, int h, int kb) {
-    const int shift = (h == E) ? P.CL / 2 : 0;
-    return ((kb + 1 + shift) % P.CL) == 0;
+    const int shift = (h == E) ? (P.CL >> 1) : 0;
+    return ((kb + 1 + shift) & (P.CL - 1)) == 0;
 }
 
 // Does the chunk of half h end with k block kb (its accumulators are read)?
@@ -86,40 +86,62 @@ TC_HD bool ascending(long long seg) {
 // Slot and fill count of A plane p in global k block G.  With 8 planes each
 // plane has a slot of its own (refilled once per k block); with one plane the
 // slots form a ring over k blocks.
-TC_HD int a_slot(const Plan& P, long long G, int p) { return P.SA == 1 ? (int)(G % kNAS) : p; }
-TC_HD long long a_fill(const Plan& P, long long G) { return P.SA == 1 ? G / kNAS : G; }
+TC_HD int a_slot(const Plan& P, long long G, int p) { return P.SA == 1 ? (int)(G & (kNAS - 1)) : p; }
+TC_HD long long a_fill(const Plan& P, long long G) { return P.SA == 1 ? (G >> 3) : G; }
+static_assert(kNAS == 8, "a_slot and a_fill assume eight A slots");
+
+// Position in the B ring: slot and fill count, advanced without divisions.
+struct BRing {
+    int slot = 0;
+    long long fill = 0;
+    TC_HD void next() {
+        if (++slot == kNBS) {
+            slot = 0;
+            ++fill;
+        }
+    }
+};
 
 // ---------------------------------------------------------------- roles
 // Visitor methods return false when a bounded wait gave up; the role stops.
 
 // TMA producer: per k block the first segment's B half, the A planes in the
-// order the MMAs need them, then the second segment's B half.
-template <class V>
+// order the MMAs need them, then the second segment's B half.  SA (the number
+// of A planes, P.SA) is a compile-time constant so that the plane loops unroll.
+template <int SA, class V>
 TC_HD void producer(const Plan& P, int cta, V& v) {
-    long long G = 0, bseg = 0;
+    long long G = 0;
+    BRing br;
     int it = 0;
     for (int tile = cta; tile < P.ntiles; tile += P.grid, ++it) {
         const int E = early_half(P, it);
+        v.tile_begin(tile);
         for (int kb = 0; kb < P.KB; ++kb, ++G) {
             const int h1 = first_half(P, E, kb);
-            if (!v.load_b(tile, kb, h1, (int)(bseg % kNBS), bseg / kNBS)) return;
-            ++bseg;
+            if (!v.load_b(tile, kb, h1, br.slot, br.fill)) return;
+            br.next();
+            const long long fill = a_fill(P, G);
             const bool asc = ascending(2 * G);
-            for (int j = 0; j < P.SA; ++j) {
-                const int p = asc ? j : P.SA - 1 - j;
-                if (!v.load_a(tile, kb, p, a_slot(P, G, p), a_fill(P, G))) return;
+#pragma unroll 1
+            for (int j = 0; j < SA; ++j) {
+                const int p = asc ? j : SA - 1 - j;
+                if (!v.load_a(tile, kb, p, a_slot(P, G, p), fill)) return;
             }
-            if (!v.load_b(tile, kb, 1 - h1, (int)(bseg % kNBS), bseg / kNBS)) return;
-            ++bseg;
+            if (!v.load_b(tile, kb, 1 - h1, br.slot, br.fill)) return;
+            br.next();
         }
     }
 }
 
 // MMA issuer: per k block two segments; a half waits for its accumulators to
 // be free at the start of each of its chunks and signals them full at the end.
-template <class V>
+// The plane loops are not unrolled: the single issuing thread's code stays
+// small (unrolling them measured slower, the kernel's code being large).
+
+template <int SA, class V>
 TC_HD void mma_issuer(const Plan& P, int cta, V& v) {
-    long long G = 0, bseg = 0;
+    long long G = 0;
+    BRing br;
     long long chunks[2] = {0, 0};
     int it = 0;
     for (int tile = cta; tile < P.ntiles; tile += P.grid, ++it) {
@@ -130,18 +152,20 @@ TC_HD void mma_issuer(const Plan& P, int cta, V& v) {
                 const int h = j ? 1 - h1 : h1;
                 if (kb == 0 || chunk_end(P, E, h, kb - 1))
                     if (!v.wait_acc_empty(h, chunks[h])) return;
-                const int sb = (int)(bseg % kNBS);
-                if (!v.wait_full_b(sb, bseg / kNBS)) return;
+                const int sb = br.slot;
+                if (!v.wait_full_b(sb, br.fill)) return;
                 const bool asc = ascending(2 * G + j);
-                for (int jj = 0; jj < P.SA; ++jj) {
-                    const int p = asc ? jj : P.SA - 1 - jj;
+                const long long fill = a_fill(P, G);
+#pragma unroll 1
+                for (int jj = 0; jj < SA; ++jj) {
+                    const int p = asc ? jj : SA - 1 - jj;
                     const int sa = a_slot(P, G, p);
-                    if (j == 0 && !v.wait_full_a(sa, a_fill(P, G))) return;
+                    if (j == 0 && !v.wait_full_a(sa, fill)) return;
                     v.mma(tile, kb, h, p, sa, sb);
                     if (j == 1) v.release_a(sa);
                 }
                 v.release_b(sb);
-                ++bseg;
+                br.next();
                 if (chunk_end(P, E, h, kb)) {
                     v.acc_ready(h);
                     ++chunks[h];

@@ -86,6 +86,7 @@ struct Sim {
 struct ProdRec {
     Sim& S;
     std::vector<Step>& out;
+    void tile_begin(int) {}
     bool load_a(int tile, int kb, int p, int slot, long long fill) {
         out.push_back({[this, slot, fill] { return S.empty_a[slot].passes(fill - 1); },
                        [this, tile, kb, p, slot] {
@@ -226,9 +227,16 @@ int main(int argc, char** argv) {
         Sim S(P, cta);
         std::vector<std::vector<Step>> roles(18);
         ProdRec pr{S, roles[0]};
-        tcs::producer(P, cta, pr);
         MmaRec mr{S, roles[1]};
-        tcs::mma_issuer(P, cta, mr);
+        if (P.SA == 8) {
+            tcs::producer<8>(P, cta, pr);
+            tcs::mma_issuer<8>(P, cta, mr);
+        } else if (P.SA == 1) {
+            tcs::producer<1>(P, cta, pr);
+            tcs::mma_issuer<1>(P, cta, mr);
+        } else {
+            fail("SA must be 8 or 1");
+        }
         std::vector<EpiRec> ep;
         ep.reserve(16);
         for (int w = 0; w < 16; ++w) ep.push_back(EpiRec{S, roles[2 + w], w});
