@@ -20,19 +20,18 @@
 // 128-byte swizzled) and three B slots of one half-stage (the 8 planes of 32
 // columns x 64 k, 32 KiB), with full/empty mbarriers.
 //
-// Warp roles (608 threads); the order of their work is tc_schedule.cuh's:
+// Warp roles (576 threads); the order of their work is tc_schedule.cuh's:
 //   warp 0      TMA producer (one thread): per 64-deep k block the B half of
-//               half 0, the SA A planes, the B half of half 1;
-//   warps 1, 2  one thread each issues the MMAs of half 0 and half 1 (warp 1
-//               also allocates the 512 TMEM columns).  Segment (k block,
-//               half h), A plane p: the B planes q = 0..7-p of the half lie back
-//               to back in its B slot, so one tcgen05.mma.kind::f16 (M = 128,
-//               N = 32 (8 - p), K = 16) whose accumulator starts at TMEM column
-//               256 h + 32 p lands plane q in group p + q; four such MMAs cover
-//               the k block.  The halves' chunk ends are staggered, so while
-//               one issuer waits for its half's epilogue the other keeps the
-//               tensor core busy (the two issue streams share it);
-//   warps 3-18  epilogue, eight warps per half (warp w reads TMEM lanes
+//               the first segment, the SA A planes, the B half of the second;
+//   warp 1      allocates the 512 TMEM columns; one thread issues the MMAs.
+//               Segment (k block, half h), A plane p: the B planes q = 0..7-p of
+//               the half lie back to back in its B slot, so one
+//               tcgen05.mma.kind::f16 (M = 128, N = 32 (8 - p), K = 16) whose
+//               accumulator starts at TMEM column 256 h + 32 p lands plane q in
+//               group p + q; four such MMAs cover the k block.  The half whose
+//               chunk ends in a k block goes first, so the epilogue of one half
+//               overlaps the other half's MMAs;
+//   warps 2-17  epilogue, eight warps per half (warp w reads TMEM lanes
 //               32 (w % 4) ..; two warps share a lane quarter, 16 columns
 //               each).  After each chunk a warp reads the eight groups with
 //               tcgen05.ld, zeroes them with tcgen05.st, releases the half and
@@ -59,10 +58,10 @@ constexpr int TC_M = 128, TC_N = 64, TC_HN = 32, TC_KB = 64;   // tile rows, col
 constexpr int TC_NP = 8;                                        // planes of op(B)
 constexpr int TC_NG = 8;                                        // groups t = 0..7
 constexpr int TC_EPI = 16;                                      // epilogue warps
-constexpr int TC_THREADS = 96 + 32 * TC_EPI;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI;
 constexpr int TC_APLANE = TC_M * TC_KB * 2;                     // 16 KiB per A slot
 constexpr int TC_BHALF = TC_NP * TC_HN * TC_KB * 2;             // 32 KiB per B slot
-constexpr int TC_NBAR = 2 * tcs::kNAS + 2 * tcs::kNBS + 2 + 2 + 2;
+constexpr int TC_NBAR = 2 * tcs::kNAS + 2 * tcs::kNBS + 2 + 2 + 1;
 constexpr size_t TC_SMEM =
     1024 + (size_t)tcs::kNAS * TC_APLANE + (size_t)tcs::kNBS * TC_BHALF + 8 * TC_NBAR + 16;
 constexpr unsigned long long kTcSpin = 1ull << 26;   // test_wait polls: a few seconds
@@ -233,7 +232,7 @@ struct TcArgs {
     int* err;
 };
 
-// Barrier addresses: full_a[8], empty_a[8], full_b[3], empty_b[3], acc_full[2], acc_empty[2], drain[2].
+// Barrier addresses: full_a[8], empty_a[8], full_b[3], empty_b[3], acc_full[2], acc_empty[2], drain.
 struct Bars {
     uint32_t base;
     __device__ uint32_t full_a(int s) const { return base + 8 * s; }
@@ -242,7 +241,7 @@ struct Bars {
     __device__ uint32_t empty_b(int s) const { return base + 8 * (2 * tcs::kNAS + tcs::kNBS + s); }
     __device__ uint32_t acc_full(int h) const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + h); }
     __device__ uint32_t acc_empty(int h) const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + 2 + h); }
-    __device__ uint32_t drain(int h) const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + 4 + h); }
+    __device__ uint32_t drain() const { return base + 8 * (2 * tcs::kNAS + 2 * tcs::kNBS + 4); }
 };
 
 // ---------------------------------------------------------------- role visitors
@@ -429,7 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < tcs::kNAS; ++s) {
             mbar_init(bar.full_a(s), 1);
-            mbar_init(bar.empty_a(s), 2);   // released by both issuers
+            mbar_init(bar.empty_a(s), 1);
         }
         for (int s = 0; s < tcs::kNBS; ++s) {
             mbar_init(bar.full_b(s), 1);
@@ -439,8 +438,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(bar.acc_full(h), 1);
             mbar_init(bar.acc_empty(h), TC_EPI / 2);
         }
-        mbar_init(bar.drain(0), 1);
-        mbar_init(bar.drain(1), 1);
+        mbar_init(bar.drain(), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -466,17 +464,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int s = 0; s < tcs::kNBS; ++s)
                 if (v.last_b[s] >= 0) mbar_drain(bar.full_b(s), (uint32_t)(v.last_b[s] & 1));
         }
-    } else if (warp == 1 || warp == 2) {
+    } else if (warp == 1) {
         if (lane == 0) {
-            const int h = warp - 1;
             MmaV v{&p, bar, sdesc(su32(sA)), sdesc(su32(sB)), tmem};
-            tcs::mma_issuer<SA>(p.plan, blockIdx.x, h, v);
-            // every MMA this thread issued completes before TMEM is released
-            mma_commit(bar.drain(h));
-            mbar_drain(bar.drain(h), 0);
+            tcs::mma_issuer<SA>(p.plan, blockIdx.x, v);
+            // every issued MMA completes before TMEM is released
+            mma_commit(bar.drain());
+            mbar_drain(bar.drain(), 0);
         }
     } else {
-        const int e = warp - 3;                 // epilogue warp 0..15
+        const int e = warp - 2;                 // epilogue warp 0..15
         const int h = e / 8, sub = (e / 4) % 2, lq = warp % 4;
         EpilogueV v;
         v.p = &p;

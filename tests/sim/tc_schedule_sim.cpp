@@ -1,7 +1,6 @@
 // CPU simulation of the tensor-core slice GEMM's schedule (tc_schedule.cuh):
-// the producer, the two MMA issuers (one per accumulator half) and the
-// epilogue roles of one CTA run as interleaved processes over simulated
-// mbarriers with the hardware's parity-wait rule.
+// the producer, MMA-issuer and epilogue roles of one CTA run as interleaved
+// processes over simulated mbarriers with the hardware's parity-wait rule.
 // Checks: every role runs to completion (no wait is left unsatisfied), no
 // wait could confuse two phases of a barrier, every MMA reads the A plane and
 // B half it expects, no slot is refilled before its uses are released, MMAs
@@ -70,7 +69,6 @@ struct Sim {
     std::vector<int> tiles_seen;
 
     Sim(tcs::Plan p, int c) : P(p), cta(c) {
-        for (int s = 0; s < tcs::kNAS; ++s) empty_a[s].count = 2;   // released by both issuers
         for (int h = 0; h < 2; ++h) {
             acc_empty[h].count = 8;
             acc_empty[h].on_complete = [this, h] {
@@ -146,7 +144,7 @@ struct MmaRec {
     }
     void release_a(int sa) {
         out.push_back({[] { return true; }, [this, sa] {
-                           if (S.a_uses[sa] < 1) fail("A slot released before its use");
+                           if (S.a_uses[sa] != 2) fail("A slot released early");
                            S.empty_a[sa].arrive();
                        }});
     }
@@ -227,23 +225,21 @@ int main(int argc, char** argv) {
     std::mt19937 rng(seed);
     for (int cta = 0; cta < std::min(P.grid, P.ntiles); ++cta) {
         Sim S(P, cta);
-        std::vector<std::vector<Step>> roles(19);
+        std::vector<std::vector<Step>> roles(18);
         ProdRec pr{S, roles[0]};
-        MmaRec mr0{S, roles[1]}, mr1{S, roles[2]};
+        MmaRec mr{S, roles[1]};
         if (P.SA == 8) {
             tcs::producer<8>(P, cta, pr);
-            tcs::mma_issuer<8>(P, cta, 0, mr0);
-            tcs::mma_issuer<8>(P, cta, 1, mr1);
+            tcs::mma_issuer<8>(P, cta, mr);
         } else if (P.SA == 1) {
             tcs::producer<1>(P, cta, pr);
-            tcs::mma_issuer<1>(P, cta, 0, mr0);
-            tcs::mma_issuer<1>(P, cta, 1, mr1);
+            tcs::mma_issuer<1>(P, cta, mr);
         } else {
             fail("SA must be 8 or 1");
         }
         std::vector<EpiRec> ep;
         ep.reserve(16);
-        for (int w = 0; w < 16; ++w) ep.push_back(EpiRec{S, roles[3 + w], w});
+        for (int w = 0; w < 16; ++w) ep.push_back(EpiRec{S, roles[2 + w], w});
         for (int w = 0; w < 16; ++w) tcs::epilogue(P, cta, w / 8, ep[w]);
         std::vector<size_t> pc(roles.size(), 0);
         while (true) {
