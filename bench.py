@@ -73,6 +73,32 @@ def mixed_roofline(fp64eq_tflops):
             "counting": "36 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
 
 
+# DRAM traffic of one trailing C -= Y.W2 launch (dgemm_kernel<0,0>, rows k.. of the
+# block), from an ncu capture of the 8192^2, b = 256 solve (one launch at
+# s = 2304: C 5888 x 5888, K = 256): dram__bytes_read.sum + dram__bytes_write.sum
+# = 302,608,896 + 220,156,160 bytes against 578.8 MB of operand bytes (C read and
+# written once, Y and W2 read once).  The traffic follows the operand bytes, so a
+# launch of another size is scaled by them.
+TRAILING_CAPTURE = {"rows": 5888, "cols": 5888, "k": 256, "dram_bytes": 302608896 + 220156160}
+
+
+def gemm_operand_bytes(rows, cols, k):
+    """C (rows x cols) read and written once, Y (rows x k) and W2 (k x cols) read once, FP64."""
+    return 8.0 * (2 * rows * cols + rows * k + k * cols)
+
+
+def trailing_traffic(m, n, b):
+    """DRAM bytes of the first block's C -= Y.W2 launch of an m x n solve with block b,
+    scaled from the capture by operand bytes."""
+    cap = TRAILING_CAPTURE
+    ratio = cap["dram_bytes"] / gemm_operand_bytes(cap["rows"], cap["cols"], cap["k"])
+    rows, cols = m - b, n - b
+    return {"bytes": ratio * gemm_operand_bytes(rows, cols, b), "launch": f"C -= Y.W2, C {rows}x{cols}, K={b}",
+            "dram_over_operand_bytes": ratio,
+            "how": ("scaled by operand bytes from one ncu capture of the 8192^2, b=256 solve "
+                    "(C 5888x5888, K=256: 522.8 MB of DRAM traffic against 578.8 MB of operand bytes)")}
+
+
 def canonical_flops(m, n):
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
 
@@ -937,7 +963,9 @@ def main():
         roofline = mixed_roofline(achieved)
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                    "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                    "traffic": trailing_traffic(a.m or a.n, a.n, a.b)["bytes"],
+                    "traffic_launch": trailing_traffic(a.m or a.n, a.n, a.b),
                     "kernel": "dgemm_kernel (FP64 SIMT GEMMs of the trailing block-reflector update)",
                     "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
                     "dfma_probe_tflops": probe}

@@ -16,8 +16,10 @@
 //   * the products of one group t = p + q are summed on the tensor cores in
 //     FP32.  Every partial sum is an integer of magnitude below
 //     8 * Kc * 127^2 < 2^24 for a K chunk Kc = 128, so FP32 holds it exactly;
-//     after each chunk the eight group sums are added exactly into two 64-bit
-//     integers (ozaki_tc.cu), which are rounded once to FP64 at the end.
+//     after each chunk the eight group sums are combined exactly, rounded to a
+//     multiple of 2^dsh (dsh = ceil(log2 K) + 1) and added into one 64-bit
+//     integer per element (ozaki_tc.cu), which is rounded once to FP64 at the
+//     end.
 // The result matches an FP64 GEMM to a few units of roundoff (normwise).  A
 // sketch with +-1 entries is exact in one slice, so S*A needs only the eight
 // products S A_q.

@@ -35,11 +35,12 @@
 //               32 (w % 4) ..; two warps share a lane quarter, 16 columns
 //               each).  After each chunk a warp reads the eight groups with
 //               tcgen05.ld, zeroes them with tcgen05.st, releases the half and
-//               adds the sums into two 64-bit integers per element, exactly:
-//                 HI += sum_{t <= 3} G_t 2^(7(3-t)),  LO += sum_{t >= 4} G_t 2^(7(7-t));
-//               after a tile's last chunk (the half is already released for the
-//               next tile) C = alpha (HI 2^28 + LO) 2^(ea+eb-63) + beta C, the
-//               128-bit integer rounded once to FP64 with integer operations.
+//               forms the chunk's exact value per element,
+//                 W = (sum_{t <= 3} G_t 2^(7(3-t))) 2^28 + sum_{t >= 4} G_t 2^(7(7-t)),
+//               rounded to a multiple of 2^dsh and added into one 64-bit
+//               integer; after a tile's last chunk (the half is already
+//               released for the next tile) C = alpha acc 2^(ea+eb-63+dsh) + beta C,
+//               the integer rounded once to FP64 with integer operations.
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error
 // flag, the roles stop issuing work, in-flight copies and MMAs are waited for
 // (bounded), TMEM is freed and the CTA returns.

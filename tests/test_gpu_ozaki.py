@@ -132,6 +132,31 @@ def test_sketch_tc_exact_on_integer_data(d, m, n):
     assert np.array_equal(np_(Msk), ref)
 
 
+def test_sketch_tc_more_tiles_than_sms():
+    """d = 320, n = 40000: 3 x 625 tiles, so every CTA of the persistent grid
+    runs several tiles; 64 sampled columns (the first, the last and the ragged
+    final tile among them) checked bit-exact on integer data."""
+    d, m, n = 320, 4096, 40000
+    rng = np.random.default_rng(7)
+    A = rng.integers(-40, 40, size=(m, n)).astype(np.float64)
+    Msk = np_(bq.binding.bqrrp_sketch_apply_tc(dev(A), d, 5))
+    cols = np.unique(np.concatenate([[0, 63, 64, n - 65, n - 1], rng.integers(0, n, 59)]))
+    ref = oracle.sketch_apply(oracle.sketch_operator(d, m, 5), A[:, cols])
+    assert np.array_equal(Msk[:, cols], ref)
+
+
+def test_ozaki_more_tiles_than_sms():
+    """M = N = 1500, K = 700: 12 x 24 tiles (a ragged last row and column
+    tile) over a grid of one CTA per SM, integer data, bit-exact."""
+    M, N, K = 1500, 1500, 700
+    rng = np.random.default_rng(11)
+    A = rng.integers(-(1 << 19), 1 << 19, size=(M, K)).astype(np.float64)
+    Bm = rng.integers(-(1 << 19), 1 << 19, size=(K, N)).astype(np.float64)
+    C = dev(np.zeros((M, N)))
+    bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
+    assert np.array_equal(np_(C), (A.astype(np.int64) @ Bm.astype(np.int64)).astype(np.float64))
+
+
 def test_sketch_tc_gaussian_within_fp64_bound():
     d, m, n = 160, 2000, 1000
     A = W.gaussian(m, n, 3)
