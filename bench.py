@@ -137,7 +137,7 @@ def parse():
     p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
     p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")
     p.add_argument("--panel", choices=["cholqr", "hqr"], default="cholqr")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+    p.add_argument("--precision", choices=["fp64", "mixed", "mixed_sketch32"], default="fp64",
                    help="mixed: sketch and trailing-update products on the bf16 tensor cores (exact slices)")
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--schedule", choices=["overlap", "serial"], default="overlap",
@@ -157,13 +157,15 @@ def parse():
     p.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 512], metavar=("M", "N", "K"))
     p.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                    help="batched: 4096 independent matrices (m log-uniform in [64, 1024], n log-uniform in "
-                        "[32, m], sigma_k = 10^(-8(k-1)/(n-1))), autotuned b and d, one CUDA graph per step")
+                        "[32, m], sigma_k = 10^(-8(k-1)/(n-1))), autotuned b, d and tile width, one CUDA graph per step")
     p.add_argument("--batch", type=int, default=4096)
     p.add_argument("--requests", type=int, default=200,
                    help="serving: requests per load level (a bounded sample of the 20000-request stream)")
     p.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.2])
     p.add_argument("--batch-b", type=int, default=0,
                    help="batched: fixed block size for every matrix instead of the autotuner (d = ceil(1.25 b))")
+    p.add_argument("--batch-tile", type=int, default=64, choices=[32, 64],
+                   help="batched, with --batch-b: trailing tile width (columns) of every matrix")
     a = p.parse_args()
     a.m = a.m or a.n
     a.d = a.d or int(math.ceil(1.25 * a.b))
@@ -173,7 +175,8 @@ def parse():
 def workload_name(a):
     fam = "iid N(0,1)" if a.family == "gaussian" else "U diag(sigma) V^T, sigma geometric 1..1e-12"
     sk = "dense Philox +-1" if a.sketch == "dense" else "sparse-sign (8 nnz/col)"
-    prec = "FP64" if a.precision == "fp64" else "mixed-precision (bf16 tensor-core slices, FP64 accuracy)"
+    prec = {"fp64": "FP64", "mixed": "mixed-precision (bf16 tensor-core slices, FP64 accuracy)",
+            "mixed_sketch32": "mixed-precision (bf16 tensor-core slices, FP64 accuracy; FP32 sketch QR)"}[a.precision]
     return f"{prec} BQRRP m={a.m} n={a.n} b={a.b} d={a.d}, {fam}, {sk} sketch, {a.panel} panel"
 
 
@@ -370,7 +373,7 @@ def time_own_qr(A, A0, precision, reps):
     from paper_2507_00976_b300 import binding as B
     m, n = A.shape
     tau = torch.empty(n, dtype=torch.float64, device="cuda")
-    if precision == "mixed":
+    if precision.startswith("mixed"):
         ws = torch.empty(B.bqrrp_geqrf_mixed_workspace(m, n), dtype=torch.uint8, device="cuda")
     else:
         ws = torch.empty(B.bqrrp_geqrf_workspace(m, n, 0), dtype=torch.uint8, device="cuda")
@@ -381,7 +384,7 @@ def time_own_qr(A, A0, precision, reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if precision == "mixed":
+        if precision.startswith("mixed"):
             B.bqrrp_geqrf_mixed(A, tau=tau, workspace=ws)
         else:
             B.bqrrp_geqrf(A, 0, tau=tau, workspace=ws)
@@ -512,11 +515,12 @@ def run_batched(a, world, rank, local):
     if a.batch_b > 0:
         b = np.full(a.batch, a.batch_b, dtype=np.int64)
         d = np.full(a.batch, int(math.ceil(1.25 * a.batch_b)), dtype=np.int64)
+        tiles = np.full(a.batch, a.batch_tile, dtype=np.int64)
         tuned_ms = None
     else:
-        b, d, tuned_ms = B.bqrrp_batch_autotune(m, n, seeds, A0, tol)
+        b, d, tiles, tuned_ms = B.bqrrp_batch_autotune_tiles(m, n, seeds, A0, tol)
     t_tune = time.perf_counter() - t_tune
-    plan = B.BatchPlan(m, n, b, d, seeds, tol)
+    plan = B.BatchPlan(m, n, b, d, seeds, tol, tiles=tiles)
     A = torch.empty_like(A0)
     jpvt = torch.empty(tot_j, dtype=torch.int64, device="cuda")
     tau = torch.empty(tot_j, dtype=torch.float64, device="cuda")
@@ -623,7 +627,8 @@ def run_batched(a, world, rank, local):
         sel = (n >= lo) & (n < hi)
         if sel.any():
             classes[f"n in [{lo},{hi})"] = {"count": int(sel.sum()), "b": sorted(set(b[sel].tolist())),
-                                           "d": sorted(set(d[sel].tolist()))}
+                                           "d": sorted(set(d[sel].tolist())),
+                                           "tile_cols": sorted(set(tiles[sel].tolist()))}
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
         "warmup": max(3, a.warmup), "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -634,7 +639,8 @@ def run_batched(a, world, rank, local):
                                f"step", "batch": a.batch, "trunc_tol": tol, "seed": a.seed,
                    "total_canonical_gflop": flops / 1e9, "matrix_bytes": A0.numel() * 8,
                    "l2": f"inputs larger than L2 (the batch is {A0.numel() * 8 / 1e9:.2f} GB, L2 126 MB)",
-                   "block_sizes": "fixed" if a.batch_b > 0 else "autotuned", "classes": classes,
+                   "block_sizes": "fixed" if a.batch_b > 0 else "autotuned (b, d and trailing tile width)",
+                   "classes": classes,
                    "autotune_s": t_tune, "autotune_best_ms": tuned_ms,
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": statistics.median(lat), "p99": p99, "best": lat[0]},
@@ -721,6 +727,8 @@ def run_serving(a, world, rank, local):
     # warm-up: one of each shape
     run([(k, 0) for k in range(len(SERVING_SHAPES))], [0.0] * len(SERVING_SHAPES))
     l0 = B.bqrrp_launch_counter()
+    sampler = ClockSampler(local)
+    sampler.start()
     # capacity: the sample offered all at once
     base_stream = draw(a.requests, rng)
     done, sub = run(base_stream, [0.0] * len(base_stream))
@@ -751,6 +759,7 @@ def run_serving(a, world, rank, local):
                             "p99_ms": float(np.percentile(lat, 99)),
                             "status_nonzero": int(sum(1 for c in done if c["status"] != 0)),
                             "per_shape": per_shape}
+    clocks = sampler.stop()
     st = S.stats()
     launches = B.bqrrp_launch_counter() - l0
     S.close()
@@ -766,8 +775,10 @@ def run_serving(a, world, rank, local):
                                "1024x512 / 4096x2048 / 8192x4096 with weights 0.5/0.3/0.15/0.05, spectra geometric "
                                "from 1 to a decay uniform in exponent on [1e-14, 1e-4], truncation 1e-8, admission by "
                                "a 120 GB HBM budget, continuous batching of the small shapes",
-                   "requests_per_load": len(base_stream), "sample": f"{len(base_stream)} requests per load level "
-                   f"(a bounded sample of the 20000-request stream)", "hbm_budget_bytes": budget,
+                   "requests_per_load": len(base_stream),
+                   "sample": (f"{len(base_stream)} requests per load level" +
+                              (" (the configured 20000-request stream)" if len(base_stream) >= 20000 else
+                               " (a bounded sample of the 20000-request stream)")), "hbm_budget_bytes": budget,
                    "block_sizes": {f"{m}x{n}": [b, d] for m, n, b, d in SERVING_SHAPES},
                    "capacity_req_per_s": capacity, "mean_gflop_per_request": flops_per_req / 1e9,
                    "parallelism": "single"},
@@ -775,7 +786,7 @@ def run_serving(a, world, rank, local):
         "loads": loads, "server": st, "e2e": {"value": hi["gflops"], "unit": "GFLOP/s",
                                              "note": "every request is copied host->device at admission and its "
                                                      "R, reflectors, jpvt and tau device->host at completion"},
-        "gpu_launches": launches, "roofline": None, "cpu_baseline": None,
+        "gpu_launches": launches, "roofline": None, "cpu_baseline": None, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -829,7 +840,7 @@ def main():
     tau = torch.empty(n, dtype=torch.float64, device="cuda")
     opts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
                        B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR,
-                       B.PRECISION_FP64 if a.precision == "fp64" else B.PRECISION_MIXED,
+                       B._PRECISIONS[a.precision],
                        B.SCHEDULE_OVERLAP if a.schedule == "overlap" else B.SCHEDULE_SERIAL)
     ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -891,28 +902,43 @@ def main():
         del ws
         torch.cuda.empty_cache()
         ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, mopts), dtype=torch.uint8, device="cuda")
-        mms = []
-        B.bqrrp_profile_reset()
-        for i in range(3):
-            B.bqrrp_profile_enable(i > 0)
-            A.copy_(A0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            mrank = B.bqrrp_factor(A, b, d, 1, jpvt, tau, opts=mopts, workspace=ws)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if i > 0:
-                mms.append(e0.elapsed_time(e1))
-        B.bqrrp_profile_enable(False)
-        mprof = B.bqrrp_profile_read()
+        def time_mixed(opts_):
+            """Two timed solves after one warm-up, with the phase profile."""
+            ms_, rank_ = [], None
+            B.bqrrp_profile_reset()
+            for i in range(3):
+                B.bqrrp_profile_enable(i > 0)
+                A.copy_(A0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rank_ = B.bqrrp_factor(A, b, d, 1, jpvt, tau, opts=opts_, workspace=ws)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i > 0:
+                    ms_.append(e0.elapsed_time(e1))
+            B.bqrrp_profile_enable(False)
+            prof_ = B.bqrrp_profile_read()
+            return ms_, rank_, prof_
+
+        mms, mrank, mprof = time_mixed(mopts)
         mtr_ms, mtr_fl = mprof["trailing"]
         mgf = flops / (statistics.mean(mms) * 1e-3) / 1e9
         mtf = mtr_fl / (mtr_ms * 1e-3) / 1e12 if mtr_ms > 0 else None
+        mcalls = max(1, mprof["calls"])
         mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
                  "arith": "FP64-accurate products on bf16 tensor cores (8 exact 7-bit slices, 36 pair products); "
-                          "LU, sketch QR, panel, tau, R in FP64"}
+                          "LU, sketch QR, panel, tau, R in FP64",
+                 "phases_ms": {p_: mprof[p_][0] / mcalls for p_ in B.PHASES}}
+        # the variant with the sketch's QR factor in FP32 (pivots from the FP64 LU)
+        s32 = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
+                          B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR, B.PRECISION_MIXED_SKETCH32)
+        sms, srank, sprof = time_mixed(s32)
+        scalls = max(1, sprof["calls"])
+        mixed["sketch32"] = {"gflops": flops / (statistics.mean(sms) * 1e-3) / 1e9, "ms_mean": statistics.mean(sms),
+                             "rank": srank, "phases_ms": {p_: sprof[p_][0] / scalls for p_ in B.PHASES},
+                             "arith": "as above, with the QR that forms R^sk from the sketch's LU factor in FP32"}
         if not a.skip_qr:
             mq = time_own_qr(A, A0, "mixed", 3)[1:]   # one warm-up run, two timed
             mixed["own_qr_gflops"] = flops / (statistics.mean(mq) * 1e-3) / 1e9
@@ -959,7 +985,7 @@ def main():
         phases[name] = {"ms_per_step": ms / max(1, prof["calls"]),
                         "share": ms / max(1e-9, sum(prof[p][0] for p in B.PHASES)),
                         "tflops": (fl / (ms * 1e-3) / 1e12) if ms > 0 and fl > 0 else None}
-    if a.precision == "mixed":
+    if a.precision.startswith("mixed"):
         roofline = mixed_roofline(achieved)
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -50,9 +50,16 @@ extern "C" {
 /* Arithmetic of the dense products (sketch S*A and the trailing update). */
 #define BQRRP_PRECISION_FP64 0   /* FP64 SIMT throughout                            */
 #define BQRRP_PRECISION_MIXED 1  /* sketch and trailing-update products on the bf16
-                                    tensor cores through exact 6-bit slices (see
+                                    tensor cores through exact 7-bit slices (see
                                     bqrrp_dgemm_ozaki); LU, sketch QR, panel, tau, R
                                     in FP64                                          */
+#define BQRRP_PRECISION_MIXED_SKETCH32 2 /* as _MIXED, and the QR that forms R^sk
+                                    from the sketch's LU factor (Alg. 2) in FP32
+                                    arithmetic: the pivots still come from the FP64
+                                    LU; R^sk, which preconditions the panel and
+                                    becomes the next sketch, is accurate to FP32
+                                    relative to the current block's sketch; the
+                                    panel, tau and R stay FP64                      */
 
 /* Order of the steps of consecutive blocks (the results are the same bit for bit). */
 #define BQRRP_SCHEDULE_OVERLAP 0 /* the sketch update and Alg. 2 of block i+1 run on a
@@ -66,7 +73,7 @@ typedef struct bqrrp_opts {
     int sketch_kind;     /* BQRRP_SKETCH_DENSE (default) or BQRRP_SKETCH_SPARSE */
     int64_t sketch_nnz;  /* nonzeros per column of a sparse sketch (default 8)  */
     int panel_kind;      /* BQRRP_PANEL_CHOLQR (default) or BQRRP_PANEL_HQR    */
-    int64_t precision;   /* BQRRP_PRECISION_FP64 (default) or _MIXED            */
+    int64_t precision;   /* BQRRP_PRECISION_FP64 (default), _MIXED or _MIXED_SKETCH32 */
     int64_t schedule;    /* BQRRP_SCHEDULE_OVERLAP (default) or _SERIAL         */
     int64_t reserved[3]; /* must be zero                                        */
 } bqrrp_opts;
@@ -364,6 +371,18 @@ typedef struct bqrrp_batch_plan_s* bqrrp_batch_plan;
 int bqrrp_batch_plan_create(bqrrp_batch_plan* plan, int64_t batch, const int64_t* m, const int64_t* n,
                             const int64_t* b, const int64_t* d, const uint64_t* seed, double trunc_tol);
 
+/* The same with a tile shape per matrix: tile_cols[i] (HOST, 32 or 64) is the
+ * column width of matrix i's trailing-update and sketch-update tiles (one
+ * work item each); bqrrp_batch_plan_create uses 64.  Narrow tiles waste fewer
+ * threads on narrow trailing blocks and give a matrix's update more parallel
+ * items; wide tiles reread Y fewer times.  The arithmetic of a tile differs
+ * only in the order of the partial sums of W = Y^T C, so results agree with
+ * the 64-column form to rounding, not bit for bit.  Errors as
+ * bqrrp_batch_plan_create, and -10 for a tile width other than 32 or 64. */
+int bqrrp_batch_plan_create_tiles(bqrrp_batch_plan* plan, int64_t batch, const int64_t* m, const int64_t* n,
+                                  const int64_t* b, const int64_t* d, const int64_t* tile_cols, const uint64_t* seed,
+                                  double trunc_tol);
+
 /* Device workspace bytes the plan needs (256-byte aligned workspace). */
 size_t bqrrp_batch_workspace_bytes(bqrrp_batch_plan plan);
 
@@ -419,6 +438,16 @@ size_t bqrrp_batch_autotune_workspace_bytes(int64_t batch, const int64_t* m, con
 int bqrrp_batch_autotune(int64_t batch, const int64_t* m, const int64_t* n, const uint64_t* seed, const double* A,
                          double trunc_tol, void* workspace, size_t workspace_bytes, void* stream, int64_t* b_out,
                          int64_t* d_out, double* best_ms);
+
+/* The autotuner with tile shapes: after each size class's b, the class's
+ * trailing tile width (32 or 64 columns) is chosen by timing the class alone
+ * with that b; gamma is then chosen over the whole batch with those tiles.
+ * tile_out (HOST, `batch` entries) receives the widths, for
+ * bqrrp_batch_plan_create_tiles.  Same workspace, arguments and errors as
+ * bqrrp_batch_autotune, and -12 for a null tile_out. */
+int bqrrp_batch_autotune_tiles(int64_t batch, const int64_t* m, const int64_t* n, const uint64_t* seed,
+                               const double* A, double trunc_tol, void* workspace, size_t workspace_bytes,
+                               void* stream, int64_t* b_out, int64_t* d_out, int64_t* tile_out, double* best_ms);
 
 /* ------------------------------------------------------------------------
  * Request loop (serving layer; the paper factors one matrix per call).

@@ -24,7 +24,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "bqrrp.h")
 OK, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 SKETCH_DENSE, SKETCH_SPARSE = 0, 1
 PANEL_CHOLQR, PANEL_HQR = 0, 1
-PRECISION_FP64, PRECISION_MIXED = 0, 1
+PRECISION_FP64, PRECISION_MIXED, PRECISION_MIXED_SKETCH32 = 0, 1, 2
+_PRECISIONS = {"fp64": PRECISION_FP64, "mixed": PRECISION_MIXED, "mixed_sketch32": PRECISION_MIXED_SKETCH32}
 SCHEDULE_OVERLAP, SCHEDULE_SERIAL = 0, 1
 BATCH_PERSISTENT, BATCH_LOCKSTEP = 0, 1
 
@@ -109,6 +110,7 @@ _SIGS = {
     "bqrrp_sketch_apply_tc": ([_i64, _i64, _i64, _vp, _i64, _u64, _vp, _i64, _vp, _sz, _vp], ctypes.c_int),
     "bqrrp_sketch_apply_tc_workspace": ([_i64, _i64, _i64], _sz),
     "bqrrp_batch_plan_create": ([ctypes.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _d], ctypes.c_int),
+    "bqrrp_batch_plan_create_tiles": ([ctypes.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _d], ctypes.c_int),
     "bqrrp_batch_workspace_bytes": ([_vp], _sz),
     "bqrrp_batch_factor": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_int], ctypes.c_int),
     "bqrrp_batch_plan_destroy": ([_vp], None),
@@ -116,6 +118,8 @@ _SIGS = {
     "bqrrp_batch_plan_set_form": ([_vp, ctypes.c_int], ctypes.c_int),
     "bqrrp_batch_flops": ([_vp, ctypes.c_int], _d),
     "bqrrp_batch_autotune_workspace_bytes": ([_i64, _vp, _vp], _sz),
+    "bqrrp_batch_autotune_tiles": ([_i64, _vp, _vp, _vp, _vp, _d, _vp, _sz, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)],
+                                   ctypes.c_int),
     "bqrrp_batch_autotune": ([_i64, _vp, _vp, _vp, _vp, _d, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(_d)],
                              ctypes.c_int),
     "bqrrp_server_create": ([ctypes.POINTER(_vp), _sz, _sz, _d, _i64, ctypes.c_int, _d], ctypes.c_int),
@@ -449,7 +453,8 @@ def bqrrp_launch_counter():
 def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64", schedule="overlap",
            stream=None):
     """Factor a copy of A (any 2-D float64 tensor/array); returns
-    (F column-major with R and reflectors, jpvt, tau, rank) as device tensors."""
+    (F column-major with R and reflectors, jpvt, tau, rank) as device tensors.
+    precision: "fp64", "mixed" or "mixed_sketch32"."""
     torch = _torch()
     F = to_colmajor(A)
     m, n = F.shape
@@ -457,7 +462,7 @@ def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64
     tau = torch.empty(max(n, 1), dtype=torch.float64, device=F.device)
     opts = make_opts(SKETCH_DENSE if sketch == "dense" else SKETCH_SPARSE, nnz,
                      PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR,
-                     PRECISION_FP64 if precision == "fp64" else PRECISION_MIXED,
+                     _PRECISIONS[precision],
                      SCHEDULE_OVERLAP if schedule == "overlap" else SCHEDULE_SERIAL)
     rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
     return F, jpvt[:n], tau[:n], rank
@@ -480,17 +485,25 @@ def _np_ptr(a):
 
 class BatchPlan:
     """Owner of a ``bqrrp_batch_plan`` handle (host arrays m, n, b, d, seed;
-    the packed layout of ``workloads.batch_offsets``)."""
+    the packed layout of ``workloads.batch_offsets``).  tiles: optional host
+    array of trailing tile widths (32 or 64) per matrix."""
 
-    def __init__(self, m, n, b, d, seeds, trunc_tol=1e-8):
+    def __init__(self, m, n, b, d, seeds, trunc_tol=1e-8, tiles=None):
         self.m, self.n, self.b, self.d = _host_i64(m), _host_i64(n), _host_i64(b), _host_i64(d)
         self.seeds = _host_u64(seeds)
         self.batch = len(self.m)
         self.trunc_tol = float(trunc_tol)
         h = _vp()
-        rc = lib().bqrrp_batch_plan_create(ctypes.byref(h), self.batch, _np_ptr(self.m), _np_ptr(self.n),
-                                           _np_ptr(self.b), _np_ptr(self.d), _np_ptr(self.seeds), self.trunc_tol)
-        _check("bqrrp_batch_plan_create", rc)
+        if tiles is None:
+            rc = lib().bqrrp_batch_plan_create(ctypes.byref(h), self.batch, _np_ptr(self.m), _np_ptr(self.n),
+                                               _np_ptr(self.b), _np_ptr(self.d), _np_ptr(self.seeds), self.trunc_tol)
+            _check("bqrrp_batch_plan_create", rc)
+        else:
+            self.tiles = _host_i64(tiles)
+            rc = lib().bqrrp_batch_plan_create_tiles(ctypes.byref(h), self.batch, _np_ptr(self.m), _np_ptr(self.n),
+                                                     _np_ptr(self.b), _np_ptr(self.d), _np_ptr(self.tiles),
+                                                     _np_ptr(self.seeds), self.trunc_tol)
+            _check("bqrrp_batch_plan_create_tiles", rc)
         self.handle = h
         self.workspace = None
 
@@ -549,8 +562,28 @@ def bqrrp_batch_autotune(m, n, seeds, A, trunc_tol=1e-8, stream=None):
     return b, d, best.value
 
 
+def bqrrp_batch_autotune_tiles(m, n, seeds, A, trunc_tol=1e-8, stream=None):
+    """Pick b, d and the trailing tile width per matrix by timing on the device
+    (A packed, read only).  Returns (b, d, tiles, best_ms), numpy int64 arrays."""
+    import numpy as np
+    m, n, sd = _host_i64(m), _host_i64(n), _host_u64(seeds)
+    batch = len(m)
+    nbytes = int(lib().bqrrp_batch_autotune_workspace_bytes(batch, _np_ptr(m), _np_ptr(n)))
+    ws = _workspace(nbytes, A.device)
+    b = np.zeros(batch, dtype=np.int64)
+    d = np.zeros(batch, dtype=np.int64)
+    t = np.zeros(batch, dtype=np.int64)
+    best = _d(0.0)
+    rc = lib().bqrrp_batch_autotune_tiles(batch, _np_ptr(m), _np_ptr(n), _np_ptr(sd), _ptr(A), float(trunc_tol),
+                                          _ptr(ws), ws.numel(), _stream(stream), _np_ptr(b), _np_ptr(d), _np_ptr(t),
+                                          ctypes.byref(best))
+    _check("bqrrp_batch_autotune_tiles", rc)
+    del ws
+    return b, d, t, best.value
+
+
 def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False, stream=None,
-                   form=BATCH_PERSISTENT):
+                   form=BATCH_PERSISTENT, tiles=None):
     """Factor a copy of a packed batch.  Returns (F packed, jpvt, tau, rank,
     trunc_rank, info) as device tensors."""
     torch = _torch()
@@ -563,7 +596,7 @@ def factor_batched(A_packed, m, n, b, d, seeds, trunc_tol=1e-8, use_graph=False,
     rank = torch.empty(max(nb, 1), dtype=torch.int64, device=F.device)
     trunc = torch.empty(max(nb, 1), dtype=torch.int64, device=F.device)
     info = torch.empty(max(nb, 1), dtype=torch.int32, device=F.device)
-    plan = BatchPlan(m, n, b, d, seeds, trunc_tol)
+    plan = BatchPlan(m, n, b, d, seeds, trunc_tol, tiles=tiles)
     try:
         plan.set_form(form)
         plan.factor(F, jpvt, tau, rank, trunc, info, use_graph=use_graph, stream=stream)

@@ -50,7 +50,8 @@ constexpr int NW = BT / 32;      // warps per CTA
 constexpr int kMaxD = 256;       // largest sketch size d
 constexpr int kMaxB = 128;       // largest block size b
 constexpr int kMaxN = 4096;      // largest column count n
-constexpr int CT = 64;           // columns per tile (sketch, trailing, sketch update)
+constexpr int CT = 64;           // columns per tile (sketch); the widest trailing tile
+constexpr int CT_MIN = 32;       // the narrowest trailing tile (a plan chooses 32 or 64 per matrix)
 constexpr int SK_RK = 32;        // rows of A per sketch chunk
 constexpr int RCH = 32;          // rows per permutation chunk
 constexpr int RG = 32;           // rows per Gram chunk
@@ -59,6 +60,7 @@ constexpr int RT = 32;           // rows per trailing-update chunk
 // ------------------------------------------------------------------ plan records
 struct BatMat {                  // per matrix, written by the host, read-only on the device
     i64 m, n, b, d;
+    i64 ct;                      // columns per trailing-update / sketch-update tile: 32 or 64
     i64 offA;                    // element offset of A (column-major, lda = m)
     i64 offJ;                    // element offset of jpvt
     i64 offT;                    // element offset of tau
@@ -940,18 +942,64 @@ __global__ void __launch_bounds__(BT, 1) bat_panel_kernel(BatArgs a, Slot sl, in
 }
 
 // ------------------------------------------------------------------ trailing update
-// Item = (matrix, 64-column tile of A(:, c:)).  W = Y^T C (k x 64), then
-// C(0:keep, :) -= V(0:keep, :) W with V = Y T^T from the panel; keep = rows
-// when k = w, else k.  Shared memory: Yc (RT2 x kb, [row][col]) holds Y chunks
-// of RT rows, then V chunks of RT2 rows; Cc (RT x CT); Ws (kb x CT, [i][j]).
-// Register blocking, 4 x 4 outputs per thread and block:
-//  - W: the ceil(k/4) x 16 blocks are spread over the threads; when there are
-//    fewer blocks than threads, G = 256 / blocks groups split the rows of each
-//    chunk (group g takes rows g, g + G, ...) and their partial sums are added
-//    in group order (deterministic); with more blocks, a thread takes two;
-//  - update: thread (rb, jb) = (tid / 16, tid % 16) owns rows 4 rb .. 4 rb + 3
-//    of an RT2-row chunk and columns 4 jb .. 4 jb + 3.
+// Item = (matrix, ct-column tile of A(:, c:)), ct = 32 or 64 per matrix (the
+// plan's tile shape).  W = Y^T C (k x ct), then C(0:keep, :) -= V(0:keep, :) W
+// with V = Y T^T from the panel; keep = rows when k = w, else k.  Shared
+// memory: Yc (RT2 x kb, [row][col]) holds Y chunks of RT rows, then V chunks of
+// RT2 rows; Cc (RT x CT); Ws (kb x CT, [i][j]) (row stride CT for either ct).
+// Register blocking:
+//  - W: 4 x 4 blocks; the ceil(k/4) x (ct/4) blocks are spread over the
+//    threads; when there are fewer blocks than threads, G = 256 / blocks groups
+//    split the rows of each chunk (group g takes rows g, g + G, ...) and their
+//    partial sums are added in group order (deterministic); with more blocks, a
+//    thread takes two;
+//  - update: JB = ct/4 column blocks of 4; thread (rb, jb) = (tid / JB, tid % JB)
+//    owns RU = JB / 4 rows (4 for ct = 64, 2 for ct = 32) of an RT2-row chunk
+//    and columns 4 jb .. 4 jb + 3.
 constexpr int RT2 = 64;
+
+// C(r0 .. r0 + nr, 0 .. nc) -= Vc W for one RT2-row chunk (Vc in Yc).
+template <int JB>
+__device__ __forceinline__ void trail_update_chunk(const double* Yc, const double* Ws, double* C, i64 m, i64 r0,
+                                                   int nr, int nc, int k, int kb) {
+    constexpr int RU = RT2 * JB / BT;   // rows per thread: 4 (JB = 16) or 2 (JB = 8)
+    static_assert(RU * (BT / JB) == RT2, "the threads cover the chunk's rows");
+    const int rb = threadIdx.x / JB, jb = threadIdx.x % JB;
+    // this thread's block of C, loaded before the k loop so that the
+    // global-load latency overlaps the FMAs
+    double cpre[RU][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int col = 4 * jb + v;
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+            cpre[u][v] = (col < nc && RU * rb + u < nr) ? C[(r0 + RU * rb + u) + (i64)col * m] : 0.0;
+    }
+    double u4[RU][4];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) u4[u][v] = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double vv[RU], wv[4];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) vv[u] = Yc[(RU * rb + u) * kb + i];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) wv[v] = Ws[i * CT + 4 * jb + v];
+#pragma unroll
+        for (int u = 0; u < RU; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) u4[u][v] = fma(vv[u], wv[v], u4[u][v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int col = 4 * jb + v;
+        if (col < nc)
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                if (RU * rb + u < nr) C[(r0 + RU * rb + u) + (i64)col * m] = cpre[u][v] - u4[u][v];
+    }
+}
 
 __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, int iter, int kb) {
     extern __shared__ double sm[];
@@ -967,15 +1015,17 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
         const i64 c = min(n, s + b), w = c - s, rows = m - s;
         const int k = (int)S->k;
         const i64 keep = (k == w) ? rows : k;
-        const i64 j0 = c + (i64)sub * CT;
-        const int nc = (int)min((i64)CT, n - j0);
+        const int ct = (int)M.ct;
+        const i64 j0 = c + (i64)sub * ct;
+        const int nc = (int)min((i64)ct, n - j0);
         if (nc <= 0) return;
         const double* Y = a.wsd + M.offY;
         const double* V = a.wsd + M.offV;
         double* C = a.A + M.offA + s + j0 * m;
 
         // ---- W = Y^T C
-        const int nblk = ((k + 3) / 4) * 16;
+        const int jbs = ct / 4;   // column blocks of the tile
+        const int nblk = ((k + 3) / 4) * jbs;
         const int G = (nblk >= BT) ? 1 : BT / nblk;
         const int g = (G == 1) ? 0 : (int)threadIdx.x / nblk;
         int bi[2], bj[2];
@@ -983,8 +1033,8 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
         for (int q = 0; q < 2; ++q) {
             const int blk = (G == 1) ? (int)threadIdx.x + q * BT : (int)threadIdx.x % nblk;
             const bool on = (q == 0 || G == 1) && g < G && blk < nblk && (G == 1 || q == 0);
-            bi[q] = on ? 4 * (blk / 16) : -1;
-            bj[q] = on ? 4 * (blk % 16) : -1;
+            bi[q] = on ? 4 * (blk / jbs) : -1;
+            bj[q] = on ? 4 * (blk % jbs) : -1;
         }
         double acc[2][4][4];
 #pragma unroll
@@ -1000,7 +1050,7 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
                 const int rr = e % RT, i = e / RT;
                 Yc[rr * kb + i] = (rr < nr && i < k) ? Y[(r0 + rr) + (i64)i * m] : 0.0;
             }
-            for (int e = threadIdx.x; e < RT * CT; e += BT) {
+            for (int e = threadIdx.x; e < RT * ct; e += BT) {
                 const int rr = e % RT, j = e / RT;
                 Cc[rr * CT + j] = (rr < nr && j < nc) ? C[(r0 + rr) + (i64)j * m] : 0.0;
             }
@@ -1042,7 +1092,6 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
             __syncthreads();
         }
         // ---- C(0:keep, :) -= V(0:keep, :) W
-        const int rb = threadIdx.x / 16, jb = threadIdx.x % 16;
         for (i64 r0 = 0; r0 < keep; r0 += RT2) {
             const int nr = (int)min((i64)RT2, keep - r0);
             __syncthreads();
@@ -1051,40 +1100,10 @@ __device__ void body_trailing(const BatArgs& a, const int mat, const int sub, in
                 Yc[rr * kb + i] = (rr < nr && i < k) ? V[(r0 + rr) + (i64)i * m] : 0.0;
             }
             __syncthreads();
-            // this thread's 4 x 4 block of C, loaded before the k loop so that the
-            // global-load latency overlaps the FMAs
-            double cpre[4][4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int col = 4 * jb + v;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    cpre[u][v] = (col < nc && 4 * rb + u < nr) ? C[(r0 + 4 * rb + u) + (i64)col * m] : 0.0;
-            }
-            double u4[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) u4[u][v] = 0.0;
-            for (int i = 0; i < k; ++i) {
-                double vv[4], wv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) vv[u] = Yc[(4 * rb + u) * kb + i];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) wv[v] = Ws[i * CT + 4 * jb + v];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) u4[u][v] = fma(vv[u], wv[v], u4[u][v]);
-            }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int col = 4 * jb + v;
-                if (col < nc)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (4 * rb + u < nr) C[(r0 + 4 * rb + u) + (i64)col * m] = cpre[u][v] - u4[u][v];
-            }
+            if (ct == CT)
+                trail_update_chunk<CT / 4>(Yc, Ws, C, m, r0, nr, nc, k, kb);
+            else
+                trail_update_chunk<CT_MIN / 4>(Yc, Ws, C, m, r0, nr, nc, k, kb);
         }
     }
 }
@@ -1098,7 +1117,7 @@ __global__ void __launch_bounds__(BT) bat_trailing_kernel(BatArgs a, Slot sl, in
 }
 
 // ------------------------------------------------------------------ sketch update (Duersch-Gu)
-// Item = (matrix, 64-column tile of Msk(:, c:)).
+// Item = (matrix, ct-column tile of Msk(:, c:)), the trailing update's tiles.
 __device__ void body_skupdate(const BatArgs& a, const int mat, const int sub, int iter) {
         {
         const BatState* S = a.st + mat;
@@ -1107,8 +1126,8 @@ __device__ void body_skupdate(const BatArgs& a, const int mat, const int sub, in
         const i64 m = M.m, n = M.n, b = M.b, d = M.d;
         const i64 s = (i64)iter * b;
         const i64 c = min(n, s + b), w = c - s;
-        const i64 j0 = c + (i64)sub * CT;
-        const int nc = (int)min((i64)CT, n - j0);
+        const i64 j0 = c + (i64)sub * M.ct;
+        const int nc = (int)min(M.ct, n - j0);
         if (nc <= 0) return;
         const double* Wk = a.wsd + M.offW;
         const double* Zb = a.wsd + M.offSm + 2 * b * b;
@@ -1259,7 +1278,7 @@ __device__ void task_done(const BatArgs& a, const MegaArgs& q, int mat, int type
         case T_PANEL:
             if (S->upd_iter == iter) {
                 const i64 c = min(M.n, (i64)iter * M.b + M.b);
-                const int nt = (int)dcdiv(M.n - c, CT);
+                const int nt = (int)dcdiv(M.n - c, M.ct);
                 if (nt > 0) { ntype = T_TRAIL; count = nt; }
             }
             break;
@@ -1516,7 +1535,7 @@ double launch_flops(BatchPlan::Kind kind, const BatMat& M, i64 it) {
 // jpvt and tau (all three may be null: the packed layout).
 int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
                          const uint64_t* seed, double tol, const i64* offA_in, const i64* offJ_in,
-                         const i64* offT_in) {
+                         const i64* offT_in, const i64* ct_in) {
     if (!out) { set_error("plan pointer is null"); return -1; }
     *out = nullptr;
     if (batch < 0) { set_error("batch < 0"); return -2; }
@@ -1528,6 +1547,10 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
         if (m[i] > (i64)1 << 24) { set_error("matrix %lld: m > 2^24", (long long)i); return BQRRP_EUNSUPPORTED; }
         if (b[i] < 1 || b[i] > kMaxB) { set_error("matrix %lld: b outside [1, %d]", (long long)i, kMaxB); return -5; }
         if (d[i] < b[i] || d[i] > kMaxD) { set_error("matrix %lld: d outside [b, %d]", (long long)i, kMaxD); return -6; }
+        if (ct_in && ct_in[i] != CT && ct_in[i] != CT_MIN) {
+            set_error("matrix %lld: tile columns must be %d or %d", (long long)i, CT_MIN, CT);
+            return -10;
+        }
     }
     Device dev;
     BQ_TRY(current_device(&dev));
@@ -1551,6 +1574,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
         M.n = n[i];
         M.b = b[i];
         M.d = d[i];
+        M.ct = ct_in ? ct_in[i] : CT;
         M.seed = seed[i];
         M.offA = offA_in ? offA_in[i] : offA;
         M.offJ = offJ_in ? offJ_in[i] : offJ;
@@ -1587,7 +1611,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
                 t += (unsigned long long)cdiv(M.n, CT);         // SKETCH tiles
                 for (i64 it = 0; it * M.b < M.n; ++it) {
                     const i64 c = std::min(M.n, it * M.b + M.b);
-                    t += 2 + (unsigned long long)cdiv(M.n - c, CT);     // QRCP, PANEL, TRAIL tiles
+                    t += 2 + (unsigned long long)cdiv(M.n - c, M.ct);   // QRCP, PANEL, TRAIL tiles
                 }
             }
             tasks[i] = t;
@@ -1644,7 +1668,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
               [it](const BatMat& M) { return cost_panel(M, it * M.b); });
         auto ntail = [it](const BatMat& M) {
             const i64 c = std::min(M.n, it * M.b + M.b);
-            return (M.n > 0 && it * M.b < M.n) ? (int)cdiv(M.n - c, CT) : 0;
+            return (M.n > 0 && it * M.b < M.n) ? (int)cdiv(M.n - c, M.ct) : 0;
         };
         build(BatchPlan::K_TRAIL, (int)it, ntail,
               [it](const BatMat& M) { return (double)(M.m - it * M.b) * (double)M.b; });
@@ -1726,7 +1750,7 @@ int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n,
 
 int batch_plan_create(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
                       const uint64_t* seed, double tol) {
-    return batch_plan_create_ex(out, batch, m, n, b, d, seed, tol, nullptr, nullptr, nullptr);
+    return batch_plan_create_ex(out, batch, m, n, b, d, seed, tol, nullptr, nullptr, nullptr, nullptr);
 }
 
 size_t batch_plan_bytes(const BatchPlan* P) { return P ? P->total : 0; }
@@ -1976,12 +2000,14 @@ struct TuneBuffers {
 };
 
 // Time one batched factorization of the matrices `idx` (copied from the
-// packed source) with block sizes bsel/dsel; returns milliseconds or < 0.
+// packed source) with block sizes bsel/dsel and trailing tile widths csel;
+// returns milliseconds or < 0.
 double time_subbatch(const std::vector<int>& idx, const i64* m, const i64* n, const uint64_t* seed,
                      const double* Asrc, const std::vector<i64>& offsrc, const std::vector<i64>& bsel,
-                     const std::vector<i64>& dsel, double tol, const TuneBuffers& tb, cudaStream_t st) {
+                     const std::vector<i64>& dsel, const std::vector<i64>& csel, double tol, const TuneBuffers& tb,
+                     cudaStream_t st) {
     const i64 cnt = (i64)idx.size();
-    std::vector<i64> mm(cnt), nn(cnt), bb(cnt), dd(cnt);
+    std::vector<i64> mm(cnt), nn(cnt), bb(cnt), dd(cnt), cc(cnt);
     std::vector<uint64_t> ss(cnt);
     for (i64 q = 0; q < cnt; ++q) {
         const int i = idx[q];
@@ -1989,10 +2015,13 @@ double time_subbatch(const std::vector<int>& idx, const i64* m, const i64* n, co
         nn[q] = n[i];
         bb[q] = bsel[i];
         dd[q] = dsel[i];
+        cc[q] = csel[i];
         ss[q] = seed[i];
     }
     BatchPlan* P = nullptr;
-    if (batch_plan_create(&P, cnt, mm.data(), nn.data(), bb.data(), dd.data(), ss.data(), tol) != 0) return -1.0;
+    if (batch_plan_create_ex(&P, cnt, mm.data(), nn.data(), bb.data(), dd.data(), ss.data(), tol, nullptr, nullptr,
+                             nullptr, cc.data()) != 0)
+        return -1.0;
     double best = -1.0;
     if (P->total <= tb.ws_bytes) {
         cudaEvent_t e0, e1;
@@ -2049,8 +2078,12 @@ size_t batch_autotune_bytes(i64 batch, const i64* m, const i64* n) {
     return tot;
 }
 
+// Per size class of n: the block size b (timing the class alone), then, when
+// ct_out is given, the trailing tile width (32 or 64 columns, timing the class
+// alone with its b); then the sketch ratio gamma over the whole batch.
 int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, const double* A, double tol,
-                   void* ws, size_t ws_bytes, cudaStream_t st, i64* b_out, i64* d_out, double* best_ms) {
+                   void* ws, size_t ws_bytes, cudaStream_t st, i64* b_out, i64* d_out, i64* ct_out,
+                   double* best_ms) {
     if (batch < 0) { set_error("batch < 0"); return -1; }
     if (batch == 0) return 0;
     if (!m || !n || !seed || !A || !b_out || !d_out) { set_error("null argument"); return -2; }
@@ -2077,7 +2110,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
     tb.ws_bytes = ws_bytes - (size_t)(w - (char*)ws);
 
     const i64 cands[4] = {16, 32, 64, 128};
-    std::vector<i64> bsel(batch, 32), dsel(batch, sketch_rows(32, 1.25));
+    std::vector<i64> bsel(batch, 32), dsel(batch, sketch_rows(32, 1.25)), csel(batch, CT);
     std::vector<std::vector<int>> cls(6);
     for (i64 i = 0; i < batch; ++i) cls[size_class(n[i])].push_back((int)i);
     for (int c = 0; c < 6; ++c) {
@@ -2089,7 +2122,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
                 bsel[i] = std::min<i64>(cb, std::max<i64>(n[i], 1));    // a block never exceeds the matrix
                 dsel[i] = sketch_rows(bsel[i], 1.25);
             }
-            const double t = time_subbatch(cls[c], m, n, seed, A, offsrc, bsel, dsel, tol, tb, st);
+            const double t = time_subbatch(cls[c], m, n, seed, A, offsrc, bsel, dsel, csel, tol, tb, st);
             if (t >= 0.0 && (bt < 0.0 || t < bt)) {
                 bt = t;
                 bb = cb;
@@ -2099,6 +2132,12 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
             bsel[i] = std::min<i64>(bb, std::max<i64>(n[i], 1));
             dsel[i] = sketch_rows(bsel[i], 1.25);
         }
+        if (ct_out && bt >= 0.0) {
+            for (int i : cls[c]) csel[i] = CT_MIN;
+            const double t = time_subbatch(cls[c], m, n, seed, A, offsrc, bsel, dsel, csel, tol, tb, st);
+            const bool narrow = t >= 0.0 && t < bt;
+            for (int i : cls[c]) csel[i] = narrow ? CT_MIN : CT;
+        }
     }
     std::vector<int> all(batch);
     for (i64 i = 0; i < batch; ++i) all[i] = (int)i;
@@ -2106,7 +2145,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
     for (double g : {1.25, 1.5}) {
         std::vector<i64> dg(batch);
         for (i64 i = 0; i < batch; ++i) dg[i] = sketch_rows(bsel[i], g);
-        const double t = time_subbatch(all, m, n, seed, A, offsrc, bsel, dg, tol, tb, st);
+        const double t = time_subbatch(all, m, n, seed, A, offsrc, bsel, dg, csel, tol, tb, st);
         if (t >= 0.0 && (t_best < 0.0 || t < t_best)) {
             t_best = t;
             g_best = g;
@@ -2119,6 +2158,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
     for (i64 i = 0; i < batch; ++i) {
         b_out[i] = bsel[i];
         d_out[i] = sketch_rows(bsel[i], g_best);
+        if (ct_out) ct_out[i] = csel[i];
     }
     if (best_ms) *best_ms = t_best;
     return 0;
@@ -2134,6 +2174,17 @@ int bqrrp_batch_plan_create(bqrrp_batch_plan* plan, int64_t batch, const int64_t
     bq::set_error("");
     bq::BatchPlan* P = nullptr;
     const int rc = bq::batch_plan_create(&P, batch, m, n, b, d, seed, trunc_tol);
+    if (plan) *plan = reinterpret_cast<bqrrp_batch_plan>(P);
+    return rc;
+}
+
+int bqrrp_batch_plan_create_tiles(bqrrp_batch_plan* plan, int64_t batch, const int64_t* m, const int64_t* n,
+                                  const int64_t* b, const int64_t* d, const int64_t* tile_cols, const uint64_t* seed,
+                                  double trunc_tol) {
+    bq::set_error("");
+    bq::BatchPlan* P = nullptr;
+    const int rc = bq::batch_plan_create_ex(&P, batch, m, n, b, d, seed, trunc_tol, nullptr, nullptr, nullptr,
+                                            tile_cols);
     if (plan) *plan = reinterpret_cast<bqrrp_batch_plan>(P);
     return rc;
 }
@@ -2180,7 +2231,16 @@ int bqrrp_batch_autotune(int64_t batch, const int64_t* m, const int64_t* n, cons
                          int64_t* d_out, double* best_ms) {
     bq::set_error("");
     return bq::batch_autotune(batch, m, n, seed, A, trunc_tol, workspace, workspace_bytes, (cudaStream_t)stream,
-                              b_out, d_out, best_ms);
+                              b_out, d_out, nullptr, best_ms);
+}
+
+int bqrrp_batch_autotune_tiles(int64_t batch, const int64_t* m, const int64_t* n, const uint64_t* seed,
+                               const double* A, double trunc_tol, void* workspace, size_t workspace_bytes,
+                               void* stream, int64_t* b_out, int64_t* d_out, int64_t* tile_out, double* best_ms) {
+    bq::set_error("");
+    if (batch > 0 && !tile_out) { bq::set_error("tile_out is null"); return -12; }
+    return bq::batch_autotune(batch, m, n, seed, A, trunc_tol, workspace, workspace_bytes, (cudaStream_t)stream,
+                              b_out, d_out, tile_out, best_ms);
 }
 
 }  // extern "C"

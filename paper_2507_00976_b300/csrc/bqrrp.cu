@@ -267,6 +267,11 @@ __global__ void zero_tail_kernel(i64 from, i64 to, double* tau) {
 
 inline unsigned gblocks(const Ctx& c, i64 total) { return (unsigned)imax(1, imin(cdiv(total, 256), 8LL * c.dev.sms)); }
 
+// The products of both mixed forms run on the tensor cores.
+inline bool is_mixed(const bqrrp_opts& o) {
+    return o.precision == BQRRP_PRECISION_MIXED || o.precision == BQRRP_PRECISION_MIXED_SKETCH32;
+}
+
 // ------------------------------------------------------------------ workspace plan
 struct Bufs {
     DevStatus* st;
@@ -317,7 +322,7 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
     B->Jstage = ar.take<i64>((size_t)B->max_moved);
     B->oz_bytes = 0;
     B->oz_ws = nullptr;
-    if (o.precision == BQRRP_PRECISION_MIXED) {
+    if (is_mixed(o)) {
         size_t z = ozaki_ws_bytes(bb, n, m, kOzPlanes);         // W = Y^T C
         z = std::max(z, ozaki_ws_bytes(m, n, bb, kOzPlanes));   // C -= Y W2
         z = std::max(z, ozaki_ws_bytes(bb, n, bb, kOzPlanes));  // W2 = T^T W
@@ -364,7 +369,9 @@ int check_opts(const bqrrp_opts* o, i64 d) {
         const i64 nnz = o->sketch_nnz > 0 ? o->sketch_nnz : 8;
         if (nnz > d || nnz > 64) return 1;
     }
-    if (o->precision != BQRRP_PRECISION_FP64 && o->precision != BQRRP_PRECISION_MIXED) return 1;
+    if (o->precision != BQRRP_PRECISION_FP64 && o->precision != BQRRP_PRECISION_MIXED &&
+        o->precision != BQRRP_PRECISION_MIXED_SKETCH32)
+        return 1;
     if (o->schedule != BQRRP_SCHEDULE_OVERLAP && o->schedule != BQRRP_SCHEDULE_SERIAL) return 1;
     for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return 1;
@@ -692,7 +699,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             // ---- trailing update with the block reflector (I - Y T Y^T)^T
             double* C = A + s + cend * lda;
             const i64 keep = (k == w) ? rows : k;
-            if (nc > 0 && o.precision == BQRRP_PRECISION_MIXED) {
+            if (nc > 0 && is_mixed(o)) {
                 pr.begin(P_TRAIL);
                 BQ_TRY(ozaki_gemm(c, true, false, k, nc, rows, 1.0, B.Ypan, m, C, lda, 0.0, B.W, B.wrows,
                                   B.oz_ws, B.oz_bytes));
@@ -822,7 +829,8 @@ int factor_entry(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int64_
     c.splitk_elems = B.splitk_elems;
     c.coop = B.coop;
     c.coop_elems = B.coop_elems;
-    c.mixed = (o.precision == BQRRP_PRECISION_MIXED);
+    c.mixed = is_mixed(o);
+    c.sketch32 = (o.precision == BQRRP_PRECISION_MIXED_SKETCH32);
     c.oz_ws = B.oz_ws;
     c.oz_bytes = B.oz_bytes;
     i64 r = 0;

@@ -187,8 +187,10 @@ __device__ inline bool grid_barrier(DevStatus* st, unsigned int nblocks) {
 
 // ------------------------------------------------------------------ batched plans (batched.cu)
 struct BatchPlan;
+// ct: columns per trailing-update tile of each matrix, 32 or 64 (null: 64).
 int batch_plan_create_ex(BatchPlan** out, i64 batch, const i64* m, const i64* n, const i64* b, const i64* d,
-                         const uint64_t* seed, double tol, const i64* offA, const i64* offJ, const i64* offT);
+                         const uint64_t* seed, double tol, const i64* offA, const i64* offJ, const i64* offT,
+                         const i64* ct);
 size_t batch_plan_bytes(const BatchPlan* P);
 int batch_factor(BatchPlan* P, double* A, int64_t* jpvt, double* tau, int64_t* rank, int64_t* trunc,
                  int32_t* info, void* ws, size_t ws_bytes, cudaStream_t stream, int use_graph);
@@ -212,6 +214,9 @@ struct Ctx {
     size_t coop_elems;
     // mixed precision: large products go to the bf16-slice tensor-core GEMM
     bool mixed = false;
+    // reduced-precision sketch QR: the QR of the d x d LU factor (Alg. 2's
+    // R^sk) in FP32 arithmetic
+    bool sketch32 = false;
     void* oz_ws = nullptr;
     size_t oz_bytes = 0;
 };

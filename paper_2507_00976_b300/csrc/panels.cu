@@ -973,19 +973,36 @@ constexpr int kSqrMaxD = 640;
 
 __device__ inline void bar_sync_64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }   // warps 0-1
 
+// T: the arithmetic (double; float for the reduced-precision sketch QR, whose
+// loads and stores of W convert).  Sign and zero tests on T's bit pattern.
+__device__ __forceinline__ bool sq_nonzero(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) != 0;
+}
+__device__ __forceinline__ bool sq_nonzero(float x) { return ((unsigned)__float_as_uint(x) & 0x7fffffffu) != 0; }
+__device__ __forceinline__ bool sq_nonneg(double x) {   // x >= 0.0 (-0.0 counts as non-negative)
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool sq_nonneg(float x) {
+    const int b = __float_as_int(x);
+    return b >= 0 || b == (int)0x80000000u;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
-    extern __shared__ double loc[];                 // [ncl][d] local columns
-    __shared__ double vbuf[2][kSqrMaxD];
-    __shared__ double vloc[kSqrMaxD];
-    __shared__ double s_tau[2], s_scal[2];
-    __shared__ double red2[2];
+    extern __shared__ __align__(16) unsigned char loc_raw[];
+    T* loc = (T*)loc_raw;                           // [ncl][d] local columns
+    __shared__ T vbuf[2][kSqrMaxD];
+    __shared__ T vloc[kSqrMaxD];
+    __shared__ T s_tau[2], s_scal[2];
+    __shared__ T red2[2];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), g = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncl = (int)((s - g + C - 1) / C);    // columns g, g + C, ... below s
     for (int lc = 0; lc < ncl; ++lc) {
         const i64 gc = (i64)lc * C + g;
-        for (i64 r = tid; r < d; r += NT) loc[(i64)lc * d + r] = W[r + gc * d];
+        for (i64 r = tid; r < d; r += NT) loc[(i64)lc * d + r] = (T)W[r + gc * d];
     }
     __syncthreads();
 
@@ -997,17 +1014,16 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     // (beta, 0, ..., 0).
     // Scalars of the reflector of column j (x), given xn2 = ||x(j+1:)||^2;
     // one thread.  Writes beta into x(j) and tau, scale to s_tau/s_scal[par].
-    auto reflector_scalars = [&](double* x, i64 j, double xn2, int par) {
-        const double alpha = x[j];
-        const bool nz = ((unsigned long long)__double_as_longlong(xn2) & 0x7fffffffffffffffull) != 0;
-        double tau = 0.0, beta = alpha, scal = 1.0;
+    auto reflector_scalars = [&](T* x, i64 j, T xn2, int par) {
+        const T alpha = x[j];
+        const bool nz = sq_nonzero(xn2);
+        T tau = T(0), beta = alpha, scal = T(1);
         if (nz) {
-            const long long ab = __double_as_longlong(alpha);
-            const bool apos = ab >= 0 || ab == (long long)0x8000000000000000ull;   // alpha >= 0.0
-            const double nrm = sqrt(alpha * alpha + xn2);
+            const bool apos = sq_nonneg(alpha);
+            const T nrm = sqrt(alpha * alpha + xn2);
             beta = apos ? -nrm : nrm;
-            const double am = alpha - beta;
-            const double q = 1.0 / (beta * am);
+            const T am = alpha - beta;
+            const T q = T(1) / (beta * am);
             scal = beta * q;
             tau = -(am * am) * q;
         }
@@ -1017,8 +1033,8 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     };
     // The first reflector, by one warp.
     auto reflect = [&](i64 j, int par) {
-        double* x = loc + (j / C) * d;
-        double xn2 = 0.0;
+        T* x = loc + (j / C) * d;
+        T xn2 = T(0);
         for (i64 r = j + 1 + lane; r < d; r += 32) xn2 = fma(x[r], x[r], xn2);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
@@ -1026,16 +1042,16 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
         if (lane == 0) reflector_scalars(x, j, xn2, par);
         for (i64 r = j + 1 + lane; r < d; r += 32) {
             vbuf[par][r] = x[r];
-            x[r] = 0.0;                                   // below the diagonal of R
+            x[r] = T(0);                                  // below the diagonal of R
         }
     };
     // col -= tau v (v^T col) over rows [j, d), by one warp
-    auto apply = [&](double* col, i64 j, double tau) {
-        double dot = 0.0;
+    auto apply = [&](T* col, i64 j, T tau) {
+        T dot = T(0);
         for (i64 r = j + lane; r < d; r += 32) dot = fma(vloc[r], col[r], dot);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-        const double w = tau * dot;
+        const T w = tau * dot;
         for (i64 r = j + lane; r < d; r += 32) col[r] = fma(-w, vloc[r], col[r]);
     };
 
@@ -1045,32 +1061,32 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
         const int o = (int)(j % C), par = (int)(j & 1);
         // reflector j from its owner (the two scalars and the vector in one round of
         // remote loads)
-        const double* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
-        const double scal = *cl.map_shared_rank(&s_scal[par], o);
-        const double tau = *cl.map_shared_rank(&s_tau[par], o);
-        for (i64 r = j + tid; r < d; r += NT) vloc[r] = (r == j) ? 1.0 : vsrc[r] * scal;
+        const T* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
+        const T scal = *cl.map_shared_rank(&s_scal[par], o);
+        const T tau = *cl.map_shared_rank(&s_tau[par], o);
+        for (i64 r = j + tid; r < d; r += NT) vloc[r] = (r == j) ? T(1) : vsrc[r] * scal;
         __syncthreads();
-        const bool live = ((unsigned long long)__double_as_longlong(tau) & 0x7fffffffffffffffull) != 0;
+        const bool live = sq_nonzero(tau);
         const bool next_here = j + 1 < s && (int)((j + 1) % C) == g;
         if (next_here && warp < 2) {
             // lookahead: warps 0-1 update column j+1 first, then form its reflector
             // (rows split over 64 threads, partial sums combined through shared
             // memory behind named barrier 1)
             const int t = tid;
-            double* x = loc + ((j + 1) / C) * d;
+            T* x = loc + ((j + 1) / C) * d;
             if (live) {
-                double dot = 0.0;
+                T dot = T(0);
                 for (i64 r = j + t; r < d; r += 64) dot = fma(vloc[r], x[r], dot);
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
                 if (lane == 0) red2[warp] = dot;
                 bar_sync_64();
-                const double w = tau * (red2[0] + red2[1]);
+                const T w = tau * (red2[0] + red2[1]);
                 for (i64 r = j + t; r < d; r += 64) x[r] = fma(-w, vloc[r], x[r]);
                 bar_sync_64();
             }
             const i64 jj = j + 1;
-            double xn2 = 0.0;
+            T xn2 = T(0);
             for (i64 r = jj + 1 + t; r < d; r += 64) xn2 = fma(x[r], x[r], xn2);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, off);
@@ -1079,7 +1095,7 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
             if (t == 0) reflector_scalars(x, jj, red2[0] + red2[1], par ^ 1);
             for (i64 r = jj + 1 + t; r < d; r += 64) {   // same rows as this thread's norm terms
                 vbuf[par ^ 1][r] = x[r];
-                x[r] = 0.0;                               // below the diagonal of R
+                x[r] = T(0);                              // below the diagonal of R
             }
         }
         if (live) {
@@ -1096,19 +1112,22 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     }
     for (int lc = 0; lc < ncl; ++lc) {
         const i64 gc = (i64)lc * C + g;
-        for (i64 r = tid; r < d; r += NT) W[r + gc * d] = (r <= gc) ? loc[(i64)lc * d + r] : 0.0;
+        for (i64 r = tid; r < d; r += NT) W[r + gc * d] = (r <= gc) ? (double)loc[(i64)lc * d + r] : 0.0;
     }
     cl.sync();    // no CTA leaves while another may still read its shared memory
 }
 
 // Launch on a cluster of up to 16 CTAs; -1 when the shape or the cluster does
 // not fit (the caller then uses the blocked QR).
+// c.sketch32: the QR in FP32 arithmetic (W converted on load and store).
 int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
     if (d > kSqrMaxD || s < 1 || s > d) return -1;
     int C = 16;
     size_t smem = (size_t)((s + C - 1) / C) * (size_t)d * sizeof(double);
     if (smem > 208 * 1024) return -1;
-    BQ_TRY(kernel_attrs((const void*)small_qr_cluster_kernel, 208 * 1024, true));
+    const void* fn = c.sketch32 ? (const void*)small_qr_cluster_kernel<float> : (const void*)small_qr_cluster_kernel<double>;
+    if (c.sketch32) smem /= 2;
+    BQ_TRY(kernel_attrs(fn, 208 * 1024, true));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(NT);
@@ -1122,7 +1141,9 @@ int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     count_launch();
-    if (cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel, d, s, W) != cudaSuccess) {
+    const cudaError_t le = c.sketch32 ? cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<float>, d, s, W)
+                                      : cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<double>, d, s, W);
+    if (le != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }

@@ -260,7 +260,7 @@ int Server::do_small(std::vector<Req*>& batch) {
     }
     BatchPlan* P = nullptr;
     int rc = batch_plan_create_ex(&P, nb, m.data(), n.data(), b.data(), d.data(), sd.data(), tol, oA.data(),
-                                  oJ.data(), oT.data());
+                                  oJ.data(), oT.data(), nullptr);
     if (rc != 0) return rc;
     // short per-phase launches: they interleave with the large lane's
     // grid-wide kernels, where the persistent form would hold the SMs

@@ -41,11 +41,11 @@ def unpack(F, jpvt, tau, m, n):
     return out
 
 
-def run_batch(mats, b, d, seeds, use_graph=False, tol=TOL, form=B.BATCH_PERSISTENT):
+def run_batch(mats, b, d, seeds, use_graph=False, tol=TOL, form=B.BATCH_PERSISTENT, tiles=None):
     m = np.array([A.shape[0] for A in mats], dtype=np.int64)
     n = np.array([A.shape[1] for A in mats], dtype=np.int64)
     F, jpvt, tau, rank, trunc, info = B.factor_batched(pack(mats), m, n, b, d, seeds, tol, use_graph=use_graph,
-                                                       form=form)
+                                                       form=form, tiles=tiles)
     return m, n, np_(F), np_(jpvt), np_(tau), np_(rank), np_(trunc), np_(info)
 
 
@@ -220,3 +220,63 @@ def test_dependency_driven_and_lockstep_forms_agree_bitwise():
                          (mega[0][:6], mega[1][:6], mega[2][:W.batch_offsets(mega[0][:6], mega[1][:6])[2]],
                           mega[3][:W.batch_offsets(mega[0][:6], mega[1][:6])[3]],
                           mega[4][:W.batch_offsets(mega[0][:6], mega[1][:6])[3]], mega[5][:6], mega[6][:6], mega[7][:6]))
+
+
+def test_batched_narrow_tiles_meet_the_bar():
+    """32-column trailing tiles (every other matrix), mixed shapes and block
+    sizes, against the oracle; both launch forms give the same bits, and a
+    matrix alone gives the same bits as in the mix."""
+    m, n = W.batched_shapes(30, 41, m_hi=600)
+    mats = [W.batched_matrix(int(a), int(c), 1300 + i) for i, (a, c) in enumerate(zip(m, n))]
+    b = np.array([[16, 32, 64, 128, 8][i % 5] for i in range(30)], dtype=np.int64)
+    b = np.minimum(b, np.maximum(n, 1))
+    d = np.ceil(1.25 * b).astype(np.int64)
+    tiles = np.array([32 if i % 2 == 0 else 64 for i in range(30)], dtype=np.int64)
+    seeds = np.arange(30, dtype=np.uint64) + 500
+    mega = run_batch(mats, b, d, seeds, use_graph=True, tiles=tiles)
+    lock = run_batch(mats, b, d, seeds, form=B.BATCH_LOCKSTEP, tiles=tiles)
+    for x, y in zip(mega, lock):
+        assert np.array_equal(x, y)
+    check_against_oracle(mats, b, d, seeds, mega)
+    parts = unpack(mega[2], mega[3], mega[4], mega[0], mega[1])
+    for i in [0, 7, 28]:
+        alone = run_batch([mats[i]], b[[i]], d[[i]], seeds[[i]], tiles=tiles[[i]])
+        assert np.array_equal(alone[2], parts[i][0].ravel(order="F"))
+
+
+def test_batched_narrow_tiles_full_size_and_edges():
+    shapes = [(1024, 1000), (1024, 33), (700, 64), (300, 31)]
+    mats = [W.batched_matrix(a, c, 1400 + i) for i, (a, c) in enumerate(shapes)]
+    mats += [W.low_rank(300, 200, 37, 5), np.zeros((70, 40)), W.gaussian(65, 1, 3)]
+    b = np.array([16, 16, 32, 128, 32, 16, 16], dtype=np.int64)
+    b = np.minimum(b, [A.shape[1] for A in mats])
+    d = np.ceil(1.25 * b).astype(np.int64)
+    seeds = np.arange(len(mats), dtype=np.uint64) + 40
+    tiles = np.full(len(mats), 32, dtype=np.int64)
+    check_against_oracle(mats, b, d, seeds, run_batch(mats, b, d, seeds, tiles=tiles))
+
+
+def test_batched_tile_width_is_validated():
+    with pytest.raises(B.BqrrpError):
+        B.BatchPlan([64], [32], [16], [20], [1], TOL, tiles=[48])
+
+
+def test_batched_autotune_tiles_choices_are_valid():
+    m, n = W.batched_shapes(60, 6, m_hi=600)
+    mats = [W.batched_matrix(int(a), int(c), 600 + i) for i, (a, c) in enumerate(zip(m, n))]
+    seeds = np.arange(60, dtype=np.uint64) + 19
+    A = torch.as_tensor(pack(mats), device="cuda")
+    A_before = A.clone()
+    b, d, tiles, best = B.bqrrp_batch_autotune_tiles(m, n, seeds, A, TOL)
+    assert torch.equal(A, A_before)
+    assert best > 0
+    assert np.all(np.isin(tiles, [32, 64]))
+    assert np.all(d >= b) and np.all(b >= 1) and np.all(b <= n)
+    # one tile width per size class of n
+    cls = np.minimum(np.floor(np.log2(np.maximum(n, 1) / 32.0)).clip(0), 5).astype(int)
+    for c in set(cls.tolist()):
+        assert len(set(tiles[cls == c].tolist())) == 1, c
+    pick = [1, 30, 58]
+    sub = [mats[i] for i in pick]
+    check_against_oracle(sub, b[pick], d[pick], seeds[pick],
+                         run_batch(sub, b[pick], d[pick], seeds[pick], tiles=tiles[pick]))
