@@ -162,6 +162,8 @@ def parse():
     p.add_argument("--requests", type=int, default=200,
                    help="serving: requests per load level (a bounded sample of the 20000-request stream)")
     p.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.2])
+    p.add_argument("--serving-precision", choices=["fp64", "mixed"], default="fp64",
+                   help="serving: arithmetic of the large lane (mixed: FP64-accurate products on the tensor cores)")
     p.add_argument("--batch-b", type=int, default=0,
                    help="batched: fixed block size for every matrix instead of the autotuner (d = ceil(1.25 b))")
     p.add_argument("--batch-tile", type=int, default=64, choices=[32, 64],
@@ -696,7 +698,8 @@ def run_serving(a, world, rank, local):
         outs.append((torch.empty((n, m), dtype=torch.float64).pin_memory(),
                      torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory()))
     budget = 120 << 30
-    S = B.Server(budget, 8 << 30, trunc_tol=tol, small_max_elems=1 << 20)
+    mixed_lane = a.serving_precision == "mixed"
+    S = B.Server(budget, (12 if mixed_lane else 8) << 30, trunc_tol=tol, small_max_elems=1 << 20, mixed=mixed_lane)
 
     def draw(count, rng_):
         kinds = rng_.choice(len(SERVING_SHAPES), size=count, p=SERVING_WEIGHTS)
@@ -774,7 +777,9 @@ def run_serving(a, world, rank, local):
         "config": {"workload": "serving loop: Poisson arrivals of FP64 factorization requests, shapes 256x256 / "
                                "1024x512 / 4096x2048 / 8192x4096 with weights 0.5/0.3/0.15/0.05, spectra geometric "
                                "from 1 to a decay uniform in exponent on [1e-14, 1e-4], truncation 1e-8, admission by "
-                               "a 120 GB HBM budget, continuous batching of the small shapes",
+                               "a 120 GB HBM budget, continuous batching of the small shapes"
+                               + ("; large lane in the mixed form (FP64-accurate products on the tensor cores)"
+                                  if mixed_lane else ""), "large_lane_precision": a.serving_precision,
                    "requests_per_load": len(base_stream),
                    "sample": (f"{len(base_stream)} requests per load level" +
                               (" (the configured 20000-request stream)" if len(base_stream) >= 20000 else

@@ -53,13 +53,16 @@ extern "C" {
                                     tensor cores through exact 7-bit slices (see
                                     bqrrp_dgemm_ozaki); LU, sketch QR, panel, tau, R
                                     in FP64                                          */
-#define BQRRP_PRECISION_MIXED_SKETCH32 2 /* as _MIXED, and the QR that forms R^sk
-                                    from the sketch's LU factor (Alg. 2) in FP32
-                                    arithmetic: the pivots still come from the FP64
-                                    LU; R^sk, which preconditions the panel and
-                                    becomes the next sketch, is accurate to FP32
-                                    relative to the current block's sketch; the
-                                    panel, tau and R stay FP64                      */
+#define BQRRP_PRECISION_MIXED_SKETCH32 2 /* as _MIXED, and Alg. 2 on the sketch in
+                                    FP32 arithmetic: the LU panels' pivot search and
+                                    eliminations (the sketch stays FP64 in memory,
+                                    the updates between panels are FP64 products)
+                                    and the QR that forms R^sk from the LU factor.
+                                    The pivots are FP32 decisions; R^sk, which
+                                    preconditions the panel and becomes the next
+                                    sketch, is accurate to FP32 relative to the
+                                    current block's sketch; the panel, tau and R
+                                    stay FP64                                       */
 
 /* Order of the steps of consecutive blocks (the results are the same bit for bit). */
 #define BQRRP_SCHEDULE_OVERLAP 0 /* the sketch update and Alg. 2 of block i+1 run on a
@@ -471,6 +474,11 @@ int bqrrp_batch_autotune_tiles(int64_t batch, const int64_t* m, const int64_t* n
  * memory (host-side tests of admission and batching).
  * ------------------------------------------------------------------------ */
 #define BQRRP_SERVER_DRYRUN 1
+/* flags: BQRRP_SERVER_MIXED factors the large lane's requests with
+ * opts.precision = BQRRP_PRECISION_MIXED (FP64-accurate products on the
+ * tensor cores; the same 1e-12 bar as FP64); the small lane is unchanged.
+ * Other flag bits: -6. */
+#define BQRRP_SERVER_MIXED 2
 
 typedef struct bqrrp_request {
     uint64_t id;              /* caller's tag, echoed in the completion                  */

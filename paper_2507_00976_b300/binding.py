@@ -68,6 +68,7 @@ class ServerStats(ctypes.Structure):
 
 
 SERVER_DRYRUN = 1
+SERVER_MIXED = 2
 
 
 class BqrrpError(RuntimeError):
@@ -621,11 +622,11 @@ class Server:
     alive here until their completion has been polled."""
 
     def __init__(self, hbm_budget_bytes, workspace_bytes, trunc_tol=1e-8, small_max_elems=1 << 20, dry=False,
-                 dry_gflops=1000.0):
+                 dry_gflops=1000.0, mixed=False):
         h = _vp()
+        flags = (SERVER_DRYRUN if dry else 0) | (SERVER_MIXED if mixed else 0)
         rc = lib().bqrrp_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(workspace_bytes),
-                                       float(trunc_tol), int(small_max_elems), SERVER_DRYRUN if dry else 0,
-                                       float(dry_gflops))
+                                       float(trunc_tol), int(small_max_elems), flags, float(dry_gflops))
         _check("bqrrp_server_create", rc)
         self.handle = h
         self._keep = {}

@@ -17,6 +17,7 @@ __global__ void init_status_small(DevStatus* st) {
     st->k = 0;
     st->moved = 0;
     st->r00 = 0.0;
+    st->blk00 = 0.0;
     st->bar.count = 0;
     st->bar.gen = 0;
 }

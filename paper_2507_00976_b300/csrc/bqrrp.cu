@@ -181,6 +181,7 @@ __global__ void init_status_kernel(DevStatus* st) {
     st->k = 0;
     st->moved = 0;
     st->r00 = 0.0;
+    st->blk00 = 0.0;
     st->bar.count = 0;
     st->bar.gen = 0;
 }
@@ -197,25 +198,37 @@ __global__ void plus_one_kernel(i64 n, const i64* J, i64* jpvt) {
 
 // tri_rank (Sec. 2.2, reading): k = largest j <= w with |Rsk(t,t)| > 10 d u r00
 // for all t < j, r00 = |Rsk(0,0)| of the first iteration.
+// With the FP32 sketch QRCP (fp32 != 0), R^sk carries FP32 rounding of the
+// current block's own scale, so two more cuts apply, both at 10 d 2^-24:
+// a diagonal entry that small relative to the block's |Rsk(0,0)| (a rank gap
+// inside the block), and a whole block whose |Rsk(0,0)| is that small
+// relative to the previous block's (a gap at a block boundary).  Below those
+// ratios the FP32 factor cannot tell a column from rounding noise.
+constexpr double kUnitRoundoff32 = 5.9604644775390625e-08;   // 2^-24
 __global__ void __launch_bounds__(1024) tri_rank_kernel(DevStatus* st, const double* Rsk, i64 ldr, i64 w, i64 d,
-                                                        int first) {
-    __shared__ double r00s;
-    __shared__ int firstbad;
+                                                        int first, int fp32) {
+    __shared__ double r00s, thr32s;
+    __shared__ int firstbad, cross_bad;
     if (threadIdx.x == 0) {
-        if (first) st->r00 = fabs(Rsk[0]);
+        const double a00 = fabs(Rsk[0]);
+        if (first) st->r00 = a00;
         r00s = st->r00;
         firstbad = INT_MAX;
+        const double floor32 = 10.0 * (double)d * kUnitRoundoff32;
+        thr32s = fp32 ? floor32 * a00 : 0.0;
+        cross_bad = (fp32 && !first && !(a00 > floor32 * st->blk00)) ? 1 : 0;
+        st->blk00 = a00;
     }
     __syncthreads();
     const double r00 = r00s;
-    const double thr = 10.0 * (double)d * kUnitRoundoff * r00;
+    const double thr = fmax(10.0 * (double)d * kUnitRoundoff * r00, thr32s);
     const bool scale_ok = r00 > 0.0 && isfinite(r00);
     for (i64 t = threadIdx.x; t < w; t += blockDim.x) {
         const double v = Rsk[t + t * ldr];
         if (!isfinite(v) || !(fabs(v) > thr)) atomicMin(&firstbad, (int)t);
     }
     __syncthreads();
-    if (threadIdx.x == 0) st->k = scale_ok ? (firstbad < w ? (i64)firstbad : w) : 0;
+    if (threadIdx.x == 0) st->k = (scale_ok && !cross_bad) ? (firstbad < w ? (i64)firstbad : w) : 0;
 }
 
 // st->zero_col <- 1 if any entry of the column is nonzero (early-exit test)
@@ -619,7 +632,7 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         // scratch of the blocked-QR fallback: W and the column stage, which the
         // rest of the trailing update (Y, W2, C) does not touch
         BQ_TRY(rsk_from_lu(cs, d, N, B.Xlu, d, Ssk, d, B.Ub, B.sktau, B.Vqr, B.Tqr, B.W, B.stage));
-        tri_rank_kernel<<<1, 1024, 0, cs.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0);
+        tri_rank_kernel<<<1, 1024, 0, cs.stream>>>(B.st, Ssk, d, w, d, it == 0 ? 1 : 0, cs.sketch32 ? 1 : 0);
         BQ_LAUNCH_CHECK();
         pr.flops(P_SKQR, geqrf_flops((double)d, (double)N));
         if (overlap) pr.end_lane(1);

@@ -97,6 +97,7 @@ struct DevStatus {
     i64 k;                 // tri_rank result
     i64 moved;             // number of columns the permutation moves
     double r00;            // |Rsk(0,0)| of the first iteration (tri_rank scale)
+    double blk00;          // |Rsk(0,0)| of the previous iteration (FP32 sketch QRCP: rank floor)
     GridBar bar;
     unsigned int pad1[2];
 };
@@ -214,8 +215,8 @@ struct Ctx {
     size_t coop_elems;
     // mixed precision: large products go to the bf16-slice tensor-core GEMM
     bool mixed = false;
-    // reduced-precision sketch QR: the QR of the d x d LU factor (Alg. 2's
-    // R^sk) in FP32 arithmetic
+    // reduced-precision Alg. 2: the LU panels and the QR of the d x d LU
+    // factor (R^sk) in FP32 arithmetic
     bool sketch32 = false;
     void* oz_ws = nullptr;
     size_t oz_bytes = 0;

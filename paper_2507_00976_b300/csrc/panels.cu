@@ -106,6 +106,18 @@ struct Cand {
 __device__ inline unsigned long long abs_key(double x) {
     return (unsigned long long)__double_as_longlong(x) & kAbsMask;
 }
+// The panel's arithmetic type T (double; float for the reduced-precision
+// pivot choice): a value's bits as published in a slot, |value| as a key from
+// those bits, and the value back.
+__device__ inline unsigned long long abs_key(float x) { return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu); }
+__device__ inline unsigned long long val_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ inline unsigned long long val_bits(float x) { return (unsigned long long)__float_as_uint(x); }
+template <typename T> __device__ inline unsigned long long abs_of_bits(unsigned long long vb);
+template <> __device__ inline unsigned long long abs_of_bits<double>(unsigned long long vb) { return vb & kAbsMask; }
+template <> __device__ inline unsigned long long abs_of_bits<float>(unsigned long long vb) { return vb & 0x7fffffffull; }
+template <typename T> __device__ inline T from_bits(unsigned long long vb);
+template <> __device__ inline double from_bits<double>(unsigned long long vb) { return __longlong_as_double((long long)vb); }
+template <> __device__ inline float from_bits<float>(unsigned long long vb) { return __uint_as_float((unsigned)vb); }
 
 // First-maximum rule: the larger |x| wins, equal values go to the smaller row.
 __device__ inline Cand better(Cand a, Cand b) { return (b.key > a.key || (b.key == a.key && b.t < a.t)) ? b : a; }
@@ -128,14 +140,21 @@ __device__ inline Cand block_best_all(Cand x, unsigned long long* wk, long long*
     return r;
 }
 
+// T: the panel's arithmetic.  The sketch Sk stays FP64 in memory; with float
+// the slab holds the rows rounded to FP32, the pivot search, multipliers and
+// eliminations run in FP32, and the factors are written back widened.
+template <typename T>
 __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
-    extern __shared__ double slab[];          // [pw][Rp]
-    __shared__ double prow[64];
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    T* slab = (T*)slab_raw;                   // [pw][Rp]
+    T* cand_row = (T*)a.cand_row;             // [3][G][pw]
+    T* cur_row = (T*)a.cur_row;               // [3][pw]
+    __shared__ T prow[64];
     __shared__ unsigned long long wk[NT / 32];
     __shared__ long long wt[NT / 32];
     __shared__ long long s_p;
     __shared__ unsigned long long s_pivbits;
-    __shared__ double s_rpiv;
+    __shared__ T s_rpiv;
     __shared__ int s_gw, s_ok;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const i64 t0 = a.jb + (i64)g * a.R;
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
 
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
-        slab[c * Rp + rl] = a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
+        slab[c * Rp + rl] = (T)a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
     }
     // identity pivots first: a panel that gives up on the exchange (timeout)
     // leaves in-range, no-op interchanges for the kernels that follow it
@@ -161,14 +180,13 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         const i64 cur = a.jb + k;
         if (b.t != kNoRow && tid < pw) {
             const int r = (int)(b.t - t0), c = tid;
-            const double x = slab[c * Rp + r];
-            a.cand_row[((size_t)buf * G + g) * pw + c] =
-                (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
+            const T x = slab[c * Rp + r];
+            cand_row[((size_t)buf * G + g) * pw + c] = (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
         }
         if (cur >= t0 && cur < t1 && tid >= 64 && tid < 64 + pw) {
             const int r = (int)(cur - t0), c = tid - 64;
-            const double x = slab[c * Rp + r];
-            a.cur_row[(size_t)buf * pw + c] = (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
+            const T x = slab[c * Rp + r];
+            cur_row[(size_t)buf * pw + c] = (elim && c > j + 1) ? fma(-slab[j * Rp + r], prow[c], x) : x;
         }
         __syncthreads();
         if (tid == 0) {
@@ -178,7 +196,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                 st_relaxed_u64(old + 1, kSlotEmpty);
             }
             unsigned long long vb = 0;   // signed candidate value (+0 for "no candidate")
-            if (b.t != kNoRow) vb = (unsigned long long)__double_as_longlong(slab[k * Rp + (int)(b.t - t0)]);
+            if (b.t != kNoRow) vb = val_bits(slab[k * Rp + (int)(b.t - t0)]);
             if (vb == kSlotEmpty) vb = 0xfff8000000000000ull;   // that NaN pattern marks an empty slot
             fence_acq_rel_gpu();
             unsigned long long* s = a.slot + ((size_t)buf * G + g) * 2;
@@ -211,7 +229,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
                 for (int q = tid; q < G; q += 32) {
                     const unsigned long long vb = ld_relaxed_u64(sl + 2 * q), tb = ld_relaxed_u64(sl + 2 * q + 1);
                     if (vb == kSlotEmpty || tb == kSlotEmpty) { all = false; continue; }
-                    const Cand z = better(w, Cand{vb & kAbsMask, (long long)tb});
+                    const Cand z = better(w, Cand{abs_of_bits<T>(vb), (long long)tb});
                     if (z.t != w.t) { w = z; wq = q; wvb = vb; }
                 }
                 if (__all_sync(0xffffffffu, all)) break;
@@ -248,34 +266,34 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         if (!s_ok) return;
         const i64 p = s_p;
         const int gw = s_gw, buf = j % 3;
-        const bool elim = (s_pivbits & kAbsMask) != 0;   // exact zero pivot: no elimination, as GETRF
+        const bool elim = abs_of_bits<T>(s_pivbits) != 0;   // exact zero pivot: no elimination, as GETRF
         // (2) pivot row into prow and the slab; current row jg to the winner's
         // place; one warp forms 1/piv meanwhile
         if (tid < pw) {
-            const double pr = __ldcg(&a.cand_row[((size_t)buf * G + gw) * pw + tid]);
+            const T pr = __ldcg(&cand_row[((size_t)buf * G + gw) * pw + tid]);
             prow[tid] = pr;
             if (jg >= t0 && jg < t1) slab[tid * Rp + (jg - t0)] = pr;
-            if (p != jg && p >= t0 && p < t1) slab[tid * Rp + (p - t0)] = __ldcg(&a.cur_row[(size_t)buf * pw + tid]);
+            if (p != jg && p >= t0 && p < t1) slab[tid * Rp + (p - t0)] = __ldcg(&cur_row[(size_t)buf * pw + tid]);
         }
-        if (tid == 64 && elim) s_rpiv = 1.0 / __longlong_as_double((long long)s_pivbits);
+        if (tid == 64 && elim) s_rpiv = T(1) / from_bits<T>(s_pivbits);
         __syncthreads();
         // (3) multipliers and column j+1 of the owned rows below jg; next candidate.
         // l = x / piv from the reciprocal with one FMA correction (Markstein's
         // quotient refinement: r = x - piv*l is exact, l + r/piv rounds to x/piv),
         // so equal rows still cancel exactly as in GETRF.
-        const double rpiv = s_rpiv, pivv = __longlong_as_double((long long)s_pivbits);
+        const T rpiv = s_rpiv, pivv = from_bits<T>(s_pivbits);
         const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
         Cand b{0, kNoRow};
         for (int rl = r0 + tid; rl < nloc; rl += NT) {
-            double l = 0.0;
+            T l = T(0);
             if (elim) {
-                const double x = slab[j * Rp + rl];
+                const T x = slab[j * Rp + rl];
                 l = x * rpiv;
                 l = fma(fma(-pivv, l, x), rpiv, l);
                 slab[j * Rp + rl] = l;
             }
             if (has_next) {
-                double x = slab[(j + 1) * Rp + rl];
+                T x = slab[(j + 1) * Rp + rl];
                 if (elim) {
                     x = fma(-l, prow[j + 1], x);
                     slab[(j + 1) * Rp + rl] = x;
@@ -294,14 +312,14 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
         if (elim && nr > 0 && cs < pw) {
             if (nr >= NT) {
                 for (int rl = r0 + tid; rl < nloc; rl += NT) {
-                    const double l = slab[j * Rp + rl];
+                    const T l = slab[j * Rp + rl];
                     for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             } else {
                 const int ng = NT / nr, grp = tid / nr;
                 if (grp < ng) {
                     const int rl = r0 + tid - grp * nr;
-                    const double l = slab[j * Rp + rl];
+                    const T l = slab[j * Rp + rl];
                     for (int c = cs + grp; c < pw; c += ng) slab[c * Rp + rl] = fma(-l, prow[c], slab[c * Rp + rl]);
                 }
             }
@@ -310,7 +328,7 @@ __global__ void __launch_bounds__(NT) lu_panel_kernel(LuArgs a) {
     }
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
-        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = slab[c * Rp + rl];
+        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = (double)slab[c * Rp + rl];
     }
 }
 
@@ -713,6 +731,217 @@ __global__ void __launch_bounds__(NT) hh_panel_cluster_kernel(HhArgs a) {
     cl.sync();   // peers' shared memory stays alive until rank 0 has read it
 }
 
+// One panel of the row-pivoted LU on a single thread-block cluster, in FP32
+// (the reduced-precision Alg. 2 of BQRRP_PRECISION_MIXED_SKETCH32, when the
+// panel's rows fit the cluster's shared memory).  The arithmetic is that of
+// lu_panel_kernel<float> step for step -- the same first-maximum rule, the
+// same quotients and FMA updates of every row -- so the factors and pivots are
+// the same bits; only the exchange differs.  Each CTA publishes its candidate
+// (|value| key, row, signed value), the candidate's row and, if it owns it,
+// the next current row in its own shared memory (double-buffered by step
+// parity); one hardware cluster barrier per step (release / acquire) makes
+// them visible, and every CTA reads the others' through distributed shared
+// memory.  A buffer is rewritten two steps later, after a barrier that every
+// CTA reaches only once it has finished reading it.  No wait can hang: the
+// barriers are the cluster's own, reached by every CTA on every step.
+constexpr int kLuCluster = 16;
+constexpr int kMaxSmemLuCl = 200 * 1024;
+
+struct LuClArgs {
+    i64 N, jb, ldsk;
+    int pw, steps, R, Rp;
+    double* Sk;
+    i64* ipiv;
+};
+
+__global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    float* slab = (float*)slab_raw;               // [pw][Rp]
+    __shared__ float prow[64];
+    __shared__ float cand_row[2][64];             // this CTA's candidate row for a step
+    __shared__ float cur_row[2][64];              // the step's current row, if this CTA owns it
+    __shared__ unsigned long long cand_key[2];    // |value| bits of the candidate (0 with no candidate)
+    __shared__ long long cand_t[2];               // its row (kNoRow: none)
+    __shared__ unsigned int cand_vb[2];           // its signed value bits
+    __shared__ unsigned long long wk[NT / 32];
+    __shared__ long long wt[NT / 32];
+    __shared__ long long s_p;
+    __shared__ unsigned int s_pivbits;
+    __shared__ int s_gw;
+    __shared__ float s_rpiv;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), g = (int)cl.block_rank(), tid = threadIdx.x;
+    const i64 t0 = a.jb + (i64)g * a.R;
+    const i64 t1 = (t0 + a.R < a.N) ? t0 + a.R : a.N;
+    const int nloc = t1 > t0 ? (int)(t1 - t0) : 0;
+    const int pw = a.pw, Rp = a.Rp;
+
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int c = e % pw, rl = e / pw;
+        slab[c * Rp + rl] = (float)a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
+    }
+    __syncthreads();
+
+    // Publish the candidate for step k = j + 1 (j = -1: the first step) into
+    // buffer k & 1; columns > j + 1 of the rows still lack step j's update,
+    // applied here when elim is set (as lu_panel_kernel does).
+    auto publish = [&](int j, bool elim, Cand b) {
+        const int k = j + 1, buf = k & 1;
+        const i64 cur = a.jb + k;
+        if (b.t != kNoRow && tid < pw) {
+            const int r = (int)(b.t - t0), c = tid;
+            const float x = slab[c * Rp + r];
+            cand_row[buf][c] = (elim && c > j + 1) ? fmaf(-slab[j * Rp + r], prow[c], x) : x;
+        }
+        if (cur >= t0 && cur < t1 && tid >= 64 && tid < 64 + pw) {
+            const int r = (int)(cur - t0), c = tid - 64;
+            const float x = slab[c * Rp + r];
+            cur_row[buf][c] = (elim && c > j + 1) ? fmaf(-slab[j * Rp + r], prow[c], x) : x;
+        }
+        if (tid == 0) {
+            cand_key[buf] = b.key;
+            cand_t[buf] = b.t;
+            cand_vb[buf] = (b.t != kNoRow) ? __float_as_uint(slab[k * Rp + (int)(b.t - t0)]) : 0u;
+        }
+    };
+
+    {   // step 0 candidate: first maximum of |X(t, jb)| over the owned rows
+        Cand b{0, kNoRow};
+        for (int rl = tid; rl < nloc; rl += NT) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
+        b = block_best_all(b, wk, wt);
+        publish(-1, false, b);
+    }
+
+    for (int j = 0; j < a.steps; ++j) {
+        const i64 jg = a.jb + j;
+        const bool has_next = j + 1 < a.steps;
+        const int buf = j & 1;
+        cl.sync();   // every CTA's step-j candidate, candidate row and current row are visible
+        // (1) winner: largest |value|, then smallest row, over the C candidates
+        if (tid < 32) {
+            Cand w{0, kNoRow};
+            int wq = -1;
+            for (int q = tid; q < C; q += 32) {
+                const Cand z{*cl.map_shared_rank(&cand_key[buf], q), *cl.map_shared_rank(&cand_t[buf], q)};
+                if (z.t == kNoRow) continue;
+                const Cand y = better(w, z);
+                if (y.t != w.t) { w = y; wq = q; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const Cand y = shfl_down_cand(w, o);
+                const int yq = __shfl_down_sync(0xffffffffu, wq, o);
+                const Cand z = better(w, y);
+                if (z.t != w.t) { w = z; wq = yq; }
+            }
+            if (tid == 0) {
+                // a row t >= jg always exists, so some CTA has a candidate
+                s_p = (wq >= 0) ? w.t : jg;
+                s_gw = wq;
+                s_pivbits = (wq >= 0) ? *cl.map_shared_rank(&cand_vb[buf], wq) : 0u;
+                if (g == 0) a.ipiv[jg] = s_p;
+            }
+        }
+        __syncthreads();
+        const i64 p = s_p;
+        const int gw = s_gw;
+        const bool elim = gw >= 0 && (s_pivbits & 0x7fffffffu) != 0;   // exact zero pivot: no elimination
+        // (2) pivot row into prow and the slab; current row jg to the winner's place
+        if (gw >= 0 && tid < pw) {
+            const float pr = *cl.map_shared_rank(&cand_row[buf][tid], gw);
+            prow[tid] = pr;
+            if (jg >= t0 && jg < t1) slab[tid * Rp + (jg - t0)] = pr;
+            if (p != jg && p >= t0 && p < t1) {
+                const int og = (int)((jg - a.jb) / a.R);   // owner of row jg
+                slab[tid * Rp + (p - t0)] = *cl.map_shared_rank(&cur_row[buf][tid], og);
+            }
+        }
+        if (tid == 64 && elim) s_rpiv = 1.0f / __uint_as_float(s_pivbits);
+        __syncthreads();
+        // (3) multipliers (reciprocal plus one FMA correction: the rounded
+        // quotient) and column j+1 of the owned rows below jg; next candidate
+        const float rpiv = s_rpiv, pivv = __uint_as_float(s_pivbits);
+        const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
+        Cand b{0, kNoRow};
+        for (int rl = r0 + tid; rl < nloc; rl += NT) {
+            float l = 0.f;
+            if (elim) {
+                const float x = slab[j * Rp + rl];
+                l = x * rpiv;
+                l = fmaf(fmaf(-pivv, l, x), rpiv, l);
+                slab[j * Rp + rl] = l;
+            }
+            if (has_next) {
+                float x = slab[(j + 1) * Rp + rl];
+                if (elim) {
+                    x = fmaf(-l, prow[j + 1], x);
+                    slab[(j + 1) * Rp + rl] = x;
+                }
+                b = better(b, Cand{abs_key(x), t0 + rl});
+            }
+        }
+        if (has_next) {
+            b = block_best_all(b, wk, wt);
+            publish(j, elim, b);
+        }
+        __syncthreads();
+        // (4) bulk update of columns cs.. of the owned rows below jg
+        const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
+        if (elim && nr > 0 && cs < pw) {
+            if (nr >= NT) {
+                for (int rl = r0 + tid; rl < nloc; rl += NT) {
+                    const float l = slab[j * Rp + rl];
+                    for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fmaf(-l, prow[c], slab[c * Rp + rl]);
+                }
+            } else {
+                const int ng = NT / nr, grp = tid / nr;
+                if (grp < ng) {
+                    const int rl = r0 + tid - grp * nr;
+                    const float l = slab[j * Rp + rl];
+                    for (int c = cs + grp; c < pw; c += ng) slab[c * Rp + rl] = fmaf(-l, prow[c], slab[c * Rp + rl]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+    for (int e = tid; e < nloc * pw; e += NT) {
+        const int c = e % pw, rl = e / pw;
+        a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = (double)slab[c * Rp + rl];
+    }
+}
+
+// The panel on one cluster if its rows fit (R = ceil(rows / 16) rows per CTA);
+// returns -1 when they do not or the cluster cannot be launched.
+static int lu_panel_cluster(const Ctx& c, i64 N, i64 jb, int pw, int st, double* Sk, i64 ldsk, i64* ipiv) {
+    const i64 rows = N - jb;
+    const i64 R = cdiv(rows, kLuCluster);
+    const size_t smem = (size_t)pw * (size_t)(R | 1) * sizeof(float);
+    if (smem > (size_t)kMaxSmemLuCl) return -1;
+    BQ_TRY(kernel_attrs((const void*)lu_panel_cluster_kernel, kMaxSmemLuCl, true));
+    LuClArgs a{};
+    a.N = N; a.jb = jb; a.ldsk = ldsk; a.pw = pw; a.steps = st; a.R = (int)R; a.Rp = (int)(R | 1);
+    a.Sk = Sk; a.ipiv = ipiv;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kLuCluster);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kLuCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launch();
+    if (cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel, a) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return 0;
+}
+
 int coop_grid(const void* kernel, size_t smem, const Ctx& c, int want) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem) != cudaSuccess || per_sm < 1)
@@ -762,7 +991,10 @@ int getrf_pivots_ex(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv,
                     int stall_cta) {
     const i64 steps = imin(N, d);
     if (steps <= 0) return 0;
-    BQ_TRY(kernel_attrs((const void*)lu_panel_kernel, kMaxSmemLu));
+    // c.sketch32: the panels' pivot search and eliminations in FP32
+    const void* kfn = c.sketch32 ? (const void*)lu_panel_kernel<float> : (const void*)lu_panel_kernel<double>;
+    const size_t esz = c.sketch32 ? sizeof(float) : sizeof(double);
+    BQ_TRY(kernel_attrs(kfn, kMaxSmemLu));
     const i64 nbmax = 64;
     const int Gmax_all = (int)imin(c.dev.sms, 148);
     size_t need = 0;
@@ -776,34 +1008,39 @@ int getrf_pivots_ex(const Ctx& c, i64 N, i64 d, double* Sk, i64 ldsk, i64* ipiv,
         const int pw = (int)imin(nbmax, d - jb);
         const int st = (int)imin(nbmax, steps - jb);
         const i64 rows = N - jb;
-        // CTAs: one slab of >= 16 rows each, at most one per SM
-        int G = (int)imin(cdiv(rows, 16), Gmax_all);
-        i64 R = cdiv(rows, G);
-        size_t smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
-        if (smem > (size_t)kMaxSmemLu) {
-            set_error("getrf_pivots: %lld rows exceed the panel capacity", (long long)rows);
-            return BQRRP_EUNSUPPORTED;
+        // FP32 panels that fit one cluster exchange pivots through distributed
+        // shared memory; the others take the grid kernel
+        const bool on_cluster = c.sketch32 && lu_panel_cluster(c, N, jb, pw, st, Sk, ldsk, ipiv) == 0;
+        if (!on_cluster) {
+            // CTAs: one slab of >= 16 rows each, at most one per SM
+            int G = (int)imin(cdiv(rows, 16), Gmax_all);
+            i64 R = cdiv(rows, G);
+            size_t smem = (size_t)pw * (size_t)(R | 1) * esz;
+            if (smem > (size_t)kMaxSmemLu) {
+                set_error("getrf_pivots: %lld rows exceed the panel capacity", (long long)rows);
+                return BQRRP_EUNSUPPORTED;
+            }
+            const int Gc = coop_grid(kfn, smem, c, G);
+            if (Gc < G) {
+                G = Gc;
+                if (G < 1) { set_error("getrf_pivots: no co-resident grid"); return BQRRP_ECUDA; }
+                R = cdiv(rows, G);
+                smem = (size_t)pw * (size_t)(R | 1) * esz;
+                if (smem > (size_t)kMaxSmemLu) { set_error("getrf_pivots: panel too tall"); return BQRRP_EUNSUPPORTED; }
+            }
+            G = (int)cdiv(rows, R);   // drop CTAs that would own no rows
+            LuArgs a{};
+            a.N = N; a.jb = jb; a.ldsk = ldsk; a.pw = pw; a.steps = st; a.R = (int)R; a.Rp = (int)(R | 1);
+            a.Sk = Sk; a.ipiv = ipiv; a.st = c.st;
+            a.slot = reinterpret_cast<unsigned long long*>(c.coop);
+            a.cand_row = c.coop + 6 * (size_t)G;
+            a.cur_row = c.coop + 6 * (size_t)G + 3 * (size_t)G * pw;
+            a.poll_limit = poll_limit;
+            a.stall_cta = (jb == 0 && stall_cta < G) ? stall_cta : -1;
+            // every slot starts unpublished (all-ones) in each launch
+            BQ_CUDA(cudaMemsetAsync(a.slot, 0xff, 6 * (size_t)G * sizeof(unsigned long long), c.stream));
+            BQ_TRY(launch_coop(c, kfn, G, smem, &a));
         }
-        const int Gc = coop_grid((const void*)lu_panel_kernel, smem, c, G);
-        if (Gc < G) {
-            G = Gc;
-            if (G < 1) { set_error("getrf_pivots: no co-resident grid"); return BQRRP_ECUDA; }
-            R = cdiv(rows, G);
-            smem = (size_t)pw * (size_t)(R | 1) * sizeof(double);
-            if (smem > (size_t)kMaxSmemLu) { set_error("getrf_pivots: panel too tall"); return BQRRP_EUNSUPPORTED; }
-        }
-        G = (int)cdiv(rows, R);   // drop CTAs that would own no rows
-        LuArgs a{};
-        a.N = N; a.jb = jb; a.ldsk = ldsk; a.pw = pw; a.steps = st; a.R = (int)R; a.Rp = (int)(R | 1);
-        a.Sk = Sk; a.ipiv = ipiv; a.st = c.st;
-        a.slot = reinterpret_cast<unsigned long long*>(c.coop);
-        a.cand_row = c.coop + 6 * (size_t)G;
-        a.cur_row = c.coop + 6 * (size_t)G + 3 * (size_t)G * pw;
-        a.poll_limit = poll_limit;
-        a.stall_cta = (jb == 0 && stall_cta < G) ? stall_cta : -1;
-        // every slot starts unpublished (all-ones) in each launch
-        BQ_CUDA(cudaMemsetAsync(a.slot, 0xff, 6 * (size_t)G * sizeof(unsigned long long), c.stream));
-        BQ_TRY(launch_coop(c, (const void*)lu_panel_kernel, G, smem, &a));
         const i64 below = d - (jb + pw);
         if (d - pw > 0) {
             lu_swap_rows_kernel<<<(unsigned)cdiv(d - pw, kSwapRows), 256, 0, c.stream>>>(pw, d, jb, st, ipiv, Sk,

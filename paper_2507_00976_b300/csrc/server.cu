@@ -161,6 +161,7 @@ struct Server {
     int flags = 0;
     double dry_gflops = 1000.0;
     bool dry = false;
+    bool mixed = false;                           // large lane in BQRRP_PRECISION_MIXED
     int device = 0;
     static constexpr int kWorkers = 3;          // 0: small lane; 1, 2: large lane
     char* base = nullptr;                         // request arena, then workspace arena
@@ -324,7 +325,9 @@ int Server::do_large(Req* q, int wk) {
     double* rn = (double*)w;     w += up(sizeof(double) * (size_t)std::max<i64>(n, 1));
     int64_t* trd = (int64_t*)w;  w += up(sizeof(int64_t));
     const size_t have = lane_ws - (size_t)(w - wsbase[wk]);
-    const size_t need = bqrrp_workspace_query(m, n, q->r.b, q->r.d, nullptr);
+    bqrrp_opts o{};
+    o.precision = mixed ? BQRRP_PRECISION_MIXED : BQRRP_PRECISION_FP64;
+    const size_t need = bqrrp_workspace_query(m, n, q->r.b, q->r.d, &o);
     if (need > have) {
         set_error("large request needs %zu workspace bytes, the arena has %zu", need, have);
         return BQRRP_ENOMEM;
@@ -332,7 +335,7 @@ int Server::do_large(Req* q, int wk) {
     norm_partial_kernel<<<kNormParts, 256, 0, st[wk]>>>(A, m * n, part);
     BQ_LAUNCH_CHECK();
     int64_t rank = 0;
-    int rc = bqrrp_factor(m, n, A, m, q->r.b, q->r.d, q->r.seed, J, tau, &rank, nullptr, w, have, st[wk]);
+    int rc = bqrrp_factor(m, n, A, m, q->r.b, q->r.d, q->r.seed, J, tau, &rank, &o, w, have, st[wk]);
     if (rc != 0) return rc;
     if (rank > 0) {
         rownorm_kernel<<<(unsigned)cdiv(rank, 128), 128, 0, st[wk]>>>(A, m, n, rank, rn);
@@ -451,6 +454,7 @@ int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t works
         return -2;
     }
     if (!(trunc_tol >= 0.0)) { bq::set_error("trunc_tol < 0"); return -4; }
+    if (flags & ~(BQRRP_SERVER_DRYRUN | BQRRP_SERVER_MIXED)) { bq::set_error("unknown flags"); return -6; }
     auto* h = new bqrrp_server_s();
     bq::Server& S = h->s;
     S.budget = hbm_budget_bytes & ~(bq::kAlign - 1);
@@ -460,6 +464,7 @@ int bqrrp_server_create(bqrrp_server* out, size_t hbm_budget_bytes, size_t works
     S.small_max = small_max_elems;
     S.flags = flags;
     S.dry = (flags & BQRRP_SERVER_DRYRUN) != 0;
+    S.mixed = (flags & BQRRP_SERVER_MIXED) != 0;
     S.dry_gflops = dry_gflops > 0.0 ? dry_gflops : 1000.0;
     S.arena = bq::FreeList(S.budget - S.ws_bytes);
     S.t0 = std::chrono::steady_clock::now();

@@ -32,9 +32,11 @@ def make_requests():
     return reqs
 
 
-def test_server_matches_direct_calls_and_oracle():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_server_matches_direct_calls_and_oracle(mixed):
+    """mixed: the large lane factors with BQRRP_PRECISION_MIXED (BQRRP_SERVER_MIXED)."""
     reqs = make_requests()
-    S = B.Server(2048 * MiB, 256 * MiB, trunc_tol=TOL, small_max_elems=1 << 17)
+    S = B.Server(2048 * MiB, 256 * MiB, trunc_tol=TOL, small_max_elems=1 << 17, mixed=mixed)
     outs = {}
     order = np.random.default_rng(1).permutation(len(reqs))
     for k in order:
@@ -65,7 +67,7 @@ def test_server_matches_direct_calls_and_oracle():
             assert np.array_equal(jo, np_(J)) and np.array_equal(to, np_(T))
             assert c["rank"] == int(np_(rk)[0]) and c["trunc_rank"] == int(np_(tr)[0])
         else:
-            F, J, T, rk = bq.factor(r["A"], r["b"], r["d"], r["seed"])
+            F, J, T, rk = bq.factor(r["A"], r["b"], r["d"], r["seed"], precision="mixed" if mixed else "fp64")
             torch.cuda.synchronize()
             assert np.array_equal(Ao, np_(F)) and np.array_equal(jo, np_(J)) and np.array_equal(to, np_(T))
             assert c["rank"] == rk
@@ -74,7 +76,7 @@ def test_server_matches_direct_calls_and_oracle():
                 R = np.triu(Ao)[:rk]
                 i = min(want, c["trunc_rank"])
                 assert abs(np.linalg.norm(R[i:, i:]) - TOL * np.linalg.norm(r["A"])) <= 1e-9 * TOL * np.linalg.norm(r["A"])
-    for r in reqs[:4]:
+    for r in reqs[:5]:   # both lanes
         Ao, jo, to = outs[r["id"]]
         res, orth, ok = metrics(r["A"], Ao, jo, to, done[r["id"]]["rank"])
         assert ok and res <= 1e-12 and orth <= 1e-12
