@@ -694,11 +694,26 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
         } else {
             // ---- Alg. 3: precondition, Cholesky QR, reconstruction, R11 (written back)
             pr.begin(P_PANEL);
+            // With the FP32 sketch QRCP, R11's columns k.. (when the block keeps
+            // k < w columns) would come from the FP32 R^sk; they are formed
+            // instead from the panel's own columns, saved here, as Q^T A.
+            if (c.sketch32)
+                BQ_CUDA(cudaMemcpy2DAsync(B.stage, sizeof(double) * B.ldst, Ap, sizeof(double) * lda,
+                                          sizeof(double) * rows, w, cudaMemcpyDeviceToDevice, c.stream));
             {
                 Ctx cp = c;
                 cp.mixed = false;   // preconditioner, Gram, Cholesky, reconstruction, tau and R stay in FP64
                 BQ_TRY(cholqr_panel_steps(cp, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D,
                                           B.bb, tau + s));
+            }
+            if (c.sketch32 && k > 0 && k < w) {
+                // R(0:k, k:w) = the first k rows of (I - Y T Y^T)^T A(:, k:w), in FP64
+                double* Sk0 = B.stage + k * B.ldst;
+                BQ_TRY(dgemm(c, true, false, k, w - k, rows, 1.0, B.Ypan, m, Sk0, B.ldst, 0.0, B.W, B.wrows));
+                BQ_TRY(dgemm(c, true, false, k, w - k, k, 1.0, B.Tb, B.bb, B.W, B.wrows, 0.0, B.W2, B.wrows));
+                BQ_TRY(dgemm(c, false, false, k, w - k, k, -1.0, B.Ypan, m, B.W2, B.wrows, 1.0, Sk0, B.ldst));
+                BQ_CUDA(cudaMemcpy2DAsync(Ap + k * lda, sizeof(double) * lda, Sk0, sizeof(double) * B.ldst,
+                                          sizeof(double) * k, w - k, cudaMemcpyDeviceToDevice, c.stream));
             }
             {
                 const double r = (double)rows, kk = (double)k;

@@ -741,10 +741,16 @@ __global__ void __launch_bounds__(NT) hh_panel_cluster_kernel(HhArgs a) {
 // the next current row in its own shared memory (double-buffered by step
 // parity); one hardware cluster barrier per step (release / acquire) makes
 // them visible, and every CTA reads the others' through distributed shared
-// memory.  A buffer is rewritten two steps later, after a barrier that every
-// CTA reaches only once it has finished reading it.  No wait can hang: the
-// barriers are the cluster's own, reached by every CTA on every step.
+// memory.  The barrier is split: a CTA arrives as soon as it has published
+// (before its bulk elimination, which so overlaps the barrier) and waits at the
+// top of the next step.  A buffer is rewritten two steps later, after a wait
+// that completes only once every CTA has finished reading it.  No wait can
+// hang: the barriers are the cluster's own, reached by every CTA on every step.
 constexpr int kLuCluster = 16;
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 constexpr int kMaxSmemLuCl = 200 * 1024;
 
 struct LuClArgs {
@@ -760,6 +766,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
     __shared__ float prow[64];
     __shared__ float cand_row[2][64];             // this CTA's candidate row for a step
     __shared__ float cur_row[2][64];              // the step's current row, if this CTA owns it
+    __shared__ float cur_loc[64];                 // the step's current row, fetched from its owner
     __shared__ unsigned long long cand_key[2];    // |value| bits of the candidate (0 with no candidate)
     __shared__ long long cand_t[2];               // its row (kNoRow: none)
     __shared__ unsigned int cand_vb[2];           // its signed value bits
@@ -810,37 +817,48 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
         for (int rl = tid; rl < nloc; rl += NT) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
         b = block_best_all(b, wk, wt);
         publish(-1, false, b);
+        __syncthreads();
+        cluster_arrive_release();
     }
 
     for (int j = 0; j < a.steps; ++j) {
         const i64 jg = a.jb + j;
         const bool has_next = j + 1 < a.steps;
         const int buf = j & 1;
-        cl.sync();   // every CTA's step-j candidate, candidate row and current row are visible
+        cluster_wait_acquire();   // every CTA's step-j candidate, candidate row and current row are visible
         // (1) winner: largest |value|, then smallest row, over the C candidates
+        // (key, row and signed value read in one round of remote loads); warps
+        // 2-3 meanwhile fetch the current row jg from its owner
         if (tid < 32) {
             Cand w{0, kNoRow};
             int wq = -1;
+            unsigned int wvb = 0u;
             for (int q = tid; q < C; q += 32) {
-                const Cand z{*cl.map_shared_rank(&cand_key[buf], q), *cl.map_shared_rank(&cand_t[buf], q)};
-                if (z.t == kNoRow) continue;
-                const Cand y = better(w, z);
-                if (y.t != w.t) { w = y; wq = q; }
+                const unsigned long long kq = *cl.map_shared_rank(&cand_key[buf], q);
+                const long long tq = *cl.map_shared_rank(&cand_t[buf], q);
+                const unsigned int vq = *cl.map_shared_rank(&cand_vb[buf], q);
+                if (tq == kNoRow) continue;
+                const Cand y = better(w, Cand{kq, tq});
+                if (y.t != w.t) { w = y; wq = q; wvb = vq; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const Cand y = shfl_down_cand(w, o);
                 const int yq = __shfl_down_sync(0xffffffffu, wq, o);
+                const unsigned int yvb = __shfl_down_sync(0xffffffffu, wvb, o);
                 const Cand z = better(w, y);
-                if (z.t != w.t) { w = z; wq = yq; }
+                if (z.t != w.t) { w = z; wq = yq; wvb = yvb; }
             }
             if (tid == 0) {
                 // a row t >= jg always exists, so some CTA has a candidate
                 s_p = (wq >= 0) ? w.t : jg;
                 s_gw = wq;
-                s_pivbits = (wq >= 0) ? *cl.map_shared_rank(&cand_vb[buf], wq) : 0u;
+                s_pivbits = (wq >= 0) ? wvb : 0u;
                 if (g == 0) a.ipiv[jg] = s_p;
             }
+        } else if (tid >= 64 && tid < 64 + pw) {
+            const int og = (int)((jg - a.jb) / a.R);   // owner of row jg
+            cur_loc[tid - 64] = *cl.map_shared_rank(&cur_row[buf][tid - 64], og);
         }
         __syncthreads();
         const i64 p = s_p;
@@ -851,10 +869,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
             const float pr = *cl.map_shared_rank(&cand_row[buf][tid], gw);
             prow[tid] = pr;
             if (jg >= t0 && jg < t1) slab[tid * Rp + (jg - t0)] = pr;
-            if (p != jg && p >= t0 && p < t1) {
-                const int og = (int)((jg - a.jb) / a.R);   // owner of row jg
-                slab[tid * Rp + (p - t0)] = *cl.map_shared_rank(&cur_row[buf][tid], og);
-            }
+            if (p != jg && p >= t0 && p < t1) slab[tid * Rp + (p - t0)] = cur_loc[tid];
         }
         if (tid == 64 && elim) s_rpiv = 1.0f / __uint_as_float(s_pivbits);
         __syncthreads();
@@ -885,6 +900,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
             publish(j, elim, b);
         }
         __syncthreads();
+        cluster_arrive_release();   // published (or, on the last step, done reading)
         // (4) bulk update of columns cs.. of the owned rows below jg
         const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
         if (elim && nr > 0 && cs < pw) {
@@ -904,7 +920,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
         }
         __syncthreads();
     }
-    cl.sync();   // no CTA leaves while another may still read its shared memory
+    cluster_wait_acquire();   // no CTA leaves while another may still read its shared memory
     for (int e = tid; e < nloc * pw; e += NT) {
         const int c = e % pw, rl = e / pw;
         a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = (double)slab[c * Rp + rl];
