@@ -128,7 +128,8 @@ __device__ inline Cand shfl_down_cand(Cand x, int o) {
 
 // Block-wide first maximum; every thread returns the same result.  wk/wt hold
 // one entry per warp and are rewritten only after a later __syncthreads.
-__device__ inline Cand block_best_all(Cand x, unsigned long long* wk, long long* wt) {
+template <int NTB>
+__device__ inline Cand block_best_all_n(Cand x, unsigned long long* wk, long long* wt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = better(x, shfl_down_cand(x, o));
@@ -136,8 +137,11 @@ __device__ inline Cand block_best_all(Cand x, unsigned long long* wk, long long*
     __syncthreads();
     Cand r{wk[0], wt[0]};
 #pragma unroll
-    for (int q = 1; q < NT / 32; ++q) r = better(r, Cand{wk[q], wt[q]});
+    for (int q = 1; q < NTB / 32; ++q) r = better(r, Cand{wk[q], wt[q]});
     return r;
+}
+__device__ inline Cand block_best_all(Cand x, unsigned long long* wk, long long* wt) {
+    return block_best_all_n<NT>(x, wk, wt);
 }
 
 // T: the panel's arithmetic.  The sketch Sk stays FP64 in memory; with float
@@ -747,6 +751,7 @@ __global__ void __launch_bounds__(NT) hh_panel_cluster_kernel(HhArgs a) {
 // that completes only once every CTA has finished reading it.  No wait can
 // hang: the barriers are the cluster's own, reached by every CTA on every step.
 constexpr int kLuCluster = 16;
+constexpr int NTC = 256;    // threads per CTA (1024 measured slower: the step is bound by its barriers)
 __device__ __forceinline__ void cluster_arrive_release() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
@@ -760,7 +765,7 @@ struct LuClArgs {
     i64* ipiv;
 };
 
-__global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
+__global__ void __launch_bounds__(NTC) lu_panel_cluster_kernel(LuClArgs a) {
     extern __shared__ __align__(16) unsigned char slab_raw[];
     float* slab = (float*)slab_raw;               // [pw][Rp]
     __shared__ float prow[64];
@@ -770,8 +775,8 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
     __shared__ unsigned long long cand_key[2];    // |value| bits of the candidate (0 with no candidate)
     __shared__ long long cand_t[2];               // its row (kNoRow: none)
     __shared__ unsigned int cand_vb[2];           // its signed value bits
-    __shared__ unsigned long long wk[NT / 32];
-    __shared__ long long wt[NT / 32];
+    __shared__ unsigned long long wk[NTC / 32];
+    __shared__ long long wt[NTC / 32];
     __shared__ long long s_p;
     __shared__ unsigned int s_pivbits;
     __shared__ int s_gw;
@@ -783,7 +788,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
     const int nloc = t1 > t0 ? (int)(t1 - t0) : 0;
     const int pw = a.pw, Rp = a.Rp;
 
-    for (int e = tid; e < nloc * pw; e += NT) {
+    for (int e = tid; e < nloc * pw; e += NTC) {
         const int c = e % pw, rl = e / pw;
         slab[c * Rp + rl] = (float)a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk];
     }
@@ -814,8 +819,8 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
 
     {   // step 0 candidate: first maximum of |X(t, jb)| over the owned rows
         Cand b{0, kNoRow};
-        for (int rl = tid; rl < nloc; rl += NT) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
-        b = block_best_all(b, wk, wt);
+        for (int rl = tid; rl < nloc; rl += NTC) b = better(b, Cand{abs_key(slab[rl]), t0 + rl});
+        b = block_best_all_n<NTC>(b, wk, wt);
         publish(-1, false, b);
         __syncthreads();
         cluster_arrive_release();
@@ -878,7 +883,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
         const float rpiv = s_rpiv, pivv = __uint_as_float(s_pivbits);
         const int r0 = (jg + 1 > t0) ? (int)(jg + 1 - t0) : 0;
         Cand b{0, kNoRow};
-        for (int rl = r0 + tid; rl < nloc; rl += NT) {
+        for (int rl = r0 + tid; rl < nloc; rl += NTC) {
             float l = 0.f;
             if (elim) {
                 const float x = slab[j * Rp + rl];
@@ -896,7 +901,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
             }
         }
         if (has_next) {
-            b = block_best_all(b, wk, wt);
+            b = block_best_all_n<NTC>(b, wk, wt);
             publish(j, elim, b);
         }
         __syncthreads();
@@ -904,13 +909,13 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
         // (4) bulk update of columns cs.. of the owned rows below jg
         const int nr = nloc - r0, cs = has_next ? j + 2 : j + 1;
         if (elim && nr > 0 && cs < pw) {
-            if (nr >= NT) {
-                for (int rl = r0 + tid; rl < nloc; rl += NT) {
+            if (nr >= NTC) {
+                for (int rl = r0 + tid; rl < nloc; rl += NTC) {
                     const float l = slab[j * Rp + rl];
                     for (int c = cs; c < pw; ++c) slab[c * Rp + rl] = fmaf(-l, prow[c], slab[c * Rp + rl]);
                 }
             } else {
-                const int ng = NT / nr, grp = tid / nr;
+                const int ng = NTC / nr, grp = tid / nr;
                 if (grp < ng) {
                     const int rl = r0 + tid - grp * nr;
                     const float l = slab[j * Rp + rl];
@@ -921,7 +926,7 @@ __global__ void __launch_bounds__(NT) lu_panel_cluster_kernel(LuClArgs a) {
         __syncthreads();
     }
     cluster_wait_acquire();   // no CTA leaves while another may still read its shared memory
-    for (int e = tid; e < nloc * pw; e += NT) {
+    for (int e = tid; e < nloc * pw; e += NTC) {
         const int c = e % pw, rl = e / pw;
         a.Sk[(a.jb + c) + (t0 + rl) * a.ldsk] = (double)slab[c * Rp + rl];
     }
@@ -940,7 +945,7 @@ static int lu_panel_cluster(const Ctx& c, i64 N, i64 jb, int pw, int st, double*
     a.Sk = Sk; a.ipiv = ipiv;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kLuCluster);
-    cfg.blockDim = dim3(NT);
+    cfg.blockDim = dim3(NTC);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = c.stream;
     cudaLaunchAttribute at[1];
@@ -1241,8 +1246,8 @@ __device__ __forceinline__ bool sq_nonneg(float x) {
     return b >= 0 || b == (int)0x80000000u;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
+template <typename T, int NTQ>
+__global__ void __launch_bounds__(NTQ) small_qr_cluster_kernel(i64 d, i64 s, double* W) {
     extern __shared__ __align__(16) unsigned char loc_raw[];
     T* loc = (T*)loc_raw;                           // [ncl][d] local columns
     __shared__ T vbuf[2][kSqrMaxD];
@@ -1255,7 +1260,7 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     const int ncl = (int)((s - g + C - 1) / C);    // columns g, g + C, ... below s
     for (int lc = 0; lc < ncl; ++lc) {
         const i64 gc = (i64)lc * C + g;
-        for (i64 r = tid; r < d; r += NT) loc[(i64)lc * d + r] = (T)W[r + gc * d];
+        for (i64 r = tid; r < d; r += NTQ) loc[(i64)lc * d + r] = (T)W[r + gc * d];
     }
     __syncthreads();
 
@@ -1317,7 +1322,7 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
         const T* vsrc = cl.map_shared_rank(&vbuf[par][0], o);
         const T scal = *cl.map_shared_rank(&s_scal[par], o);
         const T tau = *cl.map_shared_rank(&s_tau[par], o);
-        for (i64 r = j + tid; r < d; r += NT) vloc[r] = (r == j) ? T(1) : vsrc[r] * scal;
+        for (i64 r = j + tid; r < d; r += NTQ) vloc[r] = (r == j) ? T(1) : vsrc[r] * scal;
         __syncthreads();
         const bool live = sq_nonzero(tau);
         const bool next_here = j + 1 < s && (int)((j + 1) % C) == g;
@@ -1352,7 +1357,7 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
             }
         }
         if (live) {
-            const int w0 = next_here ? 2 : 0, nw = NT / 32 - w0;
+            const int w0 = next_here ? 2 : 0, nw = NTQ / 32 - w0;
             if (warp >= w0) {
                 for (int lc = warp - w0; lc < ncl; lc += nw) {
                     const i64 gc = (i64)lc * C + g;
@@ -1365,7 +1370,7 @@ __global__ void __launch_bounds__(NT) small_qr_cluster_kernel(i64 d, i64 s, doub
     }
     for (int lc = 0; lc < ncl; ++lc) {
         const i64 gc = (i64)lc * C + g;
-        for (i64 r = tid; r < d; r += NT) W[r + gc * d] = (r <= gc) ? (double)loc[(i64)lc * d + r] : 0.0;
+        for (i64 r = tid; r < d; r += NTQ) W[r + gc * d] = (r <= gc) ? (double)loc[(i64)lc * d + r] : 0.0;
     }
     cl.sync();    // no CTA leaves while another may still read its shared memory
 }
@@ -1378,7 +1383,10 @@ int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
     int C = 16;
     size_t smem = (size_t)((s + C - 1) / C) * (size_t)d * sizeof(double);
     if (smem > 208 * 1024) return -1;
-    const void* fn = c.sketch32 ? (const void*)small_qr_cluster_kernel<float> : (const void*)small_qr_cluster_kernel<double>;
+    // 256 threads in either precision (1024 measured slower for FP32: each
+    // step is bound by its cluster barrier and the owner's reflector chain)
+    const void* fn = c.sketch32 ? (const void*)small_qr_cluster_kernel<float, NT>
+                                : (const void*)small_qr_cluster_kernel<double, NT>;
     if (c.sketch32) smem /= 2;
     BQ_TRY(kernel_attrs(fn, 208 * 1024, true));
     cudaLaunchConfig_t cfg = {};
@@ -1394,8 +1402,8 @@ int small_qr_cluster(const Ctx& c, i64 d, i64 s, double* W) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     count_launch();
-    const cudaError_t le = c.sketch32 ? cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<float>, d, s, W)
-                                      : cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<double>, d, s, W);
+    const cudaError_t le = c.sketch32 ? cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<float, NT>, d, s, W)
+                                      : cudaLaunchKernelEx(&cfg, small_qr_cluster_kernel<double, NT>, d, s, W);
     if (le != cudaSuccess) {
         cudaGetLastError();
         return -1;
