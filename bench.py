@@ -41,9 +41,9 @@ SM_MAX_MHZ = 2032.0
 # FP64: 2 DFMA per clock per SM (the measured DFMA rate is 1.82-1.97 per clock
 # per SM; tcgen05 has no f64 kind), 2 FLOP per DFMA.
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# the FP64-accurate tensor-core product runs 36 bf16 slice products per FP64
-# product (eight 7-bit slices per operand, the pairs with p + q <= 7)
-OZ_PRODUCTS = 36
+# the FP64-accurate tensor-core product runs 28 bf16 slice products per FP64
+# product (seven balanced 8-bit slices per operand, the pairs with p + q <= 6)
+OZ_PRODUCTS = 28
 
 
 def bf16_peak():
@@ -59,7 +59,7 @@ def bf16_peak():
 
 
 def mixed_roofline(fp64eq_tflops):
-    """Tensor roofline of the slice GEMM: bf16 work = 36 x the FP64-equivalent rate."""
+    """Tensor roofline of the slice GEMM: bf16 work = 28 x the FP64-equivalent rate."""
     if not fp64eq_tflops:
         return None
     peak, src = bf16_peak()
@@ -70,7 +70,7 @@ def mixed_roofline(fp64eq_tflops):
                                         "accumulators in all 512 TMEM columns, epilogue of one half overlapping the "
                                         "other half's MMAs)"),
             "fp64_equivalent_tflops": fp64eq_tflops, "peak_source": src,
-            "counting": "36 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
+            "counting": "28 bf16 slice products per FP64 product, all of them formed (no discarded products)"}
 
 
 # DRAM traffic of one trailing C -= Y.W2 launch (dgemm_kernel<0,0>, rows k.. of the
@@ -430,7 +430,7 @@ def run_gemm(a):
     line = {"metric": name, "value": tf, "unit": "TFLOP/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
             "config": {"M": M, "N": N, "K": K}, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}
     if a.only == "ozaki":
-        # 36 bf16 slice products per FP64 product
+        # OZ_PRODUCTS bf16 slice products per FP64 product
         line["bf16_tensor_tflops"] = OZ_PRODUCTS * tf
         line["roofline"] = mixed_roofline(tf)
     print(json.dumps(line), flush=True)
@@ -933,7 +933,7 @@ def main():
         mcalls = max(1, mprof["calls"])
         mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
-                 "arith": "FP64-accurate products on bf16 tensor cores (8 exact 7-bit slices, 36 pair products); "
+                 "arith": "FP64-accurate products on bf16 tensor cores (7 exact balanced 8-bit slices, 28 pair products); "
                           "LU, sketch QR, panel, tau, R in FP64",
                  "phases_ms": {p_: mprof[p_][0] / mcalls for p_ in B.PHASES}}
         # the variant with the sketch's QR factor in FP32 (pivots from the FP64 LU)

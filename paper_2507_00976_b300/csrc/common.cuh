@@ -263,7 +263,7 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
                        double* tau);
 
 // ozaki.cu (FP64-accurate products on the bf16 tensor cores)
-constexpr int kOzPlanes = 8;              // 7-bit slices per FP64 operand (56 bits)
+constexpr int kOzPlanes = 7;              // balanced 8-bit slices per FP64 operand (54-bit fixed point)
 constexpr i64 kOzMaxK = (i64)1 << 17;     // K per slice-GEMM launch (longer K is split)
 size_t ozaki_ws_bytes(i64 M, i64 N, i64 K, int sa);
 int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,

@@ -6,23 +6,25 @@
 // exactly from integer slices:
 //   * every row i of op(A) is scaled by 2^-ea_i and every column j of op(B) by
 //     2^-eb_j (ea_i, eb_j = exponent just above the row / column maximum);
-//   * the scaled value x is truncated to a 56-bit fixed-point integer X with
-//     integer bit operations, and X is cut into eight signed 7-bit slices
-//     q_0 .. q_7 (|q| <= 127, exact in bf16):  x ~ sum_p q_p 2^(e - 7 - 7p);
-//   * op(A) op(B) ~ sum_{p+q <= 7} 2^(ea_i + eb_j - 14 - 7(p+q)) (A_p B_q):
-//     the 36 slice products with p + q <= 7; the dropped pairs and the
-//     truncation together stay below about 2^-53 of max|row| * max|column| per
-//     term (FP64's own unit roundoff is 2^-53);
-//   * the products of one group t = p + q are summed on the tensor cores in
-//     FP32.  Every partial sum is an integer of magnitude below
-//     8 * Kc * 127^2 < 2^24 for a K chunk Kc = 128, so FP32 holds it exactly;
-//     after each chunk the eight group sums are combined exactly, rounded to a
-//     multiple of 2^dsh (dsh = ceil(log2 K) + 1) and added into one 64-bit
-//     integer per element (ozaki_tc.cu), which is rounded once to FP64 at the
-//     end.
-// The result matches an FP64 GEMM to a few units of roundoff (normwise).  A
-// sketch with +-1 entries is exact in one slice, so S*A needs only the eight
-// products S A_q.
+//   * the scaled value x is truncated to a 54-bit fixed-point integer X with
+//     integer bit operations, and X is written in seven balanced base-256
+//     digits q_0 .. q_6 in [-128, 127] (exact in bf16):
+//     x ~ 2^(e - 54) sum_p q_p 2^(8 (6 - p));
+//   * op(A) op(B) ~ 2^(ea_i + eb_j - 60) sum_{t <= 6} 2^(8 (6 - t)) G_t with
+//     G_t = sum_{p + q = t} A_p B_q: the 28 slice products with p + q <= 6; the
+//     dropped pairs and the truncation together stay below about 2^-53 of
+//     max|row| * max|column| per term (FP64's own unit roundoff is 2^-53);
+//   * the products of one group t are summed on the tensor cores in FP32.
+//     Every partial sum is an integer of magnitude at most 7 * Kc * 128^2 <
+//     2^24 for a K chunk Kc = 128, so FP32 holds it exactly; after each chunk
+//     the seven group sums are combined exactly, rounded to a multiple of
+//     2^dsh (dsh = ceil(log2 K) + 1) and added into one 64-bit integer per
+//     element (ozaki_tc.cu), which is rounded once to FP64 at the end.
+// Balanced digits halve the largest slice magnitude of unsigned 8-bit ones,
+// which is what lets eight bits per slice keep a 128-deep exact chunk.  The
+// result matches an FP64 GEMM to a few units of roundoff (normwise).  A sketch
+// with +-1 entries is exact in one slice, so S*A needs only the seven products
+// S A_q.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -31,7 +33,7 @@ namespace bq {
 
 namespace {
 
-constexpr int kSlices = kOzPlanes;   // 7-bit slices per FP64 operand (56 bits)
+constexpr int kSlices = kOzPlanes;   // balanced 8-bit slices per FP64 operand (54-bit fixed point)
 constexpr int OBM = 64, OBN = 32, OBK = 32;   // padding of the slice planes (rows, rows, k)
 
 __device__ __forceinline__ int exp_above(double m) {
@@ -42,13 +44,13 @@ __device__ __forceinline__ int exp_above(double m) {
     return e;
 }
 
-// x (|x| < 2^e) -> 56-bit fixed point X = trunc(x 2^(56-e)) using integer ops.
-__device__ __forceinline__ long long fixed56(double x, int e) {
+// x (|x| < 2^e) -> 54-bit fixed point X = trunc(x 2^(54-e)) using integer ops.
+__device__ __forceinline__ long long fixed54(double x, int e) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((bits >> 52) & 0x7FF);
     if (ex == 0) return 0;   // zero (subnormals are far below every slice)
     const long long mant = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    const int sh = ex - 1075 + 56 - e;   // <= 3 because |x| < 2^e
+    const int sh = ex - 1075 + 54 - e;   // <= 1 because |x| < 2^e
     long long X;
     if (sh >= 0) X = mant << sh;
     else if (sh > -63) X = mant >> (-sh);
@@ -101,13 +103,14 @@ __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ld
     for (int q = ty; q < 32; q += 8) {
         const i64 r = r0 + q, k = k0 + tx;
         if (r >= Rp || k >= ldk) continue;
-        const long long Xi = (r < R && k < K) ? fixed56(tile[q][tx], e[r]) : 0;
-        const unsigned long long a = (unsigned long long)(Xi < 0 ? -Xi : Xi);
-        const bool neg = Xi < 0;
+        long long X = (r < R && k < K) ? fixed54(tile[q][tx], e[r]) : 0;
+        // balanced digits from the least significant: q = ((X + 128) mod 256) - 128,
+        // then X = (X - q) / 256 exactly; |X| < 2^54 leaves |q_0| <= 65
 #pragma unroll
-        for (int p = 0; p < kSlices; ++p) {
-            const int v = (int)((a >> (49 - 7 * p)) & 127ull);
-            S[(size_t)p * slice + (size_t)r * ldk + k] = __int2bfloat16_rn(neg ? -v : v);
+        for (int p = kSlices - 1; p >= 0; --p) {
+            const int v = (int)((X + 128) & 255) - 128;
+            X = (X - v) >> 8;
+            S[(size_t)p * slice + (size_t)r * ldk + k] = __int2bfloat16_rn(v);
         }
     }
 }
@@ -204,7 +207,7 @@ constexpr i64 kSketchCols = 8192;
 size_t ozaki_sketch_ws_bytes(i64 d, i64 m, i64 n) { return ozaki_ws_bytes(d, imin(imax(n, 1), kSketchCols), m, 1); }
 
 // Msk = S A with the dense +-1 operator S (d x m) as one exact slice:
-// eight tensor-core products S A_q; FP32 sums of |+-1 * q| <= 127 over 2^17
+// seven tensor-core products S A_q; FP32 sums of |+-1 * q| <= 128 over 2^17
 // columns stay below 2^24, so one exact flush per 2^17 columns suffices.  A
 // is sliced and multiplied kSketchCols columns at a time (every column of Msk
 // depends only on its own column of A, so the blocking changes no bit).
@@ -226,8 +229,8 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     const unsigned blocks = (unsigned)imax(1, imin(cdiv(Mp * Kp, 256), 16LL * c.dev.sms));
     sketch_slice_kernel<<<blocks, 256, 0, c.stream>>>(d, m, Mp, Kp, seed, Ss);
     BQ_LAUNCH_CHECK();
-    // S has one slice q_0 = +-1 with weight 2^(ea - 7) = 1: ea = 7 on every row
-    fill_int_kernel<<<(unsigned)cdiv(Mp, 256), 256, 0, c.stream>>>(ea, Mp, 7);
+    // S has one slice q_0 = +-1 with weight 2^(ea - 54 + 48) = 1: ea = 6 on every row
+    fill_int_kernel<<<(unsigned)cdiv(Mp, 256), 256, 0, c.stream>>>(ea, Mp, 6);
     BQ_LAUNCH_CHECK();
     int* err = c.st ? &c.st->err_timeout : flag;
     if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));

@@ -2,31 +2,31 @@
 // the 5th-generation tensor cores: tcgen05.mma with operands staged in shared
 // memory by TMA and FP32 accumulators in tensor memory (TMEM).
 //
-// Operands are bf16 slice planes, K-contiguous: As[p][row][k] (p < SA; SA = 8
-// for an FP64 operand, 1 for the +-1 sketch) and Bs[q][col][k] (q < 8).  Every
-// slice is an integer in [-127, 127].  The product of planes p and q has
-// weight 2^-7(p+q); the pairs with p + q <= 7 are formed (36 of them for
-// SA = 8, 8 for the sketch) and the products of one group t = p + q are summed
+// Operands are bf16 slice planes, K-contiguous: As[p][row][k] (p < SA; SA = 7
+// for an FP64 operand, 1 for the +-1 sketch) and Bs[q][col][k] (q < 7).  Every
+// slice is an integer in [-128, 127].  The product of planes p and q has
+// weight 2^-8(p+q); the pairs with p + q <= 6 are formed (28 of them for
+// SA = 7, 7 for the sketch) and the products of one group t = p + q are summed
 // in one FP32 accumulator, exactly: within a K chunk of CL k blocks every
-// partial sum is an integer below 8 * 128 * 127^2 < 2^24 (SA = 8, CL = 2) or
-// 2^17 * 127 < 2^24 (sketch, CL = 2048).
+// partial sum is an integer of magnitude at most 7 * 128 * 128^2 < 2^24
+// (SA = 7, CL = 2) or 2^17 * 128 = 2^24 (sketch, CL = 2048).
 //
 // Tile: 128 rows x 64 columns; one persistent CTA per SM walks the tiles in
 // the grouped raster of tc_schedule.cuh.  TMEM (512 columns of 32 bits) holds
 // the tile's accumulators: column half h (C columns 32h .. 32h+31) owns TMEM
-// columns [256 h, 256 h + 256), group t of it [256 h + 32 t, + 32).
+// columns [256 h, 256 h + 256), group t of it [256 h + 32 t, + 32) (t < 7).
 //
-// Shared memory (225 KiB): eight A slots of one 128 x 64 plane tile (16 KiB,
-// 128-byte swizzled) and three B slots of one half-stage (the 8 planes of 32
-// columns x 64 k, 32 KiB), with full/empty mbarriers.
+// Shared memory (213 KiB): eight A slots of one 128 x 64 plane tile (16 KiB,
+// 128-byte swizzled) and three B slots of one half-stage (the 7 planes of 32
+// columns x 64 k, 28 KiB), with full/empty mbarriers.
 //
 // Warp roles (576 threads); the order of their work is tc_schedule.cuh's:
 //   warp 0      TMA producer (one thread): per 64-deep k block the B half of
 //               the first segment, the SA A planes, the B half of the second;
 //   warp 1      allocates the 512 TMEM columns; one thread issues the MMAs.
-//               Segment (k block, half h), A plane p: the B planes q = 0..7-p of
+//               Segment (k block, half h), A plane p: the B planes q = 0..6-p of
 //               the half lie back to back in its B slot, so one
-//               tcgen05.mma.kind::f16 (M = 128, N = 32 (8 - p), K = 16) whose
+//               tcgen05.mma.kind::f16 (M = 128, N = 32 (7 - p), K = 16) whose
 //               accumulator starts at TMEM column 256 h + 32 p lands plane q in
 //               group p + q; four such MMAs cover the k block.  The half whose
 //               chunk ends in a k block goes first, so the epilogue of one half
@@ -36,10 +36,10 @@
 //               each).  After each chunk a warp reads the eight groups with
 //               tcgen05.ld, zeroes them with tcgen05.st, releases the half and
 //               forms the chunk's exact value per element,
-//                 W = (sum_{t <= 3} G_t 2^(7(3-t))) 2^28 + sum_{t >= 4} G_t 2^(7(7-t)),
+//                 W = (sum_{t <= 2} G_t 2^(8(2-t))) 2^32 + sum_{t >= 3} G_t 2^(8(6-t)),
 //               rounded to a multiple of 2^dsh and added into one 64-bit
 //               integer; after a tile's last chunk (the half is already
-//               released for the next tile) C = alpha acc 2^(ea+eb-63+dsh) + beta C,
+//               released for the next tile) C = alpha acc 2^(ea+eb-60+dsh) + beta C,
 //               the integer rounded once to FP64 with integer operations.
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error
 // flag, the roles stop issuing work, in-flight copies and MMAs are waited for
@@ -56,12 +56,13 @@ namespace bq {
 namespace {
 
 constexpr int TC_M = 128, TC_N = 64, TC_HN = 32, TC_KB = 64;   // tile rows, columns, half columns, k block
-constexpr int TC_NP = 8;                                        // planes of op(B)
-constexpr int TC_NG = 8;                                        // groups t = 0..7
+constexpr int TC_NP = kOzPlanes;                                // planes of op(B)
+constexpr int TC_NG = kOzPlanes;                                // groups t = 0..6
 constexpr int TC_EPI = 16;                                      // epilogue warps
 constexpr int TC_THREADS = 64 + 32 * TC_EPI;
 constexpr int TC_APLANE = TC_M * TC_KB * 2;                     // 16 KiB per A slot
-constexpr int TC_BHALF = TC_NP * TC_HN * TC_KB * 2;             // 32 KiB per B slot
+constexpr int TC_BHALF = TC_NP * TC_HN * TC_KB * 2;             // 28 KiB per B slot
+static_assert(TC_BHALF % 1024 == 0, "B slots keep the 1024-byte swizzle alignment");
 constexpr int TC_NBAR = 2 * tcs::kNAS + 2 * tcs::kNBS + 2 + 2 + 1;
 constexpr size_t TC_SMEM =
     1024 + (size_t)tcs::kNAS * TC_APLANE + (size_t)tcs::kNBS * TC_BHALF + 8 * TC_NBAR + 16;
@@ -223,7 +224,7 @@ __device__ __forceinline__ double i64_scaled(long long w, int e) {
 
 struct TcArgs {
     tcs::Plan plan;
-    int dsh;   // bits dropped (rounded) from each chunk's sum: ceil(log2 K) + 1, at least 11
+    int dsh;   // bits dropped (rounded) from each chunk's sum: ceil(log2 K) - 2, at least 8
     i64 M, N;
     const int* ea;
     const int* eb;
@@ -301,7 +302,7 @@ struct MmaV {
     // units; every slot address stays below 2^18)
     __device__ __forceinline__ void mma(int, int, int h, int pl, int sa, int sb) {
         const uint64_t ad = ad0 + (uint64_t)(sa * (TC_APLANE >> 4));
-        const uint64_t bd = bd0 + (uint64_t)(sb * (TC_BHALF >> 4));   // planes 0 .. 7 - pl stacked along N
+        const uint64_t bd = bd0 + (uint64_t)(sb * (TC_BHALF >> 4));   // planes 0 .. 6 - pl stacked along N
         mma_f16_kblock(tmem + (uint32_t)(256 * h + TC_HN * pl), ad, bd, idesc_f16(TC_HN * (TC_NG - pl)));
     }
     __device__ __forceinline__ void release_a(int sa) { mma_commit(bar.empty_a(sa)); }
@@ -310,10 +311,12 @@ struct MmaV {
 };
 
 // Per element the epilogue keeps one 64-bit integer: the sum over chunks of
-// the chunk's exact value W (in units of 2^(ea+eb-63)) rounded to a multiple
-// of 2^dsh.  |sum| stays below K 2^63 / 2^dsh < 2^62, and the rounding adds at
-// most K/128 * 2^(dsh-1) units, under K 2^-53 max|A(i,:)| max|B(:,j)| for
-// K <= 2^17 (the launcher's limit): the normwise error of an FP64 GEMM.
+// the chunk's exact value W (in units of 2^(ea+eb-60)) rounded to a multiple
+// of 2^dsh.  One k term is at most 2^54 2^54 / 2^48 = 2^60 units, so |sum|
+// stays below K 2^60 / 2^dsh <= 2^62; the rounding adds at most
+// K/128 * 2^(dsh-1) units, about K^2 2^-70 of max|A(i,:)| max|B(:,j)|, below
+// K 2^-53 of it for K <= 2^17 (the launcher's limit): the normwise error of
+// an FP64 GEMM.
 struct EpilogueV {
     const TcArgs* p;
     Bars bar;
@@ -343,13 +346,13 @@ struct EpilogueV {
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = 0;
     }
-    // W = HI 2^28 + LO with HI = sum_{t <= 3} G_t 2^(7(3-t)) and
-    // LO = sum_{t >= 4} G_t 2^(7(7-t)), exact; the group sums obey
-    // |G_t| <= (t + 1) 128 127^2 < (t + 1) 2^21, so the pairs G_0 2^7 + G_1,
-    // G_2 2^7 + G_3, G_4 2^7 + G_5 and G_6 2^7 + G_7 fit in 32 bits.  Four
-    // columns at a time; HI 2^28 is a multiple of 2^dsh, so only LO is rounded.
+    // W = HI 2^32 + LO with HI = G_0 2^16 + G_1 2^8 + G_2 and
+    // LO = G_3 2^24 + G_4 2^16 + G_5 2^8 + G_6, exact in 64 bits: the group
+    // sums obey |G_t| <= (t + 1) 128^3 = (t + 1) 2^21 (or 2^24 for the sketch's
+    // 2^17-deep chunks), so |HI| < 2^41 and |LO| < 2^49.  Four columns at a
+    // time; HI 2^32 is a multiple of 2^dsh (dsh <= 15), so only LO is rounded.
     __device__ __forceinline__ void read_chunk(int) {
-        const int dsh = p->dsh, sh = 28 - dsh;
+        const int dsh = p->dsh, sh = 32 - dsh;
         const long long half = 1ll << (dsh - 1);
 #pragma unroll
         for (int cb = 0; cb < 4; ++cb) {
@@ -360,12 +363,10 @@ struct EpilogueV {
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int p01 = f2i(v[0][j]) * 128 + f2i(v[1][j]);
-                const int p23 = f2i(v[2][j]) * 128 + f2i(v[3][j]);
-                const int p45 = f2i(v[4][j]) * 128 + f2i(v[5][j]);
-                const int p67 = f2i(v[6][j]) * 128 + f2i(v[7][j]);
-                const long long hi = (long long)p01 * 16384 + p23;
-                const long long lo = (long long)p45 * 16384 + p67;
+                const long long hi =
+                    ((long long)f2i(v[0][j]) << 16) + ((long long)f2i(v[1][j]) << 8) + (long long)f2i(v[2][j]);
+                const long long lo = ((long long)f2i(v[3][j]) << 24) + ((long long)f2i(v[4][j]) << 16) +
+                                     ((long long)f2i(v[5][j]) << 8) + (long long)f2i(v[6][j]);
                 acc[4 * cb + j] += (hi << sh) + ((lo + half) >> dsh);
             }
         }
@@ -377,7 +378,7 @@ struct EpilogueV {
         tcs::tile_coords(p->plan, tile, &rt, &ct);
         const i64 row = (i64)rt * TC_M + 32 * lq + lane;
         if (row >= p->M) return;
-        const int er = p->ea[row] - 63 + p->dsh;
+        const int er = p->ea[row] - 60 + p->dsh;
         const double alpha = p->alpha, beta = p->beta;
         const i64 col0 = (i64)ct * TC_N + TC_HN * h + 16 * sub;
         const int ncol = (int)(p->N - col0 < 16 ? p->N - col0 : 16);
@@ -564,7 +565,7 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
     a.plan.grid = (int)imin(mt * nct, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
     int lg = 0;
     while (((i64)1 << lg) < kext) ++lg;
-    a.dsh = lg + 1 < 11 ? 11 : lg + 1;
+    a.dsh = lg - 2 < 8 ? 8 : lg - 2;
     if (SA == 1)
         ozaki_tc_kernel<1><<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
     else
@@ -575,9 +576,9 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
 
 }  // namespace
 
-// Slice products on tcgen05: the 8 x 8 FP64 split (the 36 pairs with
-// p + q <= 7, exact in chunks of two k blocks) and the +-1 sketch (one A
-// plane, eight B planes, exact in chunks of 2048 k blocks).
+// Slice products on tcgen05: the 7 x 7 FP64 split (the 28 pairs with
+// p + q <= 6, exact in chunks of two k blocks) and the +-1 sketch (one A
+// plane, seven B planes, exact in chunks of 2048 k blocks).
 // K beyond kOzMaxK runs as consecutive launches over K pieces, each adding
 // its FP64-rounded part into C.
 int ozaki_tc_gemm(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,

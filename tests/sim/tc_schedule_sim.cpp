@@ -228,14 +228,14 @@ int main(int argc, char** argv) {
         std::vector<std::vector<Step>> roles(18);
         ProdRec pr{S, roles[0]};
         MmaRec mr{S, roles[1]};
-        if (P.SA == 8) {
-            tcs::producer<8>(P, cta, pr);
-            tcs::mma_issuer<8>(P, cta, mr);
+        if (P.SA == 7) {
+            tcs::producer<7>(P, cta, pr);
+            tcs::mma_issuer<7>(P, cta, mr);
         } else if (P.SA == 1) {
             tcs::producer<1>(P, cta, pr);
             tcs::mma_issuer<1>(P, cta, mr);
         } else {
-            fail("SA must be 8 or 1");
+            fail("SA must be 7 or 1");
         }
         std::vector<EpiRec> ep;
         ep.reserve(16);

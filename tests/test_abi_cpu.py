@@ -23,20 +23,20 @@ def test_workspace_queries_are_consistent():
     assert 0 < small < big
     # dominant terms: 2 d n + 2 b n + m b + max(m, d) min(n, 2d) doubles, the
     # split-K partials (2048 n doubles), the bf16 slice planes of the dense
-    # sketch (8 planes of min(n, 8192) columns of A, one plane of S), plus
+    # sketch (7 planes of min(n, 8192) columns of A, one plane of S), plus
     # fixed scratch
     m, n, b, d = 32768, 32768, 1024, 1280
     est = 8 * (2 * d * n + m * b + 2 * b * n + max(m, d) * min(n, 2 * d) + 2048 * n)
-    est += 2 * 8 * m * min(n, 8192) + 2 * d * m
+    est += 2 * 7 * m * min(n, 8192) + 2 * d * m
     assert est <= big <= est + 256 * 2**20
     assert B.bqrrp_workspace_query(100, 200, 10, 12) == 0          # m < n
     assert B.bqrrp_workspace_query(100, 50, 0, 12) == 0            # b < 1
     assert B.bqrrp_workspace_query(100, 50, 10, 9) == 0            # d < b
     sparse = B.make_opts(B.SKETCH_SPARSE, 8)
     # the sparse sketch's index lists (24 bytes per operator entry) take less
-    # room than the dense sketch's slice planes (16 bytes per element of A)
+    # room than the dense sketch's slice planes (14 bytes per element of A)
     # (planes padded: k to 32, columns of A to 32, rows of S to 64)
-    dense_planes = 2 * 8 * 2016 * 1024 + 2 * 192 * 2016
+    dense_planes = 2 * 7 * 2016 * 1024 + 2 * 192 * 2016
     sparse_lists = 24 * 2000 * 8
     sp = B.bqrrp_workspace_query(2000, 1000, 128, 160, sparse)
     assert abs(sp - (small - dense_planes + sparse_lists)) <= 2**20

@@ -1,16 +1,18 @@
 """The mixed-precision form: FP64-accurate products on the bf16 tensor cores
-(exact 7-bit slices, FP32 sums that stay below 2^24, exact integer
+(exact balanced 8-bit slices, FP32 sums that stay below 2^24, exact integer
 recombination rounded once to FP64), through the C ABI.
 
 Bar: integer data, whose slice products are exact, must come out bit-exact.
 General data must stay within 8 K 2^-53 max|op(A)(i,:)| max|op(B)(:,j)| of the
-exact product: the splitting's error model is truncation below 2^-56 of the
-row / column maxima, the dropped slice pairs (p + q >= 8, below 2^-53.2 of
+exact product: the splitting's error model is truncation below 2^-54 of the
+row / column maxima, the dropped slice pairs (p + q >= 7, below 2^-53 of
 max|a| max|b| per term) and the rounding of each 128-deep chunk's sum (at most
-K/128 2^(dsh-1) 2^-63 relative, dsh = ceil(log2 K) + 1), together under
-2 K 2^-53.  The factorization in mixed precision is held to the same bar as the
+K/128 2^(dsh-1) 2^-60 relative, dsh = ceil(log2 K) - 2), together under
+4 K 2^-53.  The factorization in mixed precision is held to the same bar as the
 FP64 form.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 import torch
@@ -87,18 +89,27 @@ def test_ozaki_long_k_runs_in_pieces():
 
 
 def test_ozaki_same_sign_data_near_the_exactness_bound():
-    """All entries positive with every slice large: the group sums of a chunk
-    approach the FP32 exactness bound (8 * 128 * 127^2 < 2^24)."""
+    """Every slice product as large as it gets with one sign: the group sums of
+    a 128-deep chunk approach the FP32 exactness bound (7 * 128 * 128^2 < 2^24).
+    The entries are 2^-54 X with X's balanced base-256 digits -63 (the top
+    one) and -128 (all the others, the last one even so that X has 53
+    significant bits): every product of two slices below the top is +2^14."""
     rng = np.random.default_rng(12)
     M, N, K = 256, 192, 4096
-    # 1 - j 2^-53 with j < 2^10: the 56-bit fixed-point value is 2^56 - 8j, so
-    # slices 0..5 are all 127 (and the dropped pairs are as large as they get)
-    A = 1.0 - rng.integers(1, 1 << 10, size=(M, K)) * 2.0 ** -53
-    Bm = 1.0 - rng.integers(1, 1 << 10, size=(K, N)) * 2.0 ** -53
+
+    c0 = -63 * 2 ** 48 + sum(-128 * 2 ** (8 * (6 - p)) for p in range(1, 6))
+    la = -2 * rng.integers(50, 65, size=(M, K))
+    lb = -2 * rng.integers(50, 65, size=(K, N))
+    A = (c0 + la) * 2.0 ** -54                           # exact: X = c0 + last has 53 significant bits
+    Bm = (c0 + lb) * 2.0 ** -54
     C = dev(np.zeros((M, N)))
     bq.binding.bqrrp_dgemm_ozaki("N", "N", 1.0, dev(A), dev(Bm), 0.0, C)
-    ref = A @ Bm
-    assert np.all(np.abs(np_(C) - ref) <= 8 * K * U + 4 * U * ref)
+    # the exact product, in integers (an FP64 A @ B of same-sign data errs by
+    # far more than the slice product does): sum_k (c0 + la)(c0 + lb) 2^-108
+    s1, s2, s3 = la.sum(axis=1), lb.sum(axis=0), la @ lb
+    exact = np.array([[float(Fraction(K * c0 * c0 + c0 * (int(s1[i]) + int(s2[j])) + int(s3[i, j]), 2 ** 108))
+                       for j in range(N)] for i in range(M)])
+    assert np.all(np.abs(np_(C) - exact) <= 8 * K * U * np.abs(A).max() * np.abs(Bm).max())
 
 
 def test_ozaki_wide_dynamic_range_rows_and_columns():

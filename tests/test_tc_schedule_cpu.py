@@ -24,12 +24,12 @@ def sim(tmp_path_factory):
 
 CASES = [
     # SA, KB, CL, mt, nct, grid
-    (8, 1, 2, 3, 2, 2),        # one k block per tile: both halves end at once
-    (8, 2, 2, 2, 3, 4),
-    (8, 3, 2, 5, 2, 3),        # odd k blocks: the early half keeps its role
-    (8, 4, 2, 4, 4, 5),        # even k blocks: the roles alternate between tiles
-    (8, 9, 2, 70, 2, 7),       # more row tiles than one raster group
-    (8, 512, 2, 2, 1, 2),      # long K (W = Y^T C): many chunks per tile
+    (7, 1, 2, 3, 2, 2),        # one k block per tile: both halves end at once
+    (7, 2, 2, 2, 3, 4),
+    (7, 3, 2, 5, 2, 3),        # odd k blocks: the early half keeps its role
+    (7, 4, 2, 4, 4, 5),        # even k blocks: the roles alternate between tiles
+    (7, 9, 2, 70, 2, 7),       # more row tiles than one raster group
+    (7, 512, 2, 2, 1, 2),      # long K (W = Y^T C): many chunks per tile
     (1, 5, 2048, 3, 3, 2),     # the sketch: one A plane, one chunk per tile
     (1, 40, 16, 2, 2, 3),      # the sketch with several chunks per tile
     (1, 1, 2048, 1, 1, 1),
