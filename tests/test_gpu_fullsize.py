@@ -85,12 +85,13 @@ def apply_q(F, tau, Z, transpose=False, nb=256):
 
 # The configuration's largest size, m = n = 32768 (b = 256, d = 320, iid
 # N(0,1), the bench's input), held to the same properties in the FP64 and the
-# mixed form.  No 32768^2 Q is formed: for a
+# mixed forms.  No 32768^2 Q is formed: for a
 # matrix E and a probe block X with iid N(0,1) entries (p columns),
 # E ||E X||_F^2 = p ||E||_F^2, so ||E X||_F / sqrt(p) estimates ||E||_F (within
 # a small factor with overwhelming probability at p = 16).  Q is applied to
-# the probes from the reflectors block by block (apply_q).
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+# the probes from the reflectors block by block (apply_q).  The FP32 sketch
+# QRCP variant is held to the same bar.
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_sketch32"])
 def test_largest_size_factorization_probes(precision):
     m = n = 32768
     p = 16
