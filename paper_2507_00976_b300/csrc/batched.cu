@@ -1299,7 +1299,7 @@ __device__ void task_done(const BatArgs& a, const MegaArgs& q, int mat, int type
 
 constexpr unsigned long long kPollLimit = 1ull << 27;
 
-__global__ void __launch_bounds__(BT, 2) bat_mega_kernel(BatArgs a, MegaArgs q) {
+__global__ void __launch_bounds__(BT, 3) bat_mega_kernel(BatArgs a, MegaArgs q) {
     __shared__ unsigned long long s_task;
     __shared__ int s_stop;
     __shared__ unsigned int s_low;    // reserved normal slot (valid while s_have)
@@ -1973,7 +1973,8 @@ int batch_plan_launches(const BatchPlan* P) {
 // Picks b per size class (by n: [0,64), [64,128), [128,256), [256,512),
 // [512,1024), [1024, ...)) from {16, 32, 64, 128} (capped at n: a block wider
 // than the matrix only makes the sketch larger) by timing each class alone,
-// then the sketch ratio d/b from {1.25, 1.5} on the whole batch.  Every trial
+// refines each class's pick by one step on the whole batch, then picks the
+// sketch ratio d/b from {1.25, 1.5} on the whole batch.  Every trial
 // factors a fresh copy of the caller's matrices; the caller's A is not
 // modified.
 namespace bq {
@@ -2080,7 +2081,8 @@ size_t batch_autotune_bytes(i64 batch, const i64* m, const i64* n) {
 
 // Per size class of n: the block size b (timing the class alone), then, when
 // ct_out is given, the trailing tile width (32 or 64 columns, timing the class
-// alone with its b); then the sketch ratio gamma over the whole batch.
+// alone with its b); then one step of b per class (half or double) on the
+// whole batch; then the sketch ratio gamma over the whole batch.
 int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, const double* A, double tol,
                    void* ws, size_t ws_bytes, cudaStream_t st, i64* b_out, i64* d_out, i64* ct_out,
                    double* best_ms) {
@@ -2112,6 +2114,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
     const i64 cands[4] = {16, 32, 64, 128};
     std::vector<i64> bsel(batch, 32), dsel(batch, sketch_rows(32, 1.25)), csel(batch, CT);
     std::vector<std::vector<int>> cls(6);
+    std::vector<i64> cls_b(6, 32);
     for (i64 i = 0; i < batch; ++i) cls[size_class(n[i])].push_back((int)i);
     for (int c = 0; c < 6; ++c) {
         if (cls[c].empty()) continue;
@@ -2128,6 +2131,7 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
                 bb = cb;
             }
         }
+        cls_b[c] = bb;
         for (int i : cls[c]) {
             bsel[i] = std::min<i64>(bb, std::max<i64>(n[i], 1));
             dsel[i] = sketch_rows(bsel[i], 1.25);
@@ -2141,14 +2145,45 @@ int batch_autotune(i64 batch, const i64* m, const i64* n, const uint64_t* seed, 
     }
     std::vector<int> all(batch);
     for (i64 i = 0; i < batch; ++i) all[i] = (int)i;
-    double g_best = -1.0, t_best = -1.0;
-    for (double g : {1.25, 1.5}) {
+    // A class timed alone may not fill the GPU, so its pick favours the
+    // shorter critical path of a wider block; in the whole batch the classes
+    // share the SMs and total work decides.  So each class's neighbouring
+    // block sizes (half and double its pick) are retried on the whole batch,
+    // widest class first, keeping a change only when the batch gets faster.
+    double t_best = time_subbatch(all, m, n, seed, A, offsrc, bsel, dsel, csel, tol, tb, st);
+    for (int c = 5; c >= 0 && t_best >= 0.0; --c) {
+        if (cls[c].empty()) continue;
+        int pick = 0;
+        for (int ci = 0; ci < 4; ++ci) {
+            if (cands[ci] == cls_b[c]) pick = ci;
+        }
+        std::vector<i64> bkeep(batch), dkeep(batch);
+        for (int i : cls[c]) { bkeep[i] = bsel[i]; dkeep[i] = dsel[i]; }
+        for (int ci : {pick - 1, pick + 1}) {
+            if (ci < 0 || ci > 3) continue;
+            bool changed = false;
+            for (int i : cls[c]) {
+                bsel[i] = std::min<i64>(cands[ci], std::max<i64>(n[i], 1));
+                dsel[i] = sketch_rows(bsel[i], 1.25);
+                changed |= bsel[i] != bkeep[i];
+            }
+            if (!changed) continue;   // every matrix of the class is narrower than both blocks
+            const double t = time_subbatch(all, m, n, seed, A, offsrc, bsel, dsel, csel, tol, tb, st);
+            if (t >= 0.0 && t < t_best) {
+                t_best = t;
+                for (int i : cls[c]) { bkeep[i] = bsel[i]; dkeep[i] = dsel[i]; }
+            }
+        }
+        for (int i : cls[c]) { bsel[i] = bkeep[i]; dsel[i] = dkeep[i]; }
+    }
+    double g_best = 1.25;
+    {
         std::vector<i64> dg(batch);
-        for (i64 i = 0; i < batch; ++i) dg[i] = sketch_rows(bsel[i], g);
+        for (i64 i = 0; i < batch; ++i) dg[i] = sketch_rows(bsel[i], 1.5);
         const double t = time_subbatch(all, m, n, seed, A, offsrc, bsel, dg, csel, tol, tb, st);
         if (t >= 0.0 && (t_best < 0.0 || t < t_best)) {
             t_best = t;
-            g_best = g;
+            g_best = 1.5;
         }
     }
     if (t_best < 0.0) {
