@@ -934,7 +934,8 @@ def main():
         mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
                  "arith": "FP64-accurate products on bf16 tensor cores (7 exact balanced 8-bit slices, 28 pair products); "
-                          "LU, sketch QR, panel, tau, R in FP64",
+                          "the panel's Gram and its tall solves' block updates also as slice products; "
+                          "LU, sketch QR, Cholesky, reconstruction, tau, R in FP64",
                  "phases_ms": {p_: mprof[p_][0] / mcalls for p_ in B.PHASES}}
         # the variant with the sketch's QR factor in FP32 (pivots from the FP64 LU)
         s32 = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,

@@ -406,6 +406,7 @@ size_t bqrrp_geqrf_mixed_workspace(int64_t m, int64_t n) {
     size_t oz = ozaki_ws_bytes(kOuterQr, nn, mm, kOzPlanes);             // Vo^T C, Vo^T Vo
     oz = std::max(oz, ozaki_ws_bytes(mm, nn, kOuterQr, kOzPlanes));      // C -= Vo Wo2
     oz = std::max(oz, ozaki_ws_bytes(64, nn, mm, kOzPlanes));            // the panels' own updates
+    oz += ozaki_split_reserve();
     ar.take<char>(oz);
     return ar.off + 256;
 }
@@ -428,6 +429,7 @@ int bqrrp_geqrf_mixed(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
     size_t oz = ozaki_ws_bytes(kOuterQr, n, m, kOzPlanes);
     oz = std::max(oz, ozaki_ws_bytes(m, n, kOuterQr, kOzPlanes));
     oz = std::max(oz, ozaki_ws_bytes(64, n, m, kOzPlanes));
+    oz += ozaki_split_reserve();
     c.oz_ws = ar.take<char>(oz);
     c.oz_bytes = oz;
     c.mixed = true;

@@ -343,6 +343,7 @@ void carve(Arena& ar, i64 m, i64 n, i64 b, i64 d, const bqrrp_opts& o, Bufs* B) 
         z = std::max(z, ozaki_ws_bytes(d, n, 64, kOzPlanes));   // LU trailing updates
         z = std::max(z, ozaki_ws_bytes(d, n, d, kOzPlanes));    // R^sk = R1 L^T
         z = std::max(z, ozaki_ws_bytes(64, n, m, kOzPlanes));           // Householder panel updates (HQR panel)
+        z += ozaki_split_reserve();   // the split-K sums of any smaller product (the panel's Gram among them)
         B->oz_bytes = z;
         B->oz_ws = ar.take<char>(z);
     } else if (o.sketch_kind == BQRRP_SKETCH_DENSE) {
@@ -417,8 +418,8 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
     i64 k = *kio;
     View Yv = colmajor(Y, ldy);
     BQ_TRY(copy_mat(c, rows, k, Mp, ldm, Y, ldy));
-    BQ_TRY(trsm_ru(c, rows, k, colmajor(Rsk, ldr), Yv, false));                       // Pre = M Rsk11^-1
-    BQ_TRY(dgemm(c, true, false, k, k, rows, 1.0, Y, ldy, Y, ldy, 0.0, G, ldb, kGemmCUpper));   // G = Pre^T Pre
+    BQ_TRY(trsm_ru_tall(c, rows, k, Rsk, ldr, Y, ldy));                                 // Pre = M Rsk11^-1
+    BQ_TRY(pgemm(c, true, false, k, k, rows, 1.0, Y, ldy, Y, ldy, 0.0, G, ldb, kGemmCUpper));   // G = Pre^T Pre
     BQ_CUDA(cudaMemsetAsync(&c.st->potrf_info, 0x7f, sizeof(int), c.stream));         // "no failure"
     BQ_TRY(potrf_u(c, k, G, ldb));                                                     // Rchol
     DevStatus hs{};
@@ -438,7 +439,7 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
     BQ_LAUNCH_CHECK();
     if (rows > k) {
         BQ_TRY(dgemm(c, false, false, k, k, k, 1.0, U, ldb, G, ldb, 0.0, R11, ldb, kGemmAUpper));   // U Rchol
-        BQ_TRY(trsm_ru(c, rows - k, k, colmajor(R11, ldb), colmajor(Y + k, ldy), false));       // Y2
+        BQ_TRY(trsm_ru_tall(c, rows - k, k, R11, ldb, Y + k, ldy));                             // Y2
     }
     BQ_TRY(trsm_ru(c, k, k, Yv.t(), colmajor(Tb, ldb), true));                        // T = -U S Y1^-T
     BQ_TRY(dgemm(c, false, false, k, w, k, 1.0, G, ldb, Rsk, ldr, 0.0, R11, ldb));     // Rchol Rsk(0:k, 0:w)
@@ -700,12 +701,11 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             if (c.sketch32)
                 BQ_CUDA(cudaMemcpy2DAsync(B.stage, sizeof(double) * B.ldst, Ap, sizeof(double) * lda,
                                           sizeof(double) * rows, w, cudaMemcpyDeviceToDevice, c.stream));
-            {
-                Ctx cp = c;
-                cp.mixed = false;   // preconditioner, Gram, Cholesky, reconstruction, tau and R stay in FP64
-                BQ_TRY(cholqr_panel_steps(cp, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D,
-                                          B.bb, tau + s));
-            }
+            // In the mixed form the panel's two tall solves and its Gram take
+            // FP64-accurate slice products; the Cholesky factor, the
+            // reconstruction, tau and R stay in FP64.
+            BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
+                                      tau + s));
             if (c.sketch32 && k > 0 && k < w) {
                 // R(0:k, k:w) = the first k rows of (I - Y T Y^T)^T A(:, k:w), in FP64
                 double* Sk0 = B.stage + k * B.ldst;

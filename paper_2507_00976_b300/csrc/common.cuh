@@ -244,6 +244,9 @@ int sketch_dense_splits(const Ctx& c, i64 d, i64 m, i64 n);
 
 // dense.cu
 int trsm_ru(const Ctx& c, i64 rows, i64 k, View R, View X, bool unit);   // X <- X * R^{-1}
+// X <- X * R^{-1} for a tall column-major X (R upper, non-unit): with
+// c.mixed the updates between 64-column blocks are pgemm products.
+int trsm_ru_tall(const Ctx& c, i64 rows, i64 k, const double* R, i64 ldr, double* X, i64 ldx);
 int potrf_u(const Ctx& c, i64 k, double* G, i64 ldg);                    // G = R^T R, info -> st
 int modlu(const Ctx& c, i64 rows, i64 k, double* Y, i64 ldy, double* D); // Householder reconstruction LU
 int copy_mat(const Ctx& c, i64 rows, i64 cols, const double* src, i64 lds, double* dst, i64 ldd);
@@ -266,6 +269,10 @@ int cholqr_panel_steps(const Ctx& c, i64 rows, i64 w, i64* kio, double* Mp, i64 
 constexpr int kOzPlanes = 7;              // balanced 8-bit slices per FP64 operand (54-bit fixed point)
 constexpr i64 kOzMaxK = (i64)1 << 17;     // K per slice-GEMM launch (longer K is split)
 size_t ozaki_ws_bytes(i64 M, i64 N, i64 K, int sa);
+// Bytes to add to a workspace sized as the largest of several ozaki_ws_bytes
+// so that every product whose slice planes fit it also has room for its
+// split-K integer sums.
+size_t ozaki_split_reserve();
 int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, const double* A, i64 lda,
                const double* B, i64 ldb, double beta, double* C, i64 ldc, void* ws, size_t ws_bytes);
 int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double* A, i64 lda, double* Msk, i64 ldsk,

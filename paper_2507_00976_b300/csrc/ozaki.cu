@@ -147,15 +147,29 @@ int check_flag(const Ctx& c, int* flag) {
 }  // namespace
 
 int ozaki_tc_gemm(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
-                  i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err);
+                  i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err,
+                  unsigned long long* acc64);
 int ozaki_tc_sketch(const Ctx& c, const __nv_bfloat16* Ss, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
                     i64 N, const int* ea, const int* eb, double* C, i64 ldc, int* err);
 
-// Workspace (bytes) for ozaki_gemm / ozaki_sketch on these sizes.
+// Products of at most this many 128 x 64 tiles may split K over the SMs
+// (half of B300's 148; a GPU with more SMs splits only when the workspace
+// holds the integer sums).
+constexpr i64 kSplitMaxTiles = 74;
+
+bool ozaki_may_split(i64 M, i64 N) { return cdiv(imax(M, 1), 128) * cdiv(imax(N, 1), 64) <= kSplitMaxTiles; }
+
+size_t ozaki_split_reserve() { return sizeof(unsigned long long) * (size_t)(kSplitMaxTiles * 128 * 64) + 256; }
+
+// Workspace (bytes) for ozaki_gemm / ozaki_sketch on these sizes: the slice
+// planes, the exponents, and for a product that may split K its M x N
+// integer sums.
 size_t ozaki_ws_bytes(i64 M, i64 N, i64 K, int sa) {
     const i64 Mp = rup(imax(M, 1), OBM), Np = rup(imax(N, 1), OBN), Kp = rup(imax(K, 1), OBK);
-    return ((size_t)sa * Mp * Kp + (size_t)kSlices * Np * Kp) * sizeof(__nv_bfloat16) +
-           (size_t)(Mp + Np) * sizeof(int) + 2048;
+    size_t z = ((size_t)sa * Mp * Kp + (size_t)kSlices * Np * Kp) * sizeof(__nv_bfloat16) +
+               (size_t)(Mp + Np) * sizeof(int) + 2048;
+    if (sa == kSlices && ozaki_may_split(M, N)) z += sizeof(unsigned long long) * (size_t)(imax(M, 1) * imax(N, 1)) + 256;
+    return z;
 }
 
 // C = alpha op(A) op(B) + beta C, FP64 in and out, products on the bf16 tensor cores.
@@ -173,6 +187,9 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
     int* ea = ar.take<int>((size_t)Mp);
     int* eb = ar.take<int>((size_t)Np);
     int* flag = ar.take<int>(1);
+    unsigned long long* acc64 = nullptr;
+    if (ozaki_may_split(M, N) || ar.off + sizeof(unsigned long long) * (size_t)(M * N) + 256 <= ar.cap)
+        acc64 = ar.take<unsigned long long>((size_t)(M * N));
     if (!ar.ok()) { set_error("ozaki_gemm: workspace too small"); return BQRRP_ENOMEM; }
     // exponents: rows of op(A), columns of op(B) (= rows of op(B)^T)
     row_exp_kernel<<<(unsigned)M, 256, 0, c.stream>>>(M, K, A, lda, ta ? 1 : 0, ea);
@@ -188,7 +205,7 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
     BQ_LAUNCH_CHECK();
     int* err = c.st ? &c.st->err_timeout : flag;
     if (!c.st) BQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
-    BQ_TRY(ozaki_tc_gemm(c, As, Mp, Bs, Np, Kp, M, N, ea, eb, alpha, beta, C, ldc, err));
+    BQ_TRY(ozaki_tc_gemm(c, As, Mp, Bs, Np, Kp, M, N, ea, eb, alpha, beta, C, ldc, err, acc64));
     return check_flag(c, flag);
 }
 
@@ -198,6 +215,25 @@ int pgemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha, con
         ozaki_ws_bytes(M, N, K, kSlices) <= c.oz_bytes)
         return ozaki_gemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.oz_ws, c.oz_bytes);
     return dgemm(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+}
+
+// Right-looking blocked solve: each 64-column block of X is solved against
+// its diagonal block of R in FP64 (trsm_ru), then removed from the columns to
+// its right with one product.  In the mixed form those products (three
+// quarters of the solve's work for k = 256) run on the tensor cores; with the
+// FP64 form, or when X is short, this is trsm_ru itself.
+int trsm_ru_tall(const Ctx& c, i64 rows, i64 k, const double* R, i64 ldr, double* X, i64 ldx) {
+    constexpr i64 kBlk = 64;
+    if (!c.mixed || !c.oz_ws || rows < 2048 || k <= kBlk)
+        return trsm_ru(c, rows, k, colmajor(R, ldr), colmajor(X, ldx), false);
+    for (i64 jb = 0; jb < k; jb += kBlk) {
+        const i64 nb = imin(kBlk, k - jb);
+        BQ_TRY(trsm_ru(c, rows, nb, colmajor(R + jb + jb * ldr, ldr), colmajor(X + jb * ldx, ldx), false));
+        if (jb + nb < k)   // X(:, jb+nb:k) -= X(:, jb:jb+nb) R(jb:jb+nb, jb+nb:k)
+            BQ_TRY(pgemm(c, false, false, rows, k - jb - nb, nb, -1.0, X + jb * ldx, ldx, R + jb + (jb + nb) * ldr,
+                         ldr, 1.0, X + (jb + nb) * ldx, ldx));
+    }
+    return 0;
 }
 
 // Columns of A sliced at a time by ozaki_sketch (the slice planes of a block

@@ -232,7 +232,21 @@ struct TcArgs {
     double* C;
     i64 ldc;
     int* err;
+    // Split K: plan.ntiles = tiles x nsplit, tile index = split * tiles + tile,
+    // split s covering k blocks [s KB, (s + 1) KB).  Each split adds its 64-bit
+    // integers into acc64 (M x N, column-major, zeroed before the launch); a
+    // second kernel converts the sums.  nsplit = 1: acc64 is unused.
+    int nsplit;
+    unsigned long long* acc64;
 };
+
+// Split and tile (within the split) of a tile index.
+__device__ __forceinline__ int split_of(const TcArgs* p, int tile, int* t) {
+    const int per = p->plan.mt * p->plan.nct;
+    const int s = tile / per;
+    *t = tile - s * per;
+    return s;
+}
 
 // Barrier addresses: full_a[8], empty_a[8], full_b[3], empty_b[3], acc_full[2], acc_empty[2], drain.
 struct Bars {
@@ -253,26 +267,27 @@ struct ProducerV {
     uint32_t sA, sB;
     const CUtensorMap* tmA;
     const CUtensorMap* tmB;
-    int m0, n0;                    // origin of the current tile
+    int m0, n0, kb0;               // origin of the current tile; its split's first k block
     long long last_a[tcs::kNAS];   // last fill issued per slot (-1: none)
     long long last_b[tcs::kNBS];
     __device__ __forceinline__ void tile_begin(int tile) {
-        int rt, ct;
-        tcs::tile_coords(p->plan, tile, &rt, &ct);
+        int rt, ct, t;
+        kb0 = split_of(p, tile, &t) * p->plan.KB;
+        tcs::tile_coords(p->plan, t, &rt, &ct);
         m0 = rt * TC_M;
         n0 = ct * TC_N;
     }
     __device__ __forceinline__ bool load_a(int, int kb, int pl, int slot, long long fill) {
         if (!mbar_wait(bar.empty_a(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
         mbar_expect_tx(bar.full_a(slot), TC_APLANE);
-        tma_load_3d(sA + slot * TC_APLANE, tmA, kb * TC_KB, m0, pl, bar.full_a(slot));
+        tma_load_3d(sA + slot * TC_APLANE, tmA, (kb0 + kb) * TC_KB, m0, pl, bar.full_a(slot));
         last_a[slot] = fill;
         return true;
     }
     __device__ __forceinline__ bool load_b(int, int kb, int h, int slot, long long fill) {
         if (!mbar_wait(bar.empty_b(slot), (uint32_t)((fill & 1) ^ 1), p->err)) return false;
         mbar_expect_tx(bar.full_b(slot), TC_BHALF);
-        tma_load_3d(sB + slot * TC_BHALF, tmB, kb * TC_KB, n0 + h * TC_HN, 0, bar.full_b(slot));
+        tma_load_3d(sB + slot * TC_BHALF, tmB, (kb0 + kb) * TC_KB, n0 + h * TC_HN, 0, bar.full_b(slot));
         last_b[slot] = fill;
         return true;
     }
@@ -374,14 +389,23 @@ struct EpilogueV {
         for (int t = 0; t < TC_NG; ++t) tmem_zero16(tl + (uint32_t)(TC_HN * t));
     }
     __device__ __forceinline__ void tile_end(int tile, int h) {
-        int rt, ct;
-        tcs::tile_coords(p->plan, tile, &rt, &ct);
+        int rt, ct, t;
+        split_of(p, tile, &t);
+        tcs::tile_coords(p->plan, t, &rt, &ct);
         const i64 row = (i64)rt * TC_M + 32 * lq + lane;
         if (row >= p->M) return;
-        const int er = p->ea[row] - 60 + p->dsh;
-        const double alpha = p->alpha, beta = p->beta;
         const i64 col0 = (i64)ct * TC_N + TC_HN * h + 16 * sub;
         const int ncol = (int)(p->N - col0 < 16 ? p->N - col0 : 16);
+        if (p->nsplit > 1) {
+            // integer sums add exactly in any order (|total| < 2^62, see above)
+            unsigned long long* ap = p->acc64 + row + col0 * p->M;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < ncol) atomicAdd(ap + j * p->M, (unsigned long long)acc[j]);
+            return;
+        }
+        const int er = p->ea[row] - 60 + p->dsh;
+        const double alpha = p->alpha, beta = p->beta;
         double* cp = p->C + row + col0 * p->ldc;
         // alpha = +-1 (a negation of the integer) and beta = 0 or 1 (the
         // library's products) take loops of their own, so that the only FP64
@@ -455,7 +479,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            ProducerV v{&p, bar, su32(sA), su32(sB), &tmA, &tmB, 0, 0, {}, {}};
+            ProducerV v{&p, bar, su32(sA), su32(sB), &tmA, &tmB, 0, 0, 0, {}, {}};
             for (int s = 0; s < tcs::kNAS; ++s) v.last_a[s] = -1;
             for (int s = 0; s < tcs::kNBS; ++s) v.last_b[s] = -1;
             tcs::producer<SA>(p.plan, blockIdx.x, v);
@@ -491,6 +515,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+// The end of a split-K product: C = alpha acc64 2^(ea+eb-60+dsh) + beta C per
+// element, with the epilogue's rounding and its alpha / beta forms.
+__global__ void tc_splitk_finish_kernel(i64 M, i64 N, const unsigned long long* __restrict__ acc64,
+                                        const int* __restrict__ ea, const int* __restrict__ eb, int dsh, double alpha,
+                                        double beta, double* C, i64 ldc) {
+    const i64 total = M * N;
+    for (i64 idx = (i64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (i64)gridDim.x * blockDim.x) {
+        const i64 i = idx % M, j = idx / M;
+        const long long w = (long long)acc64[idx];
+        const int e = ea[i] - 60 + dsh + eb[j];
+        double* cj = C + i + j * ldc;
+        if ((alpha == 1.0 || alpha == -1.0) && beta == 0.0) {
+            *cj = i64_scaled(alpha == -1.0 ? -w : w, e);
+        } else if ((alpha == 1.0 || alpha == -1.0) && beta == 1.0) {
+            *cj = *cj + i64_scaled(alpha == -1.0 ? -w : w, e);
+        } else {
+            const double out = alpha * i64_scaled(w, e);
+            *cj = (beta == 0.0) ? out : fma(beta, *cj, out);
+        }
     }
 }
 
@@ -532,10 +578,14 @@ int make_plane_map(CUtensorMap* tm, const void* base, i64 ldk, i64 kext, i64 row
 }
 
 // One launch over k in [0, kext) of the planes starting at As, Bs (row
-// stride ldk): C = alpha (sum over those k) + beta C.
+// stride ldk): C = alpha (sum over those k) + beta C.  With acc64 (M x N
+// 64-bit integers) a product of fewer than half as many tiles as SMs splits
+// its k blocks over up to SMs / tiles CTAs per tile (at least 4 k blocks
+// each); the splits' integer sums are exact, so the result has the unsplit
+// product's error bound.
 int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np,
               i64 ldk, i64 kext, i64 M, i64 N, const int* ea, const int* eb, double alpha, double beta, double* C,
-              i64 ldc, int* err) {
+              i64 ldc, int* err, unsigned long long* acc64) {
     if (ldk % 8 != 0) { set_error("ozaki_tc: slice rows must be a multiple of 8 elements"); return BQRRP_EUNSUPPORTED; }
     if (kext > kOzMaxK) { set_error("ozaki_tc: K above %lld per launch", (long long)kOzMaxK); return BQRRP_EUNSUPPORTED; }
     if (CL < 2 || (CL & (CL - 1)) != 0) { set_error("ozaki_tc: chunk must be a power of two"); return BQRRP_EUNSUPPORTED; }
@@ -554,23 +604,41 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
     a.C = C;
     a.ldc = ldc;
     a.err = err;
-    const i64 KB = cdiv(kext, TC_KB), mt = cdiv(M, TC_M), nct = cdiv(N, TC_N);
+    i64 KB = cdiv(kext, TC_KB);
+    const i64 mt = cdiv(M, TC_M), nct = cdiv(N, TC_N);
     if (mt * nct > (i64)1 << 30 || KB > (i64)1 << 30) { set_error("ozaki_tc: too many tiles"); return BQRRP_EUNSUPPORTED; }
+    i64 nsplit = 1;
+    if (acc64 && 2 * mt * nct <= (i64)c.dev.sms) {
+        const i64 want = imin((i64)c.dev.sms / (mt * nct), KB / 4);
+        if (want >= 2) {
+            KB = cdiv(KB, want);           // k blocks per split; the last split may run past kext (zero fill)
+            nsplit = cdiv(cdiv(kext, TC_KB), KB);
+        }
+    }
+    a.nsplit = (int)nsplit;
+    a.acc64 = nsplit > 1 ? acc64 : nullptr;
     a.plan.SA = SA;
     a.plan.KB = (int)KB;
     a.plan.CL = CL;
     a.plan.mt = (int)mt;
     a.plan.nct = (int)nct;
-    a.plan.ntiles = (int)(mt * nct);
-    a.plan.grid = (int)imin(mt * nct, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
+    a.plan.ntiles = (int)(mt * nct * nsplit);
+    a.plan.grid = (int)imin(mt * nct * nsplit, (i64)c.dev.sms);   // one CTA per SM (TMEM, shared memory)
+    // dsh follows the whole K, so that the splits' sum stays below 2^62
     int lg = 0;
     while (((i64)1 << lg) < kext) ++lg;
     a.dsh = lg - 2 < 8 ? 8 : lg - 2;
+    if (nsplit > 1) BQ_CUDA(cudaMemsetAsync(acc64, 0, sizeof(unsigned long long) * (size_t)(M * N), c.stream));
     if (SA == 1)
         ozaki_tc_kernel<1><<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
     else
         ozaki_tc_kernel<kOzPlanes><<<(unsigned)a.plan.grid, TC_THREADS, TC_SMEM, c.stream>>>(tmA, tmB, a);
     BQ_LAUNCH_CHECK();
+    if (nsplit > 1) {
+        tc_splitk_finish_kernel<<<(unsigned)imin(cdiv(M * N, 256), 4LL * c.dev.sms), 256, 0, c.stream>>>(
+            M, N, acc64, ea, eb, a.dsh, alpha, beta, C, ldc);
+        BQ_LAUNCH_CHECK();
+    }
     return 0;
 }
 
@@ -582,10 +650,11 @@ int launch_tc(const Ctx& c, int SA, int CL, const __nv_bfloat16* As, i64 Mp, con
 // K beyond kOzMaxK runs as consecutive launches over K pieces, each adding
 // its FP64-rounded part into C.
 int ozaki_tc_gemm(const Ctx& c, const __nv_bfloat16* As, i64 Mp, const __nv_bfloat16* Bs, i64 Np, i64 ldk, i64 M,
-                  i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err) {
+                  i64 N, const int* ea, const int* eb, double alpha, double beta, double* C, i64 ldc, int* err,
+                  unsigned long long* acc64) {
     for (i64 k0 = 0; k0 < ldk; k0 += kOzMaxK)
         BQ_TRY(launch_tc(c, kOzPlanes, 2, As + k0, Mp, Bs + k0, Np, ldk, imin(kOzMaxK, ldk - k0), M, N, ea, eb,
-                         alpha, k0 == 0 ? beta : 1.0, C, ldc, err));
+                         alpha, k0 == 0 ? beta : 1.0, C, ldc, err, acc64));
     return 0;
 }
 
@@ -593,7 +662,7 @@ int ozaki_tc_sketch(const Ctx& c, const __nv_bfloat16* Ss, i64 Mp, const __nv_bf
                     i64 N, const int* ea, const int* eb, double* C, i64 ldc, int* err) {
     for (i64 k0 = 0; k0 < ldk; k0 += kOzMaxK)
         BQ_TRY(launch_tc(c, 1, (int)(kOzMaxK / TC_KB), Ss + k0, Mp, Bs + k0, Np, ldk, imin(kOzMaxK, ldk - k0), M, N,
-                         ea, eb, 1.0, k0 == 0 ? 0.0 : 1.0, C, ldc, err));
+                         ea, eb, 1.0, k0 == 0 ? 0.0 : 1.0, C, ldc, err, nullptr));
     return 0;
 }
 

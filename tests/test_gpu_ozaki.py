@@ -126,6 +126,34 @@ def test_ozaki_wide_dynamic_range_rows_and_columns():
     assert np.all(np_(C)[5] == 0.0)
 
 
+@pytest.mark.parametrize("integer", [True, False])
+def test_ozaki_split_k_gram(integer):
+    """A Gram matrix Y^T Y (256 x 256 from 16384 rows: 8 tiles, so K is split
+    over the SMs and the splits' integer sums are added): exact on integer
+    data, within the FP64 error model otherwise, for beta = 0 and beta != 0."""
+    rng = np.random.default_rng(21 + integer)
+    K, n = 16384, 256
+    if integer:
+        Y = rng.integers(-(1 << 19), 1 << 19, size=(K, n)).astype(np.float64)
+    else:
+        Y = rng.standard_normal((K, n)) * (2.0 ** rng.integers(-30, 30, size=n))[None, :]
+    C = dev(np.zeros((n, n)))
+    bq.binding.bqrrp_dgemm_ozaki("T", "N", 1.0, dev(Y), dev(Y), 0.0, C)
+    if integer:
+        assert np.array_equal(np_(C), (Y.T.astype(np.int64) @ Y.astype(np.int64)).astype(np.float64))
+        return
+    ref = Y.T @ Y
+    cmax = np.abs(Y).max(axis=0)
+    scale = cmax[:, None] * cmax[None, :]
+    assert np.all(np.abs(np_(C) - ref) <= 8 * K * U * scale + 4 * U * (np.abs(Y).T @ np.abs(Y)))
+    C0 = rng.standard_normal((n, n))
+    C = dev(C0)
+    bq.binding.bqrrp_dgemm_ozaki("T", "N", -0.5, dev(Y), dev(Y), 2.0, C)
+    ref = -0.5 * ref + 2.0 * C0
+    assert np.all(np.abs(np_(C) - ref) <= 8 * K * U * 0.5 * scale + 4 * U * (0.5 * (np.abs(Y).T @ np.abs(Y))
+                                                                           + np.abs(2.0 * C0)))
+
+
 def test_ozaki_beta_zero_ignores_nan():
     A = np.ones((70, 5))
     Bm = np.ones((5, 90))
@@ -201,10 +229,14 @@ def _pivots_agree_where_gapped(jpvt, fo, b, rank, gap=1e-3, sig=None):
     return compared
 
 
-@pytest.mark.parametrize("case", ["c1", "ragged", "lowrank", "hqr", "decay14"])
+@pytest.mark.parametrize("case", ["c1", "ragged", "lowrank", "hqr", "decay14", "tall", "tall_lowrank"])
 def test_mixed_factorization_meets_the_fp64_bar(case):
     if case == "c1":
         A, b, d, kw = W.c1_matrix(), 128, 160, {}
+    elif case == "tall":   # panels of >= 2048 rows: the blocked solves with slice-product updates
+        A, b, d, kw = W.gaussian(3000, 700, 5), 256, 320, {}
+    elif case == "tall_lowrank":   # a block keeping 144 of its 256 columns
+        A, b, d, kw = W.low_rank(3000, 700, 400, 8), 256, 320, {}
     elif case == "decay14":   # the mixed configuration's spectrum shape: sigma_k = 10^(-14 (k-1)/(n-1))
         sig = 10.0 ** (-14.0 * np.arange(600) / 599.0)
         A, b, d, kw = W.spectrum(1200, 600, sig, 21), 64, 80, {}
