@@ -137,6 +137,8 @@ def parse():
     p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
     p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")
     p.add_argument("--panel", choices=["cholqr", "hqr"], default="cholqr")
+    p.add_argument("--panel-tc", action="store_true",
+                   help="with a mixed --precision: the panel's Gram and tall-solve updates as slice products")
     p.add_argument("--precision", choices=["fp64", "mixed", "mixed_sketch32"], default="fp64",
                    help="mixed: sketch and trailing-update products on the bf16 tensor cores (exact slices)")
     p.add_argument("--seed", type=int, default=2)
@@ -179,12 +181,15 @@ def workload_name(a):
     sk = "dense Philox +-1" if a.sketch == "dense" else "sparse-sign (8 nnz/col)"
     prec = {"fp64": "FP64", "mixed": "mixed-precision (bf16 tensor-core slices, FP64 accuracy)",
             "mixed_sketch32": "mixed-precision (bf16 tensor-core slices, FP64 accuracy; FP32 sketch QR)"}[a.precision]
+    if getattr(a, "panel_tc", False) and a.precision != "fp64":
+        prec += " with the panel's Gram and tall-solve updates as slices"
     return f"{prec} BQRRP m={a.m} n={a.n} b={a.b} d={a.d}, {fam}, {sk} sketch, {a.panel} panel"
 
 
 def config(a, world):
     return {"workload": workload_name(a), "m": a.m, "n": a.n, "b": a.b, "d": a.d, "family": a.family,
-            "sketch": a.sketch, "panel": a.panel, "precision": a.precision, "seed": a.seed,
+            "sketch": a.sketch, "panel": a.panel, "precision": a.precision,
+            "panel_tc": bool(getattr(a, "panel_tc", False) and a.precision != "fp64"), "seed": a.seed,
             "schedule": a.schedule if (a.precision == "fp64" and a.panel == "cholqr") else "serial",
             "l2": f"inputs larger than L2 (A is {a.m * a.n * 8 / 1e9:.2f} GB, L2 126 MB)",
             "parallelism": "replicas" if world > 1 else "single"}
@@ -846,7 +851,8 @@ def main():
     opts = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
                        B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR,
                        B._PRECISIONS[a.precision],
-                       B.SCHEDULE_OVERLAP if a.schedule == "overlap" else B.SCHEDULE_SERIAL)
+                       B.SCHEDULE_OVERLAP if a.schedule == "overlap" else B.SCHEDULE_SERIAL,
+                       1 if (a.panel_tc and a.precision != "fp64") else 0)
     ws = torch.empty(B.bqrrp_workspace_query(m, n, b, d, opts), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     probe = B.bqrrp_probe_fp64_peak(4000)
@@ -934,8 +940,7 @@ def main():
         mixed = {"gflops": mgf, "ms_mean": statistics.mean(mms), "rank": mrank, "roofline": mixed_roofline(mtf),
                  "speedup_vs_fp64": mgf / (flops / (statistics.mean(step_ms) * 1e-3) / 1e9),
                  "arith": "FP64-accurate products on bf16 tensor cores (7 exact balanced 8-bit slices, 28 pair products); "
-                          "the panel's Gram and its tall solves' block updates also as slice products; "
-                          "LU, sketch QR, Cholesky, reconstruction, tau, R in FP64",
+                          "LU, sketch QR, panel, tau, R in FP64",
                  "phases_ms": {p_: mprof[p_][0] / mcalls for p_ in B.PHASES}}
         # the variant with the sketch's QR factor in FP32 (pivots from the FP64 LU)
         s32 = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
@@ -945,6 +950,18 @@ def main():
         mixed["sketch32"] = {"gflops": flops / (statistics.mean(sms) * 1e-3) / 1e9, "ms_mean": statistics.mean(sms),
                              "rank": srank, "phases_ms": {p_: sprof[p_][0] / scalls for p_ in B.PHASES},
                              "arith": "as above, with the QR that forms R^sk from the sketch's LU factor in FP32"}
+        # the variants with the CholQR panel's Gram and tall-solve updates as slice products
+        for key, prec, what in (("panel_tc", B.PRECISION_MIXED, "the mixed form"),
+                                ("sketch32_panel_tc", B.PRECISION_MIXED_SKETCH32, "the FP32 sketch QR variant")):
+            vo = B.make_opts(B.SKETCH_DENSE if a.sketch == "dense" else B.SKETCH_SPARSE, 8,
+                             B.PANEL_CHOLQR if a.panel == "cholqr" else B.PANEL_HQR, prec, panel_tc=1)
+            vms, vrank, vprof = time_mixed(vo)
+            vcalls = max(1, vprof["calls"])
+            mixed[key] = {"gflops": flops / (statistics.mean(vms) * 1e-3) / 1e9, "ms_mean": statistics.mean(vms),
+                          "rank": vrank, "phases_ms": {p_: vprof[p_][0] / vcalls for p_ in B.PHASES},
+                          "arith": what + ", with the CholQR panel's Gram and the block updates of its two tall "
+                                          "solves also as slice products (opts.panel_tc = 1); Cholesky, "
+                                          "reconstruction LU, tau, R in FP64"}
         if not a.skip_qr:
             mq = time_own_qr(A, A0, "mixed", 3)[1:]   # one warm-up run, two timed
             mixed["own_qr_gflops"] = flops / (statistics.mean(mq) * 1e-3) / 1e9

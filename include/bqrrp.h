@@ -50,9 +50,9 @@ extern "C" {
 /* Arithmetic of the dense products (sketch S*A and the trailing update). */
 #define BQRRP_PRECISION_FP64 0   /* FP64 SIMT throughout                            */
 #define BQRRP_PRECISION_MIXED 1  /* sketch and trailing-update products on the bf16
-                                    tensor cores through exact 7-bit slices (see
-                                    bqrrp_dgemm_ozaki); LU, sketch QR, panel, tau, R
-                                    in FP64                                          */
+                                    tensor cores through exact balanced 8-bit slices
+                                    (see bqrrp_dgemm_ozaki); LU, sketch QR, panel,
+                                    tau, R in FP64                                   */
 #define BQRRP_PRECISION_MIXED_SKETCH32 2 /* as _MIXED, and Alg. 2 on the sketch in
                                     FP32 arithmetic: the LU panels' pivot search and
                                     eliminations (the sketch stays FP64 in memory,
@@ -78,7 +78,14 @@ typedef struct bqrrp_opts {
     int panel_kind;      /* BQRRP_PANEL_CHOLQR (default) or BQRRP_PANEL_HQR    */
     int64_t precision;   /* BQRRP_PRECISION_FP64 (default), _MIXED or _MIXED_SKETCH32 */
     int64_t schedule;    /* BQRRP_SCHEDULE_OVERLAP (default) or _SERIAL         */
-    int64_t reserved[3]; /* must be zero                                        */
+    int64_t panel_tc;    /* 0 (default): the CholQR panel in FP64.  1 (only with
+                            a _MIXED precision): the panel's Gram matrix and the
+                            block updates of its two tall triangular solves
+                            (the preconditioner and the reconstruction's) as
+                            FP64-accurate slice products on the tensor cores;
+                            the Cholesky factor, the reconstruction's LU, tau
+                            and R stay in FP64                                  */
+    int64_t reserved[2]; /* must be zero                                        */
 } bqrrp_opts;
 
 /*

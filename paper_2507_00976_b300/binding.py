@@ -40,7 +40,7 @@ _lib = None
 
 class Opts(ctypes.Structure):
     _fields_ = [("sketch_kind", ctypes.c_int), ("sketch_nnz", _i64), ("panel_kind", ctypes.c_int),
-                ("precision", _i64), ("schedule", _i64), ("reserved", _i64 * 3)]
+                ("precision", _i64), ("schedule", _i64), ("panel_tc", _i64), ("reserved", _i64 * 2)]
 
 
 NPHASES = 8
@@ -211,13 +211,14 @@ def _ptr(t):
 
 
 def make_opts(sketch_kind=SKETCH_DENSE, nnz=8, panel_kind=PANEL_CHOLQR, precision=PRECISION_FP64,
-              schedule=SCHEDULE_OVERLAP):
+              schedule=SCHEDULE_OVERLAP, panel_tc=0):
     o = Opts()
     o.sketch_kind = sketch_kind
     o.sketch_nnz = nnz
     o.panel_kind = panel_kind
     o.precision = precision
     o.schedule = schedule
+    o.panel_tc = panel_tc
     return o
 
 
@@ -452,10 +453,11 @@ def bqrrp_launch_counter():
 
 # ----------------------------------------------------------------- convenience
 def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64", schedule="overlap",
-           stream=None):
+           panel_tc=False, stream=None):
     """Factor a copy of A (any 2-D float64 tensor/array); returns
     (F column-major with R and reflectors, jpvt, tau, rank) as device tensors.
-    precision: "fp64", "mixed" or "mixed_sketch32"."""
+    precision: "fp64", "mixed" or "mixed_sketch32"; panel_tc (mixed only):
+    the CholQR panel's Gram and tall-solve updates as slice products."""
     torch = _torch()
     F = to_colmajor(A)
     m, n = F.shape
@@ -464,7 +466,7 @@ def factor(A, b, d, seed, sketch="dense", nnz=8, panel="cholqr", precision="fp64
     opts = make_opts(SKETCH_DENSE if sketch == "dense" else SKETCH_SPARSE, nnz,
                      PANEL_CHOLQR if panel == "cholqr" else PANEL_HQR,
                      _PRECISIONS[precision],
-                     SCHEDULE_OVERLAP if schedule == "overlap" else SCHEDULE_SERIAL)
+                     SCHEDULE_OVERLAP if schedule == "overlap" else SCHEDULE_SERIAL, 1 if panel_tc else 0)
     rank = bqrrp_factor(F, b, d, seed, jpvt, tau, opts=opts, stream=stream)
     return F, jpvt[:n], tau[:n], rank
 

@@ -371,6 +371,7 @@ bqrrp_opts defaults(const bqrrp_opts* o) {
         r.panel_kind = o->panel_kind;
         r.precision = o->precision;
         r.schedule = o->schedule;
+        r.panel_tc = o->panel_tc;
     }
     return r;
 }
@@ -387,7 +388,9 @@ int check_opts(const bqrrp_opts* o, i64 d) {
         o->precision != BQRRP_PRECISION_MIXED_SKETCH32)
         return 1;
     if (o->schedule != BQRRP_SCHEDULE_OVERLAP && o->schedule != BQRRP_SCHEDULE_SERIAL) return 1;
-    for (int i = 0; i < 3; ++i)
+    if (o->panel_tc != 0 && o->panel_tc != 1) return 1;
+    if (o->panel_tc == 1 && o->precision == BQRRP_PRECISION_FP64) return 1;   // slice products need a mixed form
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return 1;
     return 0;
 }
@@ -701,11 +704,16 @@ int factor_impl(i64 m, i64 n, double* A, i64 lda, i64 b, i64 d, uint64_t seed, i
             if (c.sketch32)
                 BQ_CUDA(cudaMemcpy2DAsync(B.stage, sizeof(double) * B.ldst, Ap, sizeof(double) * lda,
                                           sizeof(double) * rows, w, cudaMemcpyDeviceToDevice, c.stream));
-            // In the mixed form the panel's two tall solves and its Gram take
-            // FP64-accurate slice products; the Cholesky factor, the
-            // reconstruction, tau and R stay in FP64.
-            BQ_TRY(cholqr_panel_steps(c, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D, B.bb,
-                                      tau + s));
+            {
+                // The panel stays in FP64 unless opts.panel_tc asks for its Gram
+                // and its tall solves' block updates as FP64-accurate slice
+                // products (the Cholesky factor, the reconstruction's LU, tau and
+                // R stay in FP64 either way).
+                Ctx cp = c;
+                cp.mixed = c.mixed && o.panel_tc == 1;
+                BQ_TRY(cholqr_panel_steps(cp, rows, w, &k, Ap, lda, Ssk, d, B.Ypan, m, B.G, B.U, B.Tb, B.R11, B.D,
+                                          B.bb, tau + s));
+            }
             if (c.sketch32 && k > 0 && k < w) {
                 // R(0:k, k:w) = the first k rows of (I - Y T Y^T)^T A(:, k:w), in FP64
                 double* Sk0 = B.stage + k * B.ldst;

@@ -60,8 +60,12 @@ def test_argument_errors_follow_info_convention():
     assert _factor_rc(10, 8, 4, 5, opts=bad)[0] == -11
     assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(schedule=2))[0] == -11
     bad = B.make_opts()
-    bad.reserved[2] = 1
+    bad.reserved[1] = 1
     assert _factor_rc(10, 8, 4, 5, opts=bad)[0] == -11
+    # the tensor-core panel only with a mixed precision, and only 0 or 1
+    assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(panel_tc=1))[0] == -11
+    assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(precision=B.PRECISION_MIXED, panel_tc=2))[0] == -11
+    assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(precision=B.PRECISION_MIXED, panel_tc=1))[0] == -3
     assert _factor_rc(10, 8, 4, 5, opts=B.make_opts(schedule=B.SCHEDULE_SERIAL))[0] == -3   # valid opts, A NULL
     assert _factor_rc(10, 8, 4, 5)[0] == -3                         # A is NULL
     rc, rank = _factor_rc(10, 0, 4, 5)

@@ -35,11 +35,12 @@ def problem():
     return A, J0, margin
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_sketch32"])
-def test_full_size_factorization(problem, precision):
+@pytest.mark.parametrize("precision,panel_tc", [("fp64", False), ("mixed", False), ("mixed_sketch32", False),
+                                                ("mixed", True)])
+def test_full_size_factorization(problem, precision, panel_tc):
     A, J0, margin = problem
     Ad = bq.to_colmajor(A)
-    F, jpvt, tau, rank = bq.factor(Ad, BLK, D, SEED, precision=precision)
+    F, jpvt, tau, rank = bq.factor(Ad, BLK, D, SEED, precision=precision, panel_tc=panel_tc)
     torch.cuda.synchronize()
     assert rank == N
     j = jpvt.to(torch.int64) - 1
@@ -91,12 +92,13 @@ def apply_q(F, tau, Z, transpose=False, nb=256):
 # a small factor with overwhelming probability at p = 16).  Q is applied to
 # the probes from the reflectors block by block (apply_q).  The FP32 sketch
 # QRCP variant is held to the same bar.
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_sketch32"])
-def test_largest_size_factorization_probes(precision):
+@pytest.mark.parametrize("precision,panel_tc", [("fp64", False), ("mixed", False), ("mixed_sketch32", False),
+                                                ("mixed_sketch32", True)])
+def test_largest_size_factorization_probes(precision, panel_tc):
     m = n = 32768
     p = 16
     A0 = W.gaussian_torch(m, n, 2)                                   # column-major, on the device
-    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1, precision=precision)
+    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1, precision=precision, panel_tc=panel_tc)
     torch.cuda.synchronize()
     assert rank == n
     j = jpvt.to(torch.int64) - 1

@@ -261,6 +261,33 @@ def test_mixed_factorization_meets_the_fp64_bar(case):
                   + 1e-13 * np.linalg.norm(A))
 
 
+@pytest.mark.parametrize("case", ["c1", "tall", "tall_lowrank", "decay14"])
+def test_mixed_panel_tc_meets_the_fp64_bar(case):
+    """opts.panel_tc: the CholQR panel's Gram and the block updates of its two
+    tall solves as slice products (FP64-accurate: the same bars)."""
+    if case == "c1":
+        A, b, d = W.c1_matrix(), 128, 160
+    elif case == "tall":
+        A, b, d = W.gaussian(3000, 700, 5), 256, 320
+    elif case == "tall_lowrank":
+        A, b, d = W.low_rank(3000, 700, 400, 8), 256, 320
+    else:
+        sig = 10.0 ** (-14.0 * np.arange(600) / 599.0)
+        A, b, d = W.spectrum(2400, 600, sig, 21), 128, 160
+    fo = oracle.bqrrp(A, b, d, 1)
+    F, jpvt, tau, rank = _factor_mixed(A, b, d, 1, panel_tc=True)
+    assert rank == fo.rank
+    if case == "decay14":
+        assert _pivots_agree_where_gapped(jpvt, fo, b, rank, gap=1e-6, sig=sig) >= 2
+    elif all(t["margin"] > 1e-6 for t in fo.trace):
+        assert np.array_equal(jpvt[:rank], fo.jpvt[:rank])
+    res, orth, ok = metrics(A, F, jpvt, tau, rank)
+    assert ok and res <= 1e-12 and orth <= 1e-12, (res, orth)
+    bounds = list(range(0, A.shape[1], b))
+    assert np.all(trailing_norms(F, rank, bounds) <= 1.1 * trailing_norms(fo.A, fo.rank, bounds)
+                  + 1e-13 * np.linalg.norm(A))
+
+
 @pytest.mark.parametrize("m,n,zero_col", [(300, 200, None), (2049, 130, None), (1000, 1000, None),
                                           (5000, 300, None), (700, 600, 300)])
 def test_own_qr_mixed_matches_oracle(m, n, zero_col):
