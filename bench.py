@@ -135,6 +135,8 @@ def parse():
                    help="block size (the configuration sweeps 256, 512, 1024, 2048; 256 is the fastest on this part)")
     p.add_argument("--d", type=int, default=None)
     p.add_argument("--family", choices=["gaussian", "spectrum"], default="gaussian")
+    p.add_argument("--decay", type=float, default=12.0,
+                   help="family spectrum: sigma_k = 10^(-decay (k-1)/(n-1)) (14: the mixed configuration)")
     p.add_argument("--sketch", choices=["dense", "sparse"], default="dense")
     p.add_argument("--panel", choices=["cholqr", "hqr"], default="cholqr")
     p.add_argument("--panel-tc", action="store_true",
@@ -177,7 +179,8 @@ def parse():
 
 
 def workload_name(a):
-    fam = "iid N(0,1)" if a.family == "gaussian" else "U diag(sigma) V^T, sigma geometric 1..1e-12"
+    dec = getattr(a, "decay", 12.0)
+    fam = "iid N(0,1)" if a.family == "gaussian" else f"U diag(sigma) V^T, sigma geometric 1..1e-{dec:g}"
     sk = "dense Philox +-1" if a.sketch == "dense" else "sparse-sign (8 nnz/col)"
     prec = {"fp64": "FP64", "mixed": "mixed-precision (bf16 tensor-core slices, FP64 accuracy)",
             "mixed_sketch32": "mixed-precision (bf16 tensor-core slices, FP64 accuracy; FP32 sketch QR)"}[a.precision]
@@ -188,6 +191,7 @@ def workload_name(a):
 
 def config(a, world):
     return {"workload": workload_name(a), "m": a.m, "n": a.n, "b": a.b, "d": a.d, "family": a.family,
+            "decay": getattr(a, "decay", 12.0) if a.family == "spectrum" else None,
             "sketch": a.sketch, "panel": a.panel, "precision": a.precision,
             "panel_tc": bool(getattr(a, "panel_tc", False) and a.precision != "fp64"), "seed": a.seed,
             "schedule": a.schedule if (a.precision == "fp64" and a.panel == "cholqr") else "serial",
@@ -295,7 +299,7 @@ def cpu_plan(a, budget_s=60.0):
     for s in (4096, 8192):
         if last is not None and t_used + last["s"] * (s / last["n"]) ** 3 > budget_s:
             break
-        A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -12.0),
+        A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -getattr(a, "decay", 12.0)),
                                                                                 a.seed)
         dt = time_oracle(A, a.b, a.d, ncpu, sk)
         t_used += dt
@@ -322,7 +326,7 @@ def host_lapack_context(a, s=4096):
     import scipy.linalg as sla
 
     from paper_2507_00976_b300 import workloads as W
-    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -12.0), a.seed)
+    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -getattr(a, "decay", 12.0)), a.seed)
     threads = None
     try:
         from threadpoolctl import threadpool_info
@@ -351,7 +355,7 @@ def run_reference(a, world, rank):
     s = 2048
     b, d = a.b, a.d
     _, ncpu = host_cpu()
-    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -12.0), a.seed)
+    A = W.gaussian(s, s, a.seed) if a.family == "gaussian" else W.spectrum(s, s, W.geometric_sigma(s, -getattr(a, "decay", 12.0)), a.seed)
     oracle.set_threads(ncpu)
     for _ in range(a.warmup):
         oracle.bqrrp(A, b, d, 1)
@@ -844,7 +848,7 @@ def main():
     if a.family == "gaussian":
         A0 = W.gaussian_torch(m, n, seed)
     else:
-        A0 = W.spectrum_torch(m, n, W.geometric_sigma(min(m, n), -12.0), seed)
+        A0 = W.spectrum_torch(m, n, W.geometric_sigma(min(m, n), -a.decay), seed)
     A = bq.colmajor_empty(m, n)
     jpvt = torch.empty(n, dtype=torch.int64, device="cuda")
     tau = torch.empty(n, dtype=torch.float64, device="cuda")

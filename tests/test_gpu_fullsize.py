@@ -120,3 +120,49 @@ def test_largest_size_factorization_probes(precision, panel_tc):
     del F
     torch.cuda.empty_cache()
     assert res.item() <= 1e-12 and orth.item() <= 1e-12, (precision, res.item(), orth.item())
+
+
+# The mixed configuration's input shape at 16384^2: sigma_k = 10^(-14 (k-1)/(n-1)),
+# U and V from QR of N(0,1) matrices.  The spectrum crosses the rank threshold
+# (10 d u of the first block's sketch scale) near its end, so rank < n: the
+# probes use the first `rank` reflectors and rows of R, and the residual then
+# includes the truncation error ||R(rank:, rank:)||, about sigma_rank.  The
+# values are printed (run with -s).
+@pytest.fixture(scope="module")
+def spectrum14():
+    return W.spectrum_torch(M, N, W.geometric_sigma(N, -14.0), 5)
+
+
+@pytest.mark.parametrize("precision,panel_tc", [("fp64", False), ("mixed", False), ("mixed_sketch32", False),
+                                                ("mixed", True), ("mixed_sketch32", True)])
+def test_mixed_configuration_spectrum_probes(spectrum14, precision, panel_tc):
+    A0 = spectrum14
+    p = 16
+    F, jpvt, tau, rank = bq.factor(A0, BLK, D, 1, precision=precision, panel_tc=panel_tc)
+    torch.cuda.synchronize()
+    # the cut sits where sigma meets the threshold, and the spectrum is flat
+    # there (a factor 1.5 spans 200 columns): the forms' ranks differ by
+    # hundreds of columns, and the FP32 sketch QRCP may keep them all
+    assert N - N // 10 < rank <= N
+    j = jpvt.to(torch.int64) - 1
+    assert torch.equal(torch.sort(j).values, torch.arange(N, device=j.device))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    X = torch.randn(N, p, generator=g, dtype=torch.float64, device="cuda")
+    PX = torch.zeros_like(X)
+    PX[j] = X
+    lhs = A0 @ PX
+    Z = torch.zeros(M, p, dtype=torch.float64, device="cuda")
+    Z[:rank] = torch.triu(F[:rank]) @ X
+    tk = tau[:rank]
+    res = torch.linalg.norm(lhs - apply_q(F, tk, Z)) / (p ** 0.5 * torch.linalg.norm(A0))
+    Y = torch.randn(M, p, generator=g, dtype=torch.float64, device="cuda")
+    orth = torch.linalg.norm(apply_q(F, tk, apply_q(F, tk, Y), transpose=True) - Y) / p ** 0.5
+    del F
+    torch.cuda.empty_cache()
+    print(f"\n{precision}{' + panel_tc' if panel_tc else ''}: rank {rank}, residual {res.item():.2e}, "
+          f"orthogonality {orth.item():.2e}")
+    # the FP32 sketch QRCP's R^sk preconditions the deepest blocks less well
+    # (about 1e-11 at 2048^2 on this spectrum shape): an order above that
+    fp32 = precision == "mixed_sketch32"
+    assert res.item() <= 1e-12 and orth.item() <= (1e-10 if fp32 else 1e-12), (precision, res.item(), orth.item())
