@@ -18,7 +18,7 @@
 //     Every partial sum is an integer of magnitude at most 7 * Kc * 128^2 <
 //     2^24 for a K chunk Kc = 128, so FP32 holds it exactly; after each chunk
 //     the seven group sums are combined exactly, rounded to a multiple of
-//     2^dsh (dsh = ceil(log2 K) + 1) and added into one 64-bit integer per
+//     2^dsh (dsh = max(ceil(log2 K) - 2, 8)) and added into one 64-bit integer per
 //     element (ozaki_tc.cu), which is rounded once to FP64 at the end.
 // Balanced digits halve the largest slice magnitude of unsigned 8-bit ones,
 // which is what lets eight bits per slice keep a 128-deep exact chunk.  The

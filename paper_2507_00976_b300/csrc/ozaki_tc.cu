@@ -33,7 +33,7 @@
 //               overlaps the other half's MMAs;
 //   warps 2-17  epilogue, eight warps per half (warp w reads TMEM lanes
 //               32 (w % 4) ..; two warps share a lane quarter, 16 columns
-//               each).  After each chunk a warp reads the eight groups with
+//               each).  After each chunk a warp reads the seven groups with
 //               tcgen05.ld, zeroes them with tcgen05.st, releases the half and
 //               forms the chunk's exact value per element,
 //                 W = (sum_{t <= 2} G_t 2^(8(2-t))) 2^32 + sum_{t >= 3} G_t 2^(8(6-t)),
@@ -41,6 +41,10 @@
 //               integer; after a tile's last chunk (the half is already
 //               released for the next tile) C = alpha acc 2^(ea+eb-60+dsh) + beta C,
 //               the integer rounded once to FP64 with integer operations.
+// Split K: a product of fewer tiles than half the SMs runs each tile as
+// several CTAs over consecutive ranges of k blocks; each adds its 64-bit sums
+// into an integer buffer with atomics (exact in any order) and a second kernel
+// converts them (TcArgs).
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error
 // flag, the roles stop issuing work, in-flight copies and MMAs are waited for
 // (bounded), TMEM is freed and the CTA returns.

@@ -11,7 +11,7 @@
 //
 // Layout recap (ozaki_tc.cu has the full description): a C tile is 128 x 64;
 // its two 32-column halves h = 0, 1 own TMEM columns [256 h, 256 h + 256),
-// eight groups of 32.  A k block is 64 deep.  Per k block and half there is one
+// seven groups of 32 used.  A k block is 64 deep.  Per k block and half there is one
 // "segment": the MMAs of that half over all A planes.  A half's accumulators
 // are read by the epilogue every CL k blocks (a chunk); the two halves' chunk
 // ends are staggered by CL/2 k blocks, and in each k block the half whose
@@ -28,11 +28,11 @@
 namespace tcs {
 
 constexpr int kNAS = 8;    // A slots (one plane tile each)
-constexpr int kNBS = 3;    // B slots (one half-stage each: 8 planes x 32 rows)
+constexpr int kNBS = 3;    // B slots (one half-stage each: 7 planes x 32 rows)
 constexpr int kGroupRows = 64;   // row tiles per raster group
 
 struct Plan {
-    int SA;       // planes of op(A): 8 (FP64 split) or 1 (the +-1 sketch)
+    int SA;       // planes of op(A): 7 (FP64 split) or 1 (the +-1 sketch)
     int KB;       // 64-deep k blocks per tile
     int CL;       // k blocks per exact chunk, a power of two (2, or 2048 for the sketch)
     int mt, nct;  // row tiles, column tiles
@@ -83,7 +83,7 @@ TC_HD bool ascending(long long seg) {
     return (seg & 1) ? !asc0 : asc0;
 }
 
-// Slot and fill count of A plane p in global k block G.  With 8 planes each
+// Slot and fill count of A plane p in global k block G.  With 7 planes each
 // plane has a slot of its own (refilled once per k block); with one plane the
 // slots form a ring over k blocks.
 TC_HD int a_slot(const Plan& P, long long G, int p) { return P.SA == 1 ? (int)(G & (kNAS - 1)) : p; }
