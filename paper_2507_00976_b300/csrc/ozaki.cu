@@ -58,31 +58,89 @@ __device__ __forceinline__ long long fixed54(double x, int e) {
     return (bits >> 63) ? -X : X;
 }
 
-// Row maxima exponents of op(A) (M rows, K columns); trans: op(A)(i,k) = A[k + i*lda].
-__global__ void row_exp_kernel(i64 M, i64 K, const double* A, i64 lda, int trans, int* e) {
-    const i64 i = (i64)blockIdx.x;
-    double mx = 0.0;
-    for (i64 k = threadIdx.x; k < K; k += blockDim.x) {
-        const double v = trans ? A[k + i * lda] : A[i + k * lda];
-        mx = fmax(mx, fabs(v));
-    }
-    __shared__ double red[32];
+// |v| as its bit pattern, which orders like the value for non-negative
+// doubles; NaN counts as 0 (as fmax would ignore it).  The maxima are taken
+// on these integers: FP64 min/max runs at the FP64 pipe's rate on this part,
+// integer compares at the full ALU rate.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+
+// Row maxima exponents of op(A) (M rows, K columns).  trans: op(A)(i,k) =
+// A[k + i*lda], a row is contiguous and one warp takes it; else op(A)(i,k) =
+// A[i + k*lda], 32 consecutive rows per block (one per lane, so every warp
+// load is 32 consecutive doubles) with the eight warps splitting K.  Four
+// independent maxima per thread keep several loads in flight.
+constexpr int kRowExpThreads = 256;
+__global__ void __launch_bounds__(kRowExpThreads) row_exp_kernel(i64 M, i64 K, const double* __restrict__ A,
+                                                                 i64 lda, int trans, int* __restrict__ e) {
+    typedef unsigned long long u64;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    if (trans) {
+        const i64 i = (i64)blockIdx.x * 8 + warp;
+        if (i >= M) return;
+        const double* row = A + i * lda;
+        i64 k = lane;
+        for (; k + 96 < K; k += 128) {
+            m0 = max(m0, abs_bits(row[k]));
+            m1 = max(m1, abs_bits(row[k + 32]));
+            m2 = max(m2, abs_bits(row[k + 64]));
+            m3 = max(m3, abs_bits(row[k + 96]));
+        }
+        for (; k < K; k += 32) m0 = max(m0, abs_bits(row[k]));
+        u64 mx = max(max(m0, m1), max(m2, m3));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if (lane == 0) e[i] = exp_above(__longlong_as_double((long long)mx));
+        return;
+    }
+    __shared__ u64 part[8][32];
+    const i64 i = (i64)blockIdx.x * 32 + lane;
+    if (i < M) {
+        const double* col = A + i;
+        i64 k = warp;
+        for (; k + 24 < K; k += 32) {
+            m0 = max(m0, abs_bits(col[k * lda]));
+            m1 = max(m1, abs_bits(col[(k + 8) * lda]));
+            m2 = max(m2, abs_bits(col[(k + 16) * lda]));
+            m3 = max(m3, abs_bits(col[(k + 24) * lda]));
+        }
+        for (; k < K; k += 8) m0 = max(m0, abs_bits(col[k * lda]));
+    }
+    part[warp][lane] = max(max(m0, m1), max(m2, m3));
     __syncthreads();
-    if (threadIdx.x < 32) {
-        mx = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+    if (warp == 0 && i < M) {
+        u64 mx = part[0][lane];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        if (threadIdx.x == 0) e[i] = exp_above(mx);
+        for (int w = 1; w < 8; ++w) mx = max(mx, part[w][lane]);
+        e[i] = exp_above(__longlong_as_double((long long)mx));
     }
+}
+
+// Blocks of row_exp_kernel for M rows.
+inline unsigned row_exp_blocks(i64 M, int trans) { return (unsigned)(trans ? (M + 7) / 8 : (M + 31) / 32); }
+
+// Bias that turns balanced base-256 digits into bytes: for |X| < 2^54 the
+// seven digits q_p in [-128, 127] (X = sum_p q_p 2^(8 (6 - p))) are the bytes
+// of X + sum_p 128 2^(8p), each minus 128 (the sum of digits plus 128 is the
+// plain base-256 representation of the biased value, which lies in
+// (2^54, 2^56)).
+constexpr long long kDigitBias = 0x80808080808080LL;
+
+// FP32 bit pattern of the integer b - 128, b in [0, 255]: 2^23 + b is exact
+// in FP32 (its bit pattern is 0x4B000000 | b) and the subtraction of 2^23 + 128
+// is exact.  Its upper 16 bits are the bf16 of b - 128 (8 significant bits).
+__device__ __forceinline__ uint32_t digit_f32(uint32_t b) {
+    return __float_as_uint(__uint_as_float(0x4B000000u | b) - 8388736.0f);
 }
 
 // Split op(X) (R rows x K columns, row r scaled by 2^-e[r]) into kSlices bf16
 // slices S[p][r][k] (row length ldk >= K, rows padded to Rp with zeros, k
 // padded to ldk with zeros).  trans: op(X)(r,k) = X[k + r*ldx] (k contiguous),
 // else op(X)(r,k) = X[r + k*ldx] (r contiguous; staged through shared memory).
+// Each thread writes two adjacent k of one row as one 32-bit word per plane.
 __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ldk, const double* X, i64 ldx,
                                                     int trans, const int* e, __nv_bfloat16* S) {
     __shared__ double tile[32][33];
@@ -100,17 +158,22 @@ __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ld
     }
     __syncthreads();
     const size_t slice = (size_t)Rp * (size_t)ldk;
-    for (int q = ty; q < 32; q += 8) {
-        const i64 r = r0 + q, k = k0 + tx;
-        if (r >= Rp || k >= ldk) continue;
-        long long X = (r < R && k < K) ? fixed54(tile[q][tx], e[r]) : 0;
-        // balanced digits from the least significant: q = ((X + 128) mod 256) - 128,
-        // then X = (X - q) / 256 exactly; |X| < 2^54 leaves |q_0| <= 65
+    const int kp = 2 * (threadIdx.x & 15);   // k pair within the tile
+    for (int q = threadIdx.x >> 4; q < 32; q += 16) {
+        const i64 r = r0 + q, k = k0 + kp;
+        if (r >= Rp || k >= ldk) continue;   // ldk is even, so k + 1 < ldk too
+        const int er = r < R ? e[r] : 0;
+        const long long X0 = (r < R && k < K) ? fixed54(tile[q][kp], er) : 0;
+        const long long X1 = (r < R && k + 1 < K) ? fixed54(tile[q][kp + 1], er) : 0;
+        const unsigned long long Z0 = (unsigned long long)(X0 + kDigitBias);
+        const unsigned long long Z1 = (unsigned long long)(X1 + kDigitBias);
+        uint32_t* out = reinterpret_cast<uint32_t*>(S + (size_t)r * ldk + k);
 #pragma unroll
-        for (int p = kSlices - 1; p >= 0; --p) {
-            const int v = (int)((X + 128) & 255) - 128;
-            X = (X - v) >> 8;
-            S[(size_t)p * slice + (size_t)r * ldk + k] = __int2bfloat16_rn(v);
+        for (int p = 0; p < kSlices; ++p) {
+            const int sh = 8 * (kSlices - 1 - p);   // plane 0 holds the most significant digit
+            const uint32_t b0 = (uint32_t)(Z0 >> sh) & 255u, b1 = (uint32_t)(Z1 >> sh) & 255u;
+            // low half: the bf16 of element k, high half: of element k + 1
+            out[(size_t)p * (slice / 2)] = __byte_perm(digit_f32(b0), digit_f32(b1), 0x7632);
         }
     }
 }
@@ -192,9 +255,9 @@ int ozaki_gemm(const Ctx& c, bool ta, bool tb, i64 M, i64 N, i64 K, double alpha
         acc64 = ar.take<unsigned long long>((size_t)(M * N));
     if (!ar.ok()) { set_error("ozaki_gemm: workspace too small"); return BQRRP_ENOMEM; }
     // exponents: rows of op(A), columns of op(B) (= rows of op(B)^T)
-    row_exp_kernel<<<(unsigned)M, 256, 0, c.stream>>>(M, K, A, lda, ta ? 1 : 0, ea);
+    row_exp_kernel<<<row_exp_blocks(M, ta ? 1 : 0), kRowExpThreads, 0, c.stream>>>(M, K, A, lda, ta ? 1 : 0, ea);
     BQ_LAUNCH_CHECK();
-    row_exp_kernel<<<(unsigned)N, 256, 0, c.stream>>>(N, K, B, ldb, tb ? 0 : 1, eb);
+    row_exp_kernel<<<row_exp_blocks(N, tb ? 0 : 1), kRowExpThreads, 0, c.stream>>>(N, K, B, ldb, tb ? 0 : 1, eb);
     BQ_LAUNCH_CHECK();
     // slices: op(A) rows x K, op(B)^T rows (= N) x K
     split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32)), 256, 0, c.stream>>>(M, K, Mp, Kp, A, lda,
@@ -273,7 +336,7 @@ int ozaki_sketch(const Ctx& c, i64 d, i64 m, i64 n, uint64_t seed, const double*
     for (i64 j0 = 0; j0 < n; j0 += nb) {
         const i64 nj = imin(nb, n - j0), Npj = rup(nj, OBN);
         const double* Aj = A + j0 * lda;
-        row_exp_kernel<<<(unsigned)nj, 256, 0, c.stream>>>(nj, m, Aj, lda, 1, eb);
+        row_exp_kernel<<<row_exp_blocks(nj, 1), kRowExpThreads, 0, c.stream>>>(nj, m, Aj, lda, 1, eb);
         BQ_LAUNCH_CHECK();
         split_kernel<<<dim3((unsigned)(Kp / 32), (unsigned)(Npj / 32)), 256, 0, c.stream>>>(nj, m, Npj, Kp, Aj, lda, 1,
                                                                                            eb, Bs);
