@@ -129,11 +129,12 @@ inline unsigned row_exp_blocks(i64 M, int trans) { return (unsigned)(trans ? (M 
 // (2^54, 2^56)).
 constexpr long long kDigitBias = 0x80808080808080LL;
 
-// FP32 bit pattern of the integer b - 128, b in [0, 255]: 2^23 + b is exact
-// in FP32 (its bit pattern is 0x4B000000 | b) and the subtraction of 2^23 + 128
-// is exact.  Its upper 16 bits are the bf16 of b - 128 (8 significant bits).
-__device__ __forceinline__ uint32_t digit_f32(uint32_t b) {
-    return __float_as_uint(__uint_as_float(0x4B000000u | b) - 8388736.0f);
+// FP32 bit pattern of the integer b - 128, b = byte j (0..3) of w: one byte
+// permute forms 0x4B000000 | b, the FP32 pattern of 2^23 + b (exact), and the
+// subtraction of 2^23 + 128 is exact.  Its upper 16 bits are the bf16 of
+// b - 128 (8 significant bits).
+__device__ __forceinline__ uint32_t digit_f32(uint32_t w, int j) {
+    return __float_as_uint(__uint_as_float(__byte_perm(w, 0x4Bu, 0x4650u | (uint32_t)j)) - 8388736.0f);
 }
 
 // Split op(X) (R rows x K columns, row r scaled by 2^-e[r]) into kSlices bf16
@@ -167,13 +168,14 @@ __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ld
         const long long X1 = (r < R && k + 1 < K) ? fixed54(tile[q][kp + 1], er) : 0;
         const unsigned long long Z0 = (unsigned long long)(X0 + kDigitBias);
         const unsigned long long Z1 = (unsigned long long)(X1 + kDigitBias);
+        const uint32_t w0[2] = {(uint32_t)Z0, (uint32_t)(Z0 >> 32)}, w1[2] = {(uint32_t)Z1, (uint32_t)(Z1 >> 32)};
         uint32_t* out = reinterpret_cast<uint32_t*>(S + (size_t)r * ldk + k);
 #pragma unroll
         for (int p = 0; p < kSlices; ++p) {
-            const int sh = 8 * (kSlices - 1 - p);   // plane 0 holds the most significant digit
-            const uint32_t b0 = (uint32_t)(Z0 >> sh) & 255u, b1 = (uint32_t)(Z1 >> sh) & 255u;
+            const int j = kSlices - 1 - p;   // byte of Z: plane 0 holds the most significant digit
             // low half: the bf16 of element k, high half: of element k + 1
-            out[(size_t)p * (slice / 2)] = __byte_perm(digit_f32(b0), digit_f32(b1), 0x7632);
+            out[(size_t)p * (slice / 2)] =
+                __byte_perm(digit_f32(w0[j >> 2], j & 3), digit_f32(w1[j >> 2], j & 3), 0x7632);
         }
     }
 }
