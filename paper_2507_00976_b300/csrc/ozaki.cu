@@ -147,25 +147,26 @@ __global__ void __launch_bounds__(256) split_kernel(i64 R, i64 K, i64 Rp, i64 ld
     __shared__ double tile[32][33];
     const i64 r0 = (i64)blockIdx.y * 32, k0 = (i64)blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    // load a 32 x 32 tile of op(X) as tile[r][k]
-    for (int q = ty; q < 32; q += 8) {
-        if (trans) {
-            const i64 r = r0 + q, k = k0 + tx;
-            tile[q][tx] = (r < R && k < K) ? X[k + r * ldx] : 0.0;
-        } else {
+    if (!trans) {
+        // load a 32 x 32 tile of op(X) as tile[r][k] (r contiguous in memory)
+        for (int q = ty; q < 32; q += 8) {
             const i64 r = r0 + tx, k = k0 + q;
             tile[tx][q] = (r < R && k < K) ? X[r + k * ldx] : 0.0;
         }
+        __syncthreads();
     }
-    __syncthreads();
     const size_t slice = (size_t)Rp * (size_t)ldk;
     const int kp = 2 * (threadIdx.x & 15);   // k pair within the tile
     for (int q = threadIdx.x >> 4; q < 32; q += 16) {
         const i64 r = r0 + q, k = k0 + kp;
         if (r >= Rp || k >= ldk) continue;   // ldk is even, so k + 1 < ldk too
         const int er = r < R ? e[r] : 0;
-        const long long X0 = (r < R && k < K) ? fixed54(tile[q][kp], er) : 0;
-        const long long X1 = (r < R && k + 1 < K) ? fixed54(tile[q][kp + 1], er) : 0;
+        // k contiguous in memory: the two values straight from global memory
+        // (16 lanes read 32 consecutive doubles), no staging
+        const double x0 = trans ? ((r < R && k < K) ? X[k + r * ldx] : 0.0) : tile[q][kp];
+        const double x1 = trans ? ((r < R && k + 1 < K) ? X[k + 1 + r * ldx] : 0.0) : tile[q][kp + 1];
+        const long long X0 = (r < R && k < K) ? fixed54(x0, er) : 0;
+        const long long X1 = (r < R && k + 1 < K) ? fixed54(x1, er) : 0;
         const unsigned long long Z0 = (unsigned long long)(X0 + kDigitBias);
         const unsigned long long Z1 = (unsigned long long)(X1 + kDigitBias);
         const uint32_t w0[2] = {(uint32_t)Z0, (uint32_t)(Z0 >> 32)}, w1[2] = {(uint32_t)Z1, (uint32_t)(Z1 >> 32)};
