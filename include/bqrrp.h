@@ -289,14 +289,18 @@ size_t bqrrp_dgemm_workspace(int64_t M, int64_t N, int64_t K);
 /*
  * bqrrp_dgemm_ozaki -- the same product as bqrrp_dgemm formed on the bf16
  * tensor cores: each row of op(A) and column of op(B) is scaled by a power of
- * two and cut into nine signed 6-bit integer slices (exact in bf16); the 53
- * slice products with p + q <= 9 are summed exactly in FP32 within K chunks of
- * 256 and recombined in FP64.  The error is a few units of 2^-53 times
+ * two and cut into seven balanced 8-bit integer slices in [-128, 127] (exact
+ * in bf16); the 28 slice products with p + q <= 6 are summed exactly in FP32
+ * within K chunks of 128, combined exactly in 64-bit integers and rounded
+ * once to FP64.  The error is a few units of 2^-53 times
  * max|op(A)(i,:)| * max|op(B)(:,j)| per term -- FP64 accuracy in the normwise
- * sense.  This is the "Ozaki-split" trailing update of the mixed-precision
- * form (the paper's apply_trans_q, Sec. 2.4, computed differently; the
- * splitting itself has no counterpart in the paper).  Needs
- * bqrrp_dgemm_ozaki_workspace() bytes of workspace.
+ * sense; integer data within 2^53 come out exact.  A product of fewer tiles
+ * (128 x 64) than half the SMs splits K over more CTAs and adds their
+ * integer sums exactly (same bound; the result is deterministic).  This is
+ * the "Ozaki-split" trailing update of the mixed-precision form (the paper's
+ * apply_trans_q, Sec. 2.4, computed differently; the splitting itself has no
+ * counterpart in the paper).  Needs bqrrp_dgemm_ozaki_workspace() bytes of
+ * workspace; synchronizes the stream once to read the kernel's wait status.
  */
 int bqrrp_dgemm_ozaki(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha,
                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
@@ -306,9 +310,9 @@ size_t bqrrp_dgemm_ozaki_workspace(int64_t M, int64_t N, int64_t K);
 /*
  * bqrrp_sketch_apply_tc -- Msk = S*A with the dense +-1 operator (as
  * bqrrp_sketch_apply, kind dense) on the bf16 tensor cores: S is one exact
- * slice and A is cut into nine 6-bit slices per column, so the nine products
- * S*A_q give S*A to FP64 accuracy (Alg. 1 sketching step).  Needs
- * bqrrp_sketch_apply_tc_workspace() bytes.
+ * slice and A is cut into seven balanced 8-bit slices per column, so the
+ * seven products S*A_q give S*A to FP64 accuracy (Alg. 1 sketching step).
+ * Needs bqrrp_sketch_apply_tc_workspace() bytes.
  */
 int bqrrp_sketch_apply_tc(int64_t d, int64_t m, int64_t n, const double* A, int64_t lda, uint64_t seed,
                           double* Msk, int64_t ldsk, void* workspace, size_t workspace_bytes,
